@@ -1,0 +1,230 @@
+"""Pins of the FP64 oracle's Sinkhorn pieces (no GPU).
+
+The message-passing marginals and the tree / circle algorithms are checked
+against brute force over the full N^K tensor built directly from the cost
+(Eq. cost_sparse), against Algorithm 1 iterate by iterate where the paper's
+algorithms coincide with it, against the classical two-marginal Sinkhorn, and
+against the invariants the theory fixes (duality, monotonicity, symmetry,
+scale invariance).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import sinkhorn as OS
+from paper_2208_03120_gb300 import workloads as W
+
+
+def _rand_phi(rng, n):
+    return [rng.uniform(0.3, 3.0, size=k) for k in n]
+
+
+def _tree_graph_edges(edges):
+    return [(int(a), int(b)) for a, b in edges]
+
+
+def _circle_graph_edges(K):
+    return [(k, (k + 1) % K) for k in range(K)]
+
+
+@pytest.mark.parametrize("shape", ["path", "star", "tree-random"])
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_tree_marginals_match_bruteforce(shape, d):
+    """Theorem 4.1: P_k(K (.) Phi) by the beta / gamma recursions equals the
+    marginal of the full tensor K (.) Phi for arbitrary positive phi."""
+    rng = np.random.default_rng(10 + d)
+    K = 5
+    prob = W.random_problem(rng, W.TREE, K, d, [3, 4, 2, 3, 4], eta=0.3, shape=shape)
+    phi = _rand_phi(rng, prob.n)
+    P_mp = OS.tree_marginals(prob.x64(), phi, prob.edges, prob.eta, root=int(rng.integers(0, K)))
+    Kt = OS.full_kernel_tensor(prob.x64(), _tree_graph_edges(prob.edges), prob.eta)
+    P_bf = OS.tensor_marginals(OS.plan_tensor(Kt, phi))
+    for a, b in zip(P_mp, P_bf):
+        np.testing.assert_allclose(a, b, rtol=1e-12)
+
+
+@pytest.mark.parametrize("K", [3, 4, 5])
+def test_circle_marginals_match_bruteforce(K):
+    """Theorems 4.2 / 4.3: the circle's alpha / lambda matrix recursions give the
+    marginals of the full tensor for arbitrary positive phi."""
+    rng = np.random.default_rng(20 + K)
+    n = [3, 4, 2, 3, 4][:K]
+    prob = W.random_problem(rng, W.CIRCLE, K, 2, n, eta=0.3)
+    phi = _rand_phi(rng, prob.n)
+    P_mp = OS.circle_marginals(prob.x64(), phi, prob.eta)
+    Kt = OS.full_kernel_tensor(prob.x64(), _circle_graph_edges(K), prob.eta)
+    P_bf = OS.tensor_marginals(OS.plan_tensor(Kt, phi))
+    for a, b in zip(P_mp, P_bf):
+        np.testing.assert_allclose(a, b, rtol=1e-12)
+
+
+def test_tree_structure_relabels_and_rejects():
+    """Section 4.1: after relabelling every non-root node has p(k) < k and the
+    edge set is preserved; a cycle or a disconnected graph is rejected."""
+    rng = np.random.default_rng(3)
+    edges = W.random_tree_edges(rng, 9)
+    t = OS.tree_structure(9, edges, root=4)
+    assert t.order[0] == 4
+    for k in range(1, 9):
+        assert t.parent[k] < k
+    got = {frozenset((t.order[t.parent[k]], t.order[k])) for k in range(1, 9)}
+    assert got == {frozenset(map(int, e)) for e in edges}
+    with pytest.raises(ValueError):
+        OS.tree_structure(4, [[0, 1], [1, 2], [2, 0]])
+    with pytest.raises(ValueError):
+        OS.tree_structure(4, [[0, 1], [2, 3], [0, 1]])
+
+
+def test_path_tree_algorithm2_equals_algorithm1():
+    """On a path rooted at an end, every gamma and beta that Algorithm 2 uses is
+    current, so its sweep equals the Gauss-Seidel sweep of Algorithm 1 on the
+    full tensor: the iterates agree sweep by sweep."""
+    rng = np.random.default_rng(5)
+    prob = W.random_problem(rng, W.TREE, 4, 2, [4, 3, 5, 4], eta=0.2, shape="path")
+    ts = OS.TreeSinkhorn(prob.x64(), prob.mu, prob.edges, prob.eta)
+    hist = []
+    ts.run(6, callback=lambda r, phi: hist.append([p.copy() for p in phi]))
+    Kt = OS.full_kernel_tensor(prob.x64(), _tree_graph_edges(prob.edges), prob.eta)
+    bf = OS.sinkhorn_bruteforce(Kt, prob.mu, 6)
+    for a, b in zip(hist, bf):
+        for pa, pb in zip(a, b):
+            np.testing.assert_allclose(pa, pb, rtol=1e-11)
+
+
+def test_circle_algorithm3_equals_algorithm1():
+    """Algorithm 3 updates phi^1..phi^K in order with current matrices, i.e. the
+    Gauss-Seidel sweep of Algorithm 1 for the circle-structured cost."""
+    rng = np.random.default_rng(6)
+    prob = W.random_problem(rng, W.CIRCLE, 4, 1, [4, 3, 5, 4], eta=0.2)
+    cs = OS.CircleSinkhorn(prob.x64(), prob.mu, prob.eta)
+    hist = []
+    cs.run(6, callback=lambda r, phi: hist.append([p.copy() for p in phi]))
+    Kt = OS.full_kernel_tensor(prob.x64(), _circle_graph_edges(4), prob.eta)
+    bf = OS.sinkhorn_bruteforce(Kt, prob.mu, 6)
+    for a, b in zip(hist, bf):
+        for pa, pb in zip(a, b):
+            np.testing.assert_allclose(pa, pb, rtol=1e-11)
+
+
+def test_star_tree_reaches_algorithm1_fixed_point():
+    """For a star, Algorithm 2 uses the siblings' beta of the previous sweep, so
+    only the fixed point is shared with Algorithm 1: the converged plans agree
+    and reproduce every marginal (Proposition 3.2)."""
+    rng = np.random.default_rng(8)
+    prob = W.random_problem(rng, W.TREE, 5, 1, 3, eta=0.5, shape="star")
+    ts = OS.TreeSinkhorn(prob.x64(), prob.mu, prob.edges, prob.eta)
+    res = ts.run(400)
+    Kt = OS.full_kernel_tensor(prob.x64(), _tree_graph_edges(prob.edges), prob.eta)
+    bf = OS.sinkhorn_bruteforce(Kt, prob.mu, 400)[-1]
+    Pi_a = OS.plan_tensor(Kt, res.phi)
+    Pi_b = OS.plan_tensor(Kt, bf)
+    np.testing.assert_allclose(Pi_a, Pi_b, rtol=1e-9, atol=1e-14)
+    for Pk, m in zip(OS.tensor_marginals(Pi_a), prob.mu):
+        np.testing.assert_allclose(Pk, m, rtol=1e-9)
+
+
+def test_circle_with_unit_closing_edge_is_path_tree():
+    """A circle whose closing edge {K, 1} has weight 0 (kernel identically 1) has
+    the cost of the path 1-2-...-K: Algorithm 3 and Algorithm 2 produce the same
+    iterates (both are the Gauss-Seidel sweep of Algorithm 1)."""
+    rng = np.random.default_rng(9)
+    prob = W.random_problem(rng, W.CIRCLE, 4, 2, [5, 4, 6, 3], eta=0.15)
+    w = [1.0, 1.0, 1.0, 0.0]
+    rc = OS.CircleSinkhorn(prob.x64(), prob.mu, prob.eta, edge_w=w).run(8)
+    rt = OS.TreeSinkhorn(prob.x64(), prob.mu, W.path_edges(4), prob.eta).run(8)
+    for a, b in zip(rc.phi, rt.phi):
+        np.testing.assert_allclose(a, b, rtol=1e-11)
+    np.testing.assert_allclose(rc.S, rt.S, rtol=1e-12)
+
+
+def test_two_marginals_is_classical_sinkhorn():
+    """K = 2 (one edge) reduces to two-marginal Sinkhorn: a = mu^1 / (K b),
+    b = mu^2 / (K^T a), from a = b = 1 updated in that order."""
+    rng = np.random.default_rng(11)
+    prob = W.random_problem(rng, W.TREE, 2, 2, [7, 5], eta=0.1, shape="path")
+    x0, x1 = prob.x64()
+    Kmat = np.exp(-((x0[:, None, :] - x1[None, :, :]) ** 2).sum(-1) / prob.eta)
+    a, b = np.ones(7), np.ones(5)
+    for _ in range(25):
+        a = prob.mu[0] / (Kmat @ b)
+        b = prob.mu[1] / (Kmat.T @ a)
+    res = OS.TreeSinkhorn(prob.x64(), prob.mu, prob.edges, prob.eta).run(25)
+    np.testing.assert_allclose(res.phi[0], a, rtol=1e-12)
+    np.testing.assert_allclose(res.phi[1], b, rtol=1e-12)
+
+
+def test_dual_monotone_and_gap_closes():
+    """Sinkhorn is block-coordinate ascent on S (Theorem 3.1): S^(r) is
+    non-decreasing; at convergence the primal value of Eq. (MOTe) at
+    K (.) Phi (computed entry by entry on the full tensor) equals S."""
+    rng = np.random.default_rng(12)
+    prob = W.random_problem(rng, W.TREE, 4, 2, 4, eta=0.2, shape="tree-random")
+    res = OS.TreeSinkhorn(prob.x64(), prob.mu, prob.edges, prob.eta).run(300)
+    S = np.array(res.S)
+    assert np.all(np.diff(S) >= -1e-13 * np.abs(S[1:]))
+    Kt = OS.full_kernel_tensor(prob.x64(), _tree_graph_edges(prob.edges), prob.eta)
+    P = OS.tensor_marginals(OS.plan_tensor(Kt, res.phi))
+    mass = OS.total_mass(P)
+    dual = OS.dual_value(prob.mu, res.phi, mass, prob.eta)
+    primal = OS.primal_bruteforce(Kt, prob.x64(), None, res.phi, prob.eta)
+    assert abs(primal - dual) < 1e-10 * abs(dual)
+    assert OS.violation(P, prob.mu) < 1e-10
+
+
+def test_primal_value_formula_matches_tensor():
+    """The collapsed primal value eta sum_k P_k . log phi^k - eta mass equals
+    <Pi, C> + eta <Pi, log Pi - 1> summed over the full tensor, for any phi."""
+    rng = np.random.default_rng(13)
+    prob = W.random_problem(rng, W.CIRCLE, 3, 1, [4, 5, 3], eta=0.25)
+    phi = _rand_phi(rng, prob.n)
+    Kt = OS.full_kernel_tensor(prob.x64(), _circle_graph_edges(3), prob.eta)
+    P = OS.tensor_marginals(OS.plan_tensor(Kt, phi))
+    v1 = OS.primal_value(P, phi, OS.total_mass(P), prob.eta)
+    v2 = OS.primal_bruteforce(Kt, prob.x64(), None, phi, prob.eta)
+    assert abs(v1 - v2) < 1e-12 * max(1.0, abs(v2))
+
+
+def test_scale_and_translation_invariance():
+    """exp(-||x - y||^2 / eta) is unchanged under x -> (x - c)/s, eta -> eta/s^2,
+    so the iterates are identical."""
+    rng = np.random.default_rng(14)
+    prob = W.random_problem(rng, W.TREE, 3, 2, 6, eta=0.05, shape="path")
+    c, s = np.array([0.3, -0.1]), 1.7
+    xs = [(a - c) / s for a in prob.x64()]
+    r1 = OS.TreeSinkhorn(prob.x64(), prob.mu, prob.edges, prob.eta).run(20)
+    r2 = OS.TreeSinkhorn(xs, prob.mu, prob.edges, prob.eta / s ** 2).run(20)
+    for a, b in zip(r1.phi, r2.phi):
+        np.testing.assert_allclose(a, b, rtol=1e-10)
+
+
+def test_root_choice_leaves_fixed_point():
+    """Relabelling the root changes the sweep order but not the solution of the
+    strictly convex problem: gauge-fixed potentials agree at convergence."""
+    rng = np.random.default_rng(15)
+    prob = W.random_problem(rng, W.TREE, 5, 1, 4, eta=0.3, shape="tree-random")
+    r0 = OS.TreeSinkhorn(prob.x64(), prob.mu, prob.edges, prob.eta, root=0).run(500)
+    r3 = OS.TreeSinkhorn(prob.x64(), prob.mu, prob.edges, prob.eta, root=3).run(500)
+    u0 = OS.gauge_fix([prob.eta * np.log(p) for p in r0.phi], prob.mu)
+    u3 = OS.gauge_fix([prob.eta * np.log(p) for p in r3.phi], prob.mu)
+    for a, b in zip(u0, u3):
+        np.testing.assert_allclose(a, b, atol=1e-9)
+
+
+def test_path3_workload_against_bruteforce():
+    """The 3-marginal, N=100 path workload: 200 sweeps of Algorithm 2 equal 200
+    sweeps of Algorithm 1 on the full 100^3 tensor (every 50 sweeps compared),
+    and the final marginals of the tensor plan are close to mu."""
+    prob = W.path3_d1()
+    ts = OS.TreeSinkhorn(prob.x64(), prob.mu, prob.edges, prob.eta)
+    hist = {}
+    ts.run(prob.iters, callback=lambda r, phi: hist.__setitem__(r, [p.copy() for p in phi]) if r % 50 == 0 else None)
+    Kt = OS.full_kernel_tensor(prob.x64(), _tree_graph_edges(prob.edges), prob.eta)
+    phi = [np.ones(100) for _ in range(3)]
+    for r in range(1, prob.iters + 1):
+        phi = OS.sinkhorn_bruteforce(Kt, prob.mu, 1, phi0=phi)[-1]
+        if r % 50 == 0:
+            for a, b in zip(hist[r], phi):
+                np.testing.assert_allclose(a, b, rtol=1e-9)
+    P = OS.tensor_marginals(OS.plan_tensor(Kt, phi))
+    assert OS.violation(P, prob.mu) < 1e-6
