@@ -1,0 +1,174 @@
+/*
+ * motfft.h -- C ABI of the NFFT-accelerated multi-marginal Sinkhorn library (libmotfft.so).
+ *
+ * The library computes entropy-regularised multi-marginal optimal transport with a
+ * tree- or circle-structured squared-Euclidean cost (Ba & Quellmalz, "Accelerating the
+ * Sinkhorn algorithm for sparse multi-marginal optimal transport by fast Fourier
+ * transforms", 2022).  The kernel matrix-vector products on the edges are done by
+ * NFFT-based fast summation (Section 5, Algorithm 4) or, for comparison, by dense
+ * direct summation (Eq. fastsum-sum).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers documented as "device" point to CUDA device memory owned by the caller
+ *     (e.g. the storage of torch tensors).  The library never allocates device memory
+ *     inside these calls: scratch comes from the caller's workspace, whose size the
+ *     *_workspace_bytes queries return.  The workspace must be 256-byte aligned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Work is enqueued on it; the calls return after a final readback of a few scalars
+ *     on that stream (they synchronise that stream, not the device).
+ *   - Node labels are 0-based: the paper's node k is label k-1.
+ *   - Return value: MOT_OK or one of the MOT_E* codes below.  No exception crosses the
+ *     ABI.  On an error the output buffers are unspecified.
+ */
+#ifndef MOTFFT_H
+#define MOTFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MOT_ABI_VERSION 1
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define MOT_OK           0
+#define MOT_EINVAL       1  /* bad argument: NULL pointer, size out of range, bad option       */
+#define MOT_ENOTTREE     2  /* MOT_TREE edges do not form a tree on K nodes                    */
+#define MOT_ENOMEM       3  /* caller workspace smaller than the *_workspace_bytes query       */
+#define MOT_ENUMERIC     4  /* NaN / Inf, or a marginal weight that is negative                */
+#define MOT_ENOCONV      5  /* stop test not met within max_iter (results are still valid)     */
+#define MOT_ETIMEOUT     6  /* a bounded device-side wait gave up                              */
+#define MOT_ECUDA        7  /* a CUDA runtime call failed (see mot_last_cuda_error)             */
+#define MOT_EUNSUPPORTED 8  /* valid request outside what this build implements                */
+
+/* ---- enums ----------------------------------------------------------------------- */
+#define MOT_TREE   0        /* Section 4.1: cost decouples along the edges of a tree           */
+#define MOT_CIRCLE 1        /* Section 4.2: edges {k, k+1 mod K}                               */
+
+#define MOT_PATH_NFFT         0  /* fast summation, Algorithm 4 (window spread, FFT, D, iFFT, gather), FP32 */
+#define MOT_PATH_DENSE        1  /* direct summation, Eq. (fastsum-sum), FP32 SIMT                          */
+#define MOT_PATH_DENSE_BF16X3 2  /* direct summation on tensor cores, split hi+lo BF16, FP32 accumulate     */
+
+/* Kernel classes for the optional per-kernel timing of mot_result. */
+#define MOT_K_SPREAD   0    /* window spreading onto the oversampled grid (adjoint NFFT)       */
+#define MOT_K_FFTCONV  1    /* FFT, multiply by D, inverse FFT                                 */
+#define MOT_K_GATHER   2    /* window interpolation from the grid (NFFT) + sweep epilogue      */
+#define MOT_K_DENSE    3    /* dense direct matrix-vector product                              */
+#define MOT_K_NODE     4    /* element-wise sweep updates and FP64 reductions                  */
+#define MOT_K_SETUP    5    /* normalisation, binning, kernel Fourier coefficients             */
+#define MOT_K_CIRCLE   6    /* circle-structure batched kernels                                */
+#define MOT_NKCLASS    8
+
+/* ---- problem --------------------------------------------------------------------- */
+/* Section 2 / Section 4: K marginals mu^k on points x^k in R^d, a tree or a circle, eta. */
+typedef struct {
+    int K;                          /* number of marginals, 2 <= K <= 64                      */
+    int d;                          /* space dimension, 1..3                                  */
+    const int64_t* n;               /* host [K]: n_k, 1 <= n_k <= 2^26                         */
+    const float* const* x;          /* host [K] of device pointers: x^k, row-major [n_k][d]   */
+    const double* const* mu;        /* host [K] of device pointers: mu^k [n_k], >= 0, sum 1    */
+    int topology;                   /* MOT_TREE or MOT_CIRCLE                                 */
+    const int* edges;               /* MOT_TREE: host [2*(K-1)] node pairs; ignored otherwise */
+    const double* edge_w;           /* host weights w_e > 0 of the squared distance
+                                       (Section 6.2): [K-1] in edge order (tree) or [K] for
+                                       edges {k, k+1 mod K} (circle); NULL = all 1            */
+    const unsigned char* free_nodes;/* host [K] or NULL: 1 = node without marginal constraint,
+                                       its scaling is held at 1 (Section 6.2, tree only)      */
+    double eta;                     /* entropic regularisation eta > 0 (Eq. MOTe)             */
+    int root;                       /* tree root label (the paper's node 1)                   */
+} mot_problem;
+
+/* ---- options (zero-initialised fields take the defaults in brackets) ------------- */
+typedef struct {
+    int path;           /* MOT_PATH_* [MOT_PATH_NFFT]                                          */
+    int max_iter;       /* iteration cap [1000]                                                */
+    double tol_viol;    /* stop once max_k ||P_k - mu^k||_1 <= tol_viol [1e-6]; < 0 disables    */
+    double delta_S;     /* stop once |S^(r) - S^(r-1)| < delta_S (Algorithm 2 test) [off]        */
+    int check_every;    /* iterations between stop tests (each test = one host readback) [10]  */
+    int min_iter;       /* iterations always run [0]                                           */
+    int n_grid;         /* oversampled grid length per dimension, power of two 16..4096
+                           (d=1), ..128 (d=2), ..64 (d=3) [64]; M = n_grid/4                     */
+    int m;              /* window cutoff: 2m+2 grid taps per dimension; only m = 4 [4]         */
+    int p;              /* smoothness p of the regularised kernel (Eq. Ker-reg) [3]            */
+    double eps_B;       /* boundary width eps_B of Eq. (Ker-reg), in units of the normalised
+                           period 2*tau = 1 [1/16]                                             */
+    int use_graphs;     /* 1 = replay iterations as a CUDA graph, -1 = plain launches [1]      */
+    int timing;         /* 1 = time every kernel class with CUDA events (slower) [0]          */
+} mot_options;
+
+/* Fill *o with the defaults. */
+void mot_options_default(mot_options* o);
+
+/* ---- result ---------------------------------------------------------------------- */
+typedef struct {
+    double* const* u;       /* in: host [K] of device pointers or NULL.  out: u^k = eta log phi^k
+                               [n_k] FP64 in the caller's point order (scalings, Theorem 3.1)  */
+    double violation;       /* max_k ||P_k(K (.) Phi) - mu^k||_1 at the returned scalings, the
+                               marginals computed with the path's own kernel operator           */
+    double cost_dual;       /* Sinkhorn function S at the returned scalings (Eq. dual_problem) */
+    double cost_primal;     /* Eq. (MOTe) objective at Pi = K (.) Phi                           */
+    double mass;            /* sum of K (.) Phi                                                */
+    double S_last, S_prev;  /* the last two S^(r) of the iteration (Algorithm 2 / 3)           */
+    int iters;              /* Sinkhorn iterations run                                        */
+    int status;             /* same as the return value                                       */
+    long long clamped;      /* fast-summation outputs raised to the positive floor            */
+    long long launches;     /* kernels launched by the call (graph replays counted per node)  */
+    double scale;           /* normalisation x' = (x - c) / scale onto the unit torus          */
+    double eta_norm;        /* eta / scale^2                                                   */
+    int n_grid, M;          /* grid length per dimension and Fourier half-degree used          */
+    double kernel_ms[MOT_NKCLASS];        /* with options.timing: device ms per kernel class   */
+    long long kernel_launches[MOT_NKCLASS];
+} mot_result;
+
+/* ---- entry points ---------------------------------------------------------------- */
+
+/* Human-readable text for a status code (static storage). */
+const char* mot_strerror(int status);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char* mot_last_cuda_error(void);
+
+/* MOT_ABI_VERSION of the loaded library. */
+int mot_abi_version(void);
+
+/*
+ * Workspace bytes needed by mot_solve for this problem and these options (depends on the
+ * sizes only, not on the data).  Returns MOT_EINVAL / MOT_ENOTTREE for a malformed problem.
+ */
+int mot_workspace_bytes(const mot_problem* prob, const mot_options* opt, size_t* bytes);
+
+/*
+ * Sinkhorn for a tree (Algorithm 2) or a circle (Algorithm 3) with the kernel products on
+ * the path selected by opt->path.  Runs until the marginal violation is <= tol_viol (tested
+ * every check_every iterations), |S^(r) - S^(r-1)| < delta_S, or max_iter.  Initial
+ * scalings phi^(0) = 1, or exp(u_warm^k / eta) when u_warm (host [K] of device pointers,
+ * caller order) is not NULL.  Writes u^k and the scalar fields of *res.
+ *   ws/ws_bytes : device workspace of at least mot_workspace_bytes() bytes.
+ *   Errors      : MOT_EINVAL, MOT_ENOTTREE, MOT_ENOMEM, MOT_ENUMERIC, MOT_ECUDA;
+ *                 MOT_ENOCONV when a stop test was requested and not met (results valid).
+ */
+int mot_solve(const mot_problem* prob, const mot_options* opt, void* ws, size_t ws_bytes,
+              const double* const* u_warm, mot_result* res, void* stream);
+
+/*
+ * The kernel matrix-vector product of Eq. (fastsum-sum) on its own:
+ *   beta_r[i] = sum_j alpha_r[j] exp(-||x_tgt[i] - x_src[j]||^2 / eta),  r = 0..nrhs-1,
+ * by the fast summation of Algorithm 4 (opt->path = MOT_PATH_NFFT) or directly
+ * (MOT_PATH_DENSE).  x_src: device [n_src][d] FP32; x_tgt: device [n_tgt][d];
+ * alpha: device [nrhs][n_src] FP32; beta: device [nrhs][n_tgt] FP32 (written).
+ * Both point sets are mapped onto the torus together.  *scale_out (may be NULL)
+ * receives the normalisation scale.  Errors: MOT_EINVAL, MOT_ENOMEM, MOT_ECUDA.
+ */
+int mot_fastsum_workspace_bytes(int d, int64_t n_src, int64_t n_tgt, int nrhs,
+                                const mot_options* opt, size_t* bytes);
+int mot_fastsum(int d, double eta, const float* x_src, int64_t n_src, const float* x_tgt,
+                int64_t n_tgt, const float* alpha, int nrhs, float* beta,
+                const mot_options* opt, void* ws, size_t ws_bytes, double* scale_out,
+                void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOTFFT_H */

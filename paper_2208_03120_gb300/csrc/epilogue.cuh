@@ -1,0 +1,201 @@
+// Source-side products and target-side epilogues of one kernel product (Algorithm 2 / 4).
+#pragma once
+#include "common.cuh"
+
+struct Globals {
+    int* iter;          // device iteration counter (-1 before the first iteration)
+    IterAcc* acc;       // ring of per-iteration accumulators
+    int R;              // ring length
+    float floor_;       // positive floor of fast-summation outputs
+    int n_grid;         // grid length per dimension
+    int M;              // Fourier half-degree
+    const Factor* fac;  // factor array referenced by the tasks
+};
+
+// Element-wise product of a factor list, loaded once per block into shared memory.
+struct FacCache {
+    const float* mant[MOT_MAXFAC];
+    float scale[MOT_MAXFAC];
+    int inv[MOT_MAXFAC];
+    int nf;
+    double L;           // log-scale of the normalised product
+};
+
+__device__ __forceinline__ void load_factors(FacCache& fc, const Factor* F, int f0, int nf) {
+    for (int t = threadIdx.x; t < nf; t += blockDim.x) {
+        Factor f = F[f0 + t];
+        fc.mant[t] = f.mant;
+        fc.scale[t] = 1.f / mx_of(f.sc, f.use_prev);
+        fc.inv[t] = f.inv;
+    }
+    if (threadIdx.x == 0) {
+        double L = 0.0;
+        for (int t = 0; t < nf; ++t) L += factor_L(F[f0 + t]);
+        fc.nf = nf;
+        fc.L = L;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ float eval_prod(const FacCache& fc, int i) {
+    float v = 1.f;
+    for (int f = 0; f < fc.nf; ++f) {
+        float x = __ldg(fc.mant[f] + i) * fc.scale[f];
+        v = fc.inv[f] ? v / x : v * x;
+    }
+    return v;
+}
+
+// Per-thread partial results of an epilogue, reduced once per block.
+struct EpiPartial {
+    float mx_out, mx_phi;
+    double logphi, viol, mass, plogphi;
+    unsigned int clamps;
+};
+
+__device__ __forceinline__ void epi_zero(EpiPartial& e) {
+    e.mx_out = 0.f; e.mx_phi = 0.f; e.logphi = 0.0; e.viol = 0.0; e.mass = 0.0; e.plogphi = 0.0; e.clamps = 0u;
+}
+
+// Block-start duties carried by a task: reset scale records (and keep the previous values of
+// the root scaling) and zero the accumulators of the next iteration.  Run by one thread.
+__device__ __forceinline__ void task_resets(const Task& T, const Globals& G, int bump_iter) {
+    for (int r = 0; r < T.zero_n; ++r) T.zero_d[r] = 0.0;
+    for (int r = 0; r < T.reset_n; ++r) {
+        VecScale* s = T.reset_list[r];
+        if (T.save_prev) { s->ls_prev = s->ls; s->mx_prev_bits = s->mx_bits; }
+        s->mx_bits = 0u;
+        s->clamped = 0u;
+    }
+    if (bump_iter) {
+        int it = *G.iter + 1;
+        *G.iter = it;
+        IterAcc* a = G.acc + ((it + 1) % G.R);
+        a->logphi = 0.0; a->mass = 0.0; a->rootviol = 0.0; a->pad = 0.0;
+    }
+}
+
+// Epilogue of target point i given the raw kernel sum (raw = 1 for EPI_ROOT).
+// Lsrc: log-scale of the source product; tf: target-side factors.
+// lsphi: log-scale of the scaling written by EPI_PHI (-(Lsrc + tf.L)) or EPI_ROOT (-tf.L).
+__device__ __forceinline__ double phi_logscale(const Task& T, const FacCache& tf, double Lsrc) {
+    if (T.mode == EPI_PHI_FREE || (T.mode == EPI_ROOT && T.free_node)) return 0.0;
+    return T.mode == EPI_ROOT ? -tf.L : -(Lsrc + tf.L);
+}
+
+__device__ __forceinline__ void epilogue_point(const Task& T, const FacCache& tf, double Lsrc,
+                                               float floor_, int i, float raw, EpiPartial& ep) {
+    const double lsphi = phi_logscale(T, tf, Lsrc);
+    switch (T.mode) {
+    case EPI_RAW:
+        T.out[i] = raw;
+        break;
+    case EPI_MSG: {
+        float g = raw;
+        if (!(g >= floor_)) { g = floor_; ep.clamps++; }
+        T.out[i] = g;
+        ep.mx_out = fmaxf(ep.mx_out, g);
+        break;
+    }
+    case EPI_PHI: {
+        float g = raw;
+        if (!(g >= floor_)) { g = floor_; ep.clamps++; }
+        if (T.out) T.out[i] = g;
+        float t = eval_prod(tf, i);
+        float ph = T.mu_f[i] / (g * t);
+        T.phi[i] = ph;
+        ep.mx_phi = fmaxf(ep.mx_phi, ph);
+        if (T.mu_d[i] > 0.0) ep.logphi += T.mu_d[i] * (log((double)ph) + lsphi);
+        break;
+    }
+    case EPI_PHI_FREE:
+        if (T.out) {                            // a free node's gamma feeds its children
+            float g = raw;
+            if (!(g >= floor_)) { g = floor_; ep.clamps++; }
+            T.out[i] = g;
+            ep.mx_out = fmaxf(ep.mx_out, g);
+        }
+        T.phi[i] = 1.f;
+        ep.mx_phi = 1.f;
+        break;
+    case EPI_ROOT: {
+        // mass and violation of the last iterate (scale record prev), then the update
+        float t = eval_prod(tf, i);
+        double Lold = ls_of(T.phi_sc, 1) + log((double)mx_of(T.phi_sc, 1));
+        float old = T.phi[i] / mx_of(T.phi_sc, 1);
+        double P = (double)old * (double)t * exp(Lold + tf.L);
+        ep.mass += P;
+        if (T.free_node) {
+            ep.mx_phi = 1.f;
+        } else {
+            ep.viol += fabs(P - T.mu_d[i]);
+            float ph = T.mu_f[i] / t;
+            T.phi[i] = ph;
+            ep.mx_phi = fmaxf(ep.mx_phi, ph);
+            if (T.mu_d[i] > 0.0) ep.logphi += T.mu_d[i] * (log((double)ph) + lsphi);
+        }
+        break;
+    }
+    case EPI_MARG: {
+        float g = raw;
+        if (!(g >= floor_)) { g = floor_; ep.clamps++; }
+        if (T.out) T.out[i] = g;
+        ep.mx_out = fmaxf(ep.mx_out, g);
+        float t = eval_prod(tf, i);            // phi^k and the children's messages
+        double P = (double)g * (double)t * exp(Lsrc + tf.L);
+        ep.mass += P;
+        if (T.mu_d) ep.viol += fabs(P - T.mu_d[i]);
+        if (P > 0.0) ep.plogphi += P * (log((double)T.phi[i]) + ls_of(T.phi_sc, 0));
+        break;
+    }
+    default:
+        break;
+    }
+}
+
+// Reduce the partials of the block and publish them.  All threads call it.
+__device__ __forceinline__ void epi_block_finish(const Task& T, const Globals& G, const FacCache& tf,
+                                                 double Lsrc, EpiPartial ep) {
+    __shared__ float s_mx[2][32];
+    __shared__ double s_d[4][32];
+    __shared__ unsigned int s_c[32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    float a = warp_max(ep.mx_out), b = warp_max(ep.mx_phi);
+    double l = warp_sum_d(ep.logphi), v = warp_sum_d(ep.viol), m = warp_sum_d(ep.mass), pl = warp_sum_d(ep.plogphi);
+    unsigned int c = ep.clamps;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) { s_mx[0][w] = a; s_mx[1][w] = b; s_d[0][w] = l; s_d[1][w] = v; s_d[2][w] = m; s_d[3][w] = pl; s_c[w] = c; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < nw; ++k) {
+            a = fmaxf(a, s_mx[0][k]); b = fmaxf(b, s_mx[1][k]);
+            l += s_d[0][k]; v += s_d[1][k]; m += s_d[2][k]; pl += s_d[3][k]; c += s_c[k];
+        }
+        const bool has_out = (T.mode == EPI_MSG || T.mode == EPI_MARG ||
+                              ((T.mode == EPI_PHI || T.mode == EPI_PHI_FREE) && T.out != nullptr));
+        if (has_out && T.out_sc) {
+            T.out_sc->ls = Lsrc;
+            atomic_max_pos(&T.out_sc->mx_bits, a);
+            if (c) atomicAdd(&T.out_sc->clamped, c);
+        }
+        if (T.mode == EPI_MARG && T.acc_node) {
+            atomicAdd(T.acc_node + 0, v);
+            atomicAdd(T.acc_node + 1, pl);
+            atomicAdd(T.acc_node + 2, m);
+        }
+        if (T.mode == EPI_PHI || T.mode == EPI_ROOT || T.mode == EPI_PHI_FREE) {
+            T.phi_sc->ls = phi_logscale(T, tf, Lsrc);
+            atomic_max_pos(&T.phi_sc->mx_bits, b);
+            int it = *G.iter;
+            IterAcc* nxt = G.acc + ((it + 1) % G.R);
+            if (l != 0.0) atomicAdd(&nxt->logphi, l);
+            if (T.mode == EPI_ROOT) {
+                IterAcc* cur = G.acc + (it % G.R);
+                atomicAdd(&cur->mass, m);
+                atomicAdd(&cur->rootviol, v);
+            }
+        }
+    }
+    __syncthreads();
+}

@@ -1,0 +1,75 @@
+// Host-side launchers of the libmotfft kernels (implemented in nfft.cu, dense.cu, prep.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+#include "epilogue.cuh"
+
+// Binning geometry of the oversampled grid, shared by the binning and the spread / gather kernels.
+inline __host__ __device__ int mot_tile_size(int d, int n) {
+    int t = d == 1 ? 256 : (d == 2 ? 16 : 8);
+    return t < n ? t : n;
+}
+inline __host__ __device__ int mot_sub_points(int d) { return d == 1 ? 1024 : 256; }
+inline __host__ __device__ int mot_ntiles(int d, int n) {
+    int per = n / mot_tile_size(d, n);
+    int t = 1;
+    for (int i = 0; i < d; ++i) t *= per;
+    return t;
+}
+
+// ---- fast summation (nfft.cu) -------------------------------------------------------
+// All take a device array of `ntask` tasks and launch on `st`.
+cudaError_t launch_spread(int d, const Task* tasks, int ntask, int grid_x, const Globals& G, int bump_iter,
+                          cudaStream_t st);
+cudaError_t launch_fftconv(int d, const Task* tasks, int ntask, const Globals& G, cudaStream_t st, int* nlaunch);
+// Configure the shared-memory limits of the FFT kernels for grid length n (call before launching / capturing).
+cudaError_t prepare_fftconv(int d, int n);
+cudaError_t launch_gather(int d, const Task* tasks, int ntask, int grid_x, const Globals& G, cudaStream_t st);
+int spread_smem_bytes(int d, int n);
+
+// ---- dense direct summation (dense.cu) ----------------------------------------------
+cudaError_t launch_dense(int d, const Task* tasks, int ntask, int ntb, int nsplit, const Globals& G,
+                         int bump_iter, cudaStream_t st);
+cudaError_t launch_epi(int d, const Task* tasks, int ntask, int grid_x, const Globals& G, cudaStream_t st);
+
+// ---- set-up (prep.cu) ---------------------------------------------------------------
+struct PrepSet {                 // one point set to normalise and bin
+    const float* x;              // caller points [n][d]
+    const double* mu;            // caller weights or NULL
+    int n;
+    float* u_tmp;                // [d][n] scratch
+    int* tile_of;                // [n] scratch
+    int* counts;                 // [ntiles] scratch
+    int* cursor;                 // [ntiles] scratch
+    float* u;                    // [d][n] sorted coordinates (grid units)
+    int* perm;                   // [n] sorted position -> caller index
+    float* mu_f;                 // [n] or NULL
+    double* mu_d;                // [n] or NULL
+    Sub* subs;                   // [maxsub]
+    int* nsub;                   // [1]
+    int maxsub;
+};
+// Bounding box + radius of the union of sets: out[0..2d) = (min, max) per dim, out[2d] = R^2
+// about the box centre.  `sets` is a device array.
+cudaError_t launch_bounds(const PrepSet* sets, int nsets, int d, float* box_raw, float* out, cudaStream_t st);
+// Normalise (x - c) / s onto the torus in grid units, bin into tiles, sort, build subproblems.
+cudaError_t launch_prep(const PrepSet* sets_dev, const PrepSet* sets_host, int nsets, int d, int n_grid,
+                        const double* c, double s, int* err_flag, cudaStream_t st);
+// kappa_hat by the (2M)^d FFT of Eq. (fft) in FP64, then the half-spectrum multiplier
+// D = w kappa_hat / Psi^2 for the grid of length n per dimension.
+cudaError_t launch_make_D(int d, int M, int n, double eta_n, double tau, double epsB, int p,
+                          const double* poly /* host [2p+1] coefficients in t = r - (tau-epsB) */,
+                          double* scratch_a, double* scratch_b, float* D, cudaStream_t st);
+size_t make_D_scratch_doubles(int d, int M);
+size_t D_floats(int d, int M);
+// u_out[perm[i]] = eta * (log(phi[i]) + ls)
+cudaError_t launch_output(const float* phi, const VecScale* sc, const int* perm, int n, double eta,
+                          double* u_out, cudaStream_t st);
+// phi = 1 (cold) or exp(u_warm[perm[i]]/eta - shift) (warm); sets the scale record and adds
+// sum mu log phi to *logphi.
+cudaError_t launch_init_phi(float* phi, VecScale* sc, const int* perm, const double* mu_d, int n,
+                            const double* u_warm, double eta, double* logphi, float* scratch_max,
+                            cudaStream_t st);
+// Scatter a plain vector into sorted order and back.
+cudaError_t launch_permute_in(const float* src, const int* perm, int n, float* dst, cudaStream_t st);
+cudaError_t launch_permute_out(const float* src, const int* perm, int n, float* dst, cudaStream_t st);

@@ -1,0 +1,1217 @@
+// Host orchestration of libmotfft: C-ABI entry points, plans and the Sinkhorn sweeps.
+//
+// Tree (Algorithm 2).  With the identity phi^p (.) gamma_p (.) beta^{C_p \ k} = mu^p / beta_k,
+// valid right after phi^p is updated from gamma_p and the beta of the previous sweep, the
+// forward messages gamma_k of all children of constrained nodes are independent, so the
+// forward pass is one batched launch (plus dependent levels below free nodes).  The backward
+// pass recomputes beta_k level by level from the leaves.  Every message and scaling is stored
+// as FP32 mantissas with an FP64 log-scale (VecScale); the dual value, marginal violation and
+// cost are FP64 reductions.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+
+namespace {
+thread_local std::string g_cuda_err;
+const double kPi = 3.14159265358979323846;
+const double kTau = 0.5;            // half period of the unit torus
+const double kErrExp = 20.7;        // target exponent: boundary / Fourier-tail terms below e^-20.7 ~ 1e-9
+const int kRing = 64;               // iteration accumulator ring
+}  // namespace
+
+void set_cuda_error(cudaError_t e, const char* what) {
+    g_cuda_err = std::string(what) + ": " + cudaGetErrorString(e);
+}
+
+#define CK(x)                                    \
+    do {                                         \
+        cudaError_t _e = (x);                    \
+        if (_e != cudaSuccess) {                 \
+            set_cuda_error(_e, #x);              \
+            return MOT_ECUDA;                    \
+        }                                        \
+    } while (0)
+
+#define RET(x)                                   \
+    do {                                         \
+        int _r = (x);                            \
+        if (_r != MOT_OK) return _r;             \
+    } while (0)
+
+int max_grid(int d) { return d == 1 ? 4096 : 128; }
+
+GridChoice choose_grid(int d, double R, double eta_min, double eta_max, int n_grid_opt, double epsB) {
+    GridChoice g;
+    const double width = kTau - epsB;
+    const double s_min = 2.0 * R / width;
+    std::vector<int> cands;
+    if (n_grid_opt > 0) {
+        cands.push_back(n_grid_opt);
+    } else {
+        for (int n = 16; n <= max_grid(d); n *= 2) cands.push_back(n);
+    }
+    for (size_t i = 0; i < cands.size(); ++i) {
+        const int n = cands[i];
+        const int M = n / 4;
+        const double A = width * width / eta_max;
+        const double B = kPi * kPi * eta_min * (double)M * (double)M;
+        double s2 = std::sqrt(B / A);
+        if (s2 < s_min * s_min) s2 = s_min * s_min;
+        const double E = std::min(A * s2, B / s2);
+        g.n = n;
+        g.M = M;
+        g.s = std::sqrt(s2);
+        g.err_exp = E;
+        if (E >= kErrExp) break;
+    }
+    if (!(g.s > 0.0)) g.s = 1.0;
+    return g;
+}
+
+bool boundary_poly(double eta, double tau, double epsB, int p, double* c) {
+    // kappa^(r)(a) = (-1/sqrt(eta))^r H_r(a / sqrt(eta)) exp(-a^2/eta), H_r the physicists'
+    // Hermite polynomials (H_{r+1} = 2y H_r - 2r H_{r-1}).
+    const int n = 2 * p + 1;
+    const double a = tau - epsB;
+    const double se = std::sqrt(eta), y = a / se, e0 = std::exp(-a * a / eta);
+    std::vector<double> H(p + 1);
+    H[0] = 1.0;
+    if (p >= 1) H[1] = 2.0 * y;
+    for (int r = 1; r < p; ++r) H[r + 1] = 2.0 * y * H[r] - 2.0 * r * H[r - 1];
+    std::vector<double> Amat(n * n, 0.0), rhs(n, 0.0);
+    int row = 0;
+    double fact = 1.0;
+    for (int r = 0; r <= p; ++r, ++row) {      // value / derivatives at t = 0
+        if (r > 0) fact *= r;
+        Amat[row * n + r] = fact;
+        rhs[row] = std::pow(-1.0 / se, r) * H[r] * e0;
+    }
+    for (int r = 1; r <= p; ++r, ++row) {      // derivatives vanish at t = eps_B
+        for (int j = r; j < n; ++j) {
+            double f = 1.0;
+            for (int q = j - r + 1; q <= j; ++q) f *= q;
+            Amat[row * n + j] = f * std::pow(epsB, j - r);
+        }
+        rhs[row] = 0.0;
+    }
+    // Gaussian elimination with partial pivoting
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (std::fabs(Amat[r * n + col]) > std::fabs(Amat[piv * n + col])) piv = r;
+        if (std::fabs(Amat[piv * n + col]) < 1e-300) return false;
+        if (piv != col) {
+            for (int j = 0; j < n; ++j) std::swap(Amat[col * n + j], Amat[piv * n + j]);
+            std::swap(rhs[col], rhs[piv]);
+        }
+        for (int r = col + 1; r < n; ++r) {
+            double f = Amat[r * n + col] / Amat[col * n + col];
+            if (f == 0.0) continue;
+            for (int j = col; j < n; ++j) Amat[r * n + j] -= f * Amat[col * n + j];
+            rhs[r] -= f * rhs[col];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double s = rhs[r];
+        for (int j = r + 1; j < n; ++j) s -= Amat[r * n + j] * c[j];
+        c[r] = s / Amat[r * n + r];
+    }
+    return true;
+}
+
+void fill_defaults(mot_options& o, const mot_options* in) {
+    std::memset(&o, 0, sizeof(o));
+    if (in) o = *in;
+    if (o.max_iter <= 0) o.max_iter = 1000;
+    if (o.tol_viol == 0.0) o.tol_viol = 1e-6;
+    if (o.check_every <= 0) o.check_every = 10;
+    if (o.check_every > kRing - 4) o.check_every = kRing - 4;
+    if (o.m <= 0) o.m = 4;
+    if (o.p <= 0) o.p = 3;
+    if (o.eps_B <= 0.0) o.eps_B = 1.0 / 16.0;
+    if (o.use_graphs == 0) o.use_graphs = 1;
+}
+
+// =============================================================================================
+// shared set-up: normalisation, binning and the spectral multipliers
+// =============================================================================================
+namespace {
+
+struct SetBufs {
+    int n = 0;
+    float* u = nullptr;
+    int* perm = nullptr;
+    Sub* subs = nullptr;
+    int* nsub = nullptr;
+    int maxsub = 0;
+    float* mu_f = nullptr;
+    double* mu_d = nullptr;
+    // scratch
+    float* u_tmp = nullptr;
+    int* tile_of = nullptr;
+    int* counts = nullptr;
+    int* cursor = nullptr;
+};
+
+void layout_set(Arena& A, SetBufs& S, int n, int d, int n_grid, bool with_mu) {
+    S.n = n;
+    const int ntiles = mot_ntiles(d, n_grid);
+    S.maxsub = (n + mot_sub_points(d) - 1) / mot_sub_points(d) + ntiles;
+    S.u = A.take<float>((size_t)d * n);
+    S.perm = A.take<int>(n);
+    S.subs = A.take<Sub>(S.maxsub);
+    S.nsub = A.take<int>(1);
+    if (with_mu) {
+        S.mu_f = A.take<float>(n);
+        S.mu_d = A.take<double>(n);
+    }
+    S.u_tmp = A.take<float>((size_t)d * n);
+    S.tile_of = A.take<int>(n);
+    S.counts = A.take<int>(ntiles);
+    S.cursor = A.take<int>(ntiles);
+}
+
+PointSet pointset_of(const SetBufs& S) {
+    PointSet p;
+    p.n = S.n;
+    p.u = S.u;
+    p.subs = S.subs;
+    p.nsub = S.nsub;
+    p.maxsub = S.maxsub;
+    return p;
+}
+
+PrepSet prepset_of(const SetBufs& S, const float* x, const double* mu) {
+    PrepSet P;
+    P.x = x;
+    P.mu = mu;
+    P.n = S.n;
+    P.u_tmp = S.u_tmp;
+    P.tile_of = S.tile_of;
+    P.counts = S.counts;
+    P.cursor = S.cursor;
+    P.u = S.u;
+    P.perm = S.perm;
+    P.mu_f = S.mu_f;
+    P.mu_d = S.mu_d;
+    P.subs = S.subs;
+    P.nsub = S.nsub;
+    P.maxsub = S.maxsub;
+    return P;
+}
+
+// Bounding radius of the union of point sets (one host readback), then the grid choice.
+int measure_and_choose(const std::vector<PrepSet>& sets, PrepSet* d_sets, float* box_scratch, float* box_out, int d,
+                       double eta_min, double eta_max, const mot_options& o, GridChoice& g, cudaStream_t st) {
+    CK(cudaMemcpyAsync(d_sets, sets.data(), sizeof(PrepSet) * sets.size(), cudaMemcpyHostToDevice, st));
+    CK(launch_bounds(d_sets, (int)sets.size(), d, box_scratch, box_out, st));
+    float h[7] = {0, 0, 0, 0, 0, 0, 0};
+    CK(cudaMemcpyAsync(h, box_out, sizeof(float) * (2 * d + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double c[3] = {0, 0, 0};
+    for (int t = 0; t < d; ++t) {
+        if (!std::isfinite(h[2 * t]) || !std::isfinite(h[2 * t + 1])) return MOT_ENUMERIC;
+        c[t] = 0.5 * ((double)h[2 * t] + (double)h[2 * t + 1]);
+    }
+    // radius about the FP32 box centre used on the device; add the centre rounding
+    double R = std::sqrt((double)h[2 * d]);
+    double dc = 0.0;
+    for (int t = 0; t < d; ++t) {
+        double cf = (double)(0.5f * (h[2 * t] + h[2 * t + 1]));
+        dc += (cf - c[t]) * (cf - c[t]);
+    }
+    R = R * (1.0 + 1e-6) + std::sqrt(dc) + 1e-30;
+    if (!std::isfinite(R)) return MOT_ENUMERIC;
+    g = choose_grid(d, R, eta_min, eta_max, o.n_grid, o.eps_B);
+    for (int t = 0; t < 3; ++t) g.c[t] = c[t];
+    return MOT_OK;
+}
+
+int make_D_for(double eta_e_norm, const GridChoice& g, int d, const mot_options& o, double* sa, double* sb,
+               float* D, cudaStream_t st) {
+    double poly[2 * 8 + 1];
+    if (o.p > 8) return MOT_EINVAL;
+    if (!boundary_poly(eta_e_norm, kTau, o.eps_B, o.p, poly)) return MOT_ENUMERIC;
+    CK(launch_make_D(d, g.M, g.n, eta_e_norm, kTau, o.eps_B, o.p, poly, sa, sb, D, st));
+    return MOT_OK;
+}
+
+// =============================================================================================
+// tree plan
+// =============================================================================================
+struct Level {
+    std::vector<Task> src, tgt;   // host copies
+    Task* d_src = nullptr;
+    Task* d_tgt = nullptr;
+    int grid_src = 1, grid_tgt = 1, ntb = 1, nsplit = 1;
+};
+
+struct TreePlan {
+    // problem
+    int K = 0, d = 0, path = MOT_PATH_NFFT;
+    double eta = 0.0;
+    std::vector<int> order, new_of, parent, depth;
+    std::vector<std::vector<int>> children;
+    std::vector<int> n;            // BFS labels
+    std::vector<double> w;         // weight of edge {p(k), k}
+    std::vector<unsigned char> free_;
+    GridChoice g;
+    mot_options o;
+    // device buffers
+    std::vector<SetBufs> sets;
+    std::vector<float*> phi, beta, gam, gex, grid, hgrid, rawf, rawb, rawc;
+    std::vector<float2*> spec;
+    std::vector<float*> D;          // per edge
+    VecScale* sc = nullptr;         // [4K]: phi, beta, gamma, gex
+    IterAcc* acc = nullptr;
+    int* iter = nullptr;
+    double* acc_node = nullptr;     // [3K]
+    int* err = nullptr;
+    Factor* d_fac = nullptr;
+    VecScale** d_resets = nullptr;
+    size_t n_resets = 0;
+    PrepSet* d_sets = nullptr;
+    float* box_scratch = nullptr;
+    float* box_out = nullptr;
+    double* dscr_a = nullptr;
+    double* dscr_b = nullptr;
+    char* stats_begin = nullptr;    // contiguous readback region: acc ring, acc_node, sc, err
+    size_t stats_bytes = 0;
+    Task* d_tasks = nullptr;
+    size_t n_tasks_total = 0;
+    // host-side task construction
+    std::vector<Factor> fac;
+    std::vector<VecScale*> resets;
+    std::vector<Level> fwd, bwd, chk;
+    Globals G;
+    // graph
+    cudaGraphExec_t gexec = nullptr;
+    int graph_iters = 0;
+    long long launches_per_iter = 0, launches_per_check = 0;
+
+    VecScale* phi_sc(int k) const { return sc + k; }
+    VecScale* beta_sc(int k) const { return sc + K + k; }
+    VecScale* gam_sc(int k) const { return sc + 2 * K + k; }
+    VecScale* gex_sc(int k) const { return sc + 3 * K + k; }
+};
+
+int validate_problem(const mot_problem* P) {
+    if (!P) return MOT_EINVAL;
+    if (P->K < 2 || P->K > 64 || P->d < 1 || P->d > 3) return MOT_EINVAL;
+    if (!P->n || !P->x || !P->mu) return MOT_EINVAL;
+    if (!(P->eta > 0.0) || !std::isfinite(P->eta)) return MOT_EINVAL;
+    for (int k = 0; k < P->K; ++k) {
+        if (P->n[k] < 1 || P->n[k] > (1 << 26)) return MOT_EINVAL;
+        if (!P->x[k] || !P->mu[k]) return MOT_EINVAL;
+    }
+    if (P->topology != MOT_TREE && P->topology != MOT_CIRCLE) return MOT_EINVAL;
+    if (P->topology == MOT_TREE) {
+        if (!P->edges) return MOT_EINVAL;
+        if (P->root < 0 || P->root >= P->K) return MOT_EINVAL;
+    }
+    int ne = P->topology == MOT_TREE ? P->K - 1 : P->K;
+    if (P->edge_w)
+        for (int e = 0; e < ne; ++e)
+            if (!(P->edge_w[e] > 0.0) || !std::isfinite(P->edge_w[e])) return MOT_EINVAL;
+    return MOT_OK;
+}
+
+// BFS relabelling so that p(k) < k (Section 4.1).
+int tree_structure(const mot_problem* P, TreePlan& T) {
+    const int K = P->K;
+    std::vector<std::vector<std::pair<int, double>>> adj(K);
+    for (int e = 0; e < K - 1; ++e) {
+        int a = P->edges[2 * e], b = P->edges[2 * e + 1];
+        if (a < 0 || a >= K || b < 0 || b >= K || a == b) return MOT_ENOTTREE;
+        double w = P->edge_w ? P->edge_w[e] : 1.0;
+        adj[a].push_back({b, w});
+        adj[b].push_back({a, w});
+    }
+    for (auto& v : adj) std::sort(v.begin(), v.end());
+    T.K = K;
+    T.order.assign(1, P->root);
+    T.new_of.assign(K, -1);
+    T.new_of[P->root] = 0;
+    T.parent.assign(1, -1);
+    T.depth.assign(1, 0);
+    T.w.assign(1, 1.0);
+    std::deque<int> q{P->root};
+    while (!q.empty()) {
+        int u = q.front();
+        q.pop_front();
+        for (auto& vw : adj[u]) {
+            int v = vw.first;
+            if (T.new_of[v] >= 0) continue;
+            T.new_of[v] = (int)T.order.size();
+            T.order.push_back(v);
+            T.parent.push_back(T.new_of[u]);
+            T.depth.push_back(T.depth[T.new_of[u]] + 1);
+            T.w.push_back(vw.second);
+            q.push_back(v);
+        }
+    }
+    if ((int)T.order.size() != K) return MOT_ENOTTREE;
+    T.children.assign(K, {});
+    for (int k = 1; k < K; ++k) T.children[T.parent[k]].push_back(k);
+    for (int k = 0; k < K; ++k)
+        if ((int)T.children[k].size() + 1 > MOT_MAXFAC - 2) return MOT_EUNSUPPORTED;
+    T.n.resize(K);
+    T.free_.assign(K, 0);
+    for (int k = 0; k < K; ++k) {
+        T.n[k] = (int)P->n[T.order[k]];
+        if (P->free_nodes) T.free_[k] = P->free_nodes[T.order[k]] ? 1 : 0;
+    }
+    return MOT_OK;
+}
+
+// Workspace layout of a tree plan (sizes only depend on the problem's shape and the grid).
+void layout_tree(Arena& A, TreePlan& T) {
+    const int K = T.K, d = T.d;
+    const bool nfft = T.path == MOT_PATH_NFFT;
+    const int ng = T.g.n, M = T.g.M;
+    size_t gsz = 1;
+    for (int t = 0; t < d; ++t) gsz *= ng;
+    T.sets.assign(K, SetBufs());
+    for (int k = 0; k < K; ++k) layout_set(A, T.sets[k], T.n[k], d, ng, true);
+    T.phi.assign(K, nullptr);
+    T.beta.assign(K, nullptr);
+    T.gam.assign(K, nullptr);
+    T.gex.assign(K, nullptr);
+    T.grid.assign(K, nullptr);
+    T.hgrid.assign(K, nullptr);
+    T.spec.assign(K, nullptr);
+    T.D.assign(K, nullptr);
+    T.rawf.assign(K, nullptr);
+    T.rawb.assign(K, nullptr);
+    T.rawc.assign(K, nullptr);
+    for (int k = 0; k < K; ++k) T.phi[k] = A.take<float>(T.n[k]);
+    for (int k = 1; k < K; ++k) {
+        const int p = T.parent[k];
+        T.beta[k] = A.take<float>(T.n[p]);
+        T.gam[k] = A.take<float>(T.n[k]);
+        T.gex[k] = A.take<float>(T.n[k]);
+        if (nfft) {
+            T.grid[k] = A.take<float>(gsz);
+            T.hgrid[k] = A.take<float>(gsz);
+            if (d == 3) T.spec[k] = A.take<float2>((size_t)ng * (2 * M + 1) * (M + 1));
+            T.D[k] = A.take<float>(D_floats(d, M));
+        } else {
+            T.rawf[k] = A.take<float>(T.n[k]);
+            T.rawb[k] = A.take<float>(T.n[p]);
+            T.rawc[k] = A.take<float>(T.n[k]);
+        }
+    }
+    // readback region
+    size_t stats = sizeof(IterAcc) * kRing + sizeof(double) * 3 * K + sizeof(VecScale) * 4 * K + 16;
+    T.stats_begin = A.take<char>(stats);
+    T.stats_bytes = stats;
+    if (!A.measure) {
+        T.acc = reinterpret_cast<IterAcc*>(T.stats_begin);
+        T.acc_node = reinterpret_cast<double*>(T.stats_begin + sizeof(IterAcc) * kRing);
+        T.sc = reinterpret_cast<VecScale*>(T.stats_begin + sizeof(IterAcc) * kRing + sizeof(double) * 3 * K);
+        T.err = reinterpret_cast<int*>(T.stats_begin + stats - 16);
+        T.iter = T.err + 1;
+    }
+    T.d_sets = A.take<PrepSet>(K);
+    T.box_scratch = A.take<float>(8);
+    T.box_out = A.take<float>(8);
+    if (nfft) {
+        size_t s = make_D_scratch_doubles(d, M);
+        T.dscr_a = A.take<double>(s);
+        T.dscr_b = A.take<double>(s);
+    }
+    // factor, reset and task arrays: generous upper bounds
+    const size_t maxfac = (size_t)16 * K + 8 * (size_t)K * 4;
+    T.d_fac = A.take<Factor>(maxfac + 64 * (size_t)K);
+    T.d_resets = A.take<VecScale*>(8 * (size_t)K + 8);
+    T.d_tasks = A.take<Task>(16 * (size_t)K + 16);
+}
+
+// ---- task construction ------------------------------------------------------------------
+int add_factor(TreePlan& T, const float* mant, const VecScale* sc, int inv) {
+    Factor f;
+    f.mant = mant;
+    f.sc = sc;
+    f.inv = inv;
+    f.use_prev = 0;
+    T.fac.push_back(f);
+    return (int)T.fac.size() - 1;
+}
+
+Task blank_task() {
+    Task t;
+    std::memset(&t, 0, sizeof(t));
+    return t;
+}
+
+PointSet ps_of(const TreePlan& T, int k) { return pointset_of(T.sets[k]); }
+
+// Source side of the message from node `src` towards neighbour `dst`, built from the current
+// scalings: phi^src (.) [gamma-ex_src] (.) prod of the children's beta except dst.
+void src_general(TreePlan& T, Task& t, int src, int exclude_child, bool with_phi, int gamma_kind) {
+    t.src = ps_of(T, src);
+    t.sf0 = (int)T.fac.size();
+    if (with_phi && !T.free_[src]) add_factor(T, T.phi[src], T.phi_sc(src), 0);
+    if (gamma_kind == 1 && src != 0) add_factor(T, T.gam[src], T.gam_sc(src), 0);
+    if (gamma_kind == 2 && src != 0) add_factor(T, T.gex[src], T.gex_sc(src), 0);
+    for (int c : T.children[src])
+        if (c != exclude_child) add_factor(T, T.beta[c], T.beta_sc(c), 0);
+    t.snf = (int)T.fac.size() - t.sf0;
+}
+
+void tgt_children(TreePlan& T, Task& t, int k, bool with_phi) {
+    t.tf0 = (int)T.fac.size();
+    if (with_phi && !T.free_[k]) add_factor(T, T.phi[k], T.phi_sc(k), 0);
+    for (int c : T.children[k]) add_factor(T, T.beta[c], T.beta_sc(c), 0);
+    t.tnf = (int)T.fac.size() - t.tf0;
+}
+
+void edge_grids(TreePlan& T, Task& t, int k, float* raw) {
+    t.grid = T.grid[k];
+    t.hgrid = T.hgrid[k];
+    t.spec = T.spec[k];
+    t.D = T.D[k];
+    t.raw = raw;
+    const double eta_e = T.eta / T.w[k];
+    const double eta_n = eta_e / (T.g.s * T.g.s);
+    t.eta_u = (float)(eta_n * (double)T.g.n * (double)T.g.n);
+}
+
+void build_tasks(TreePlan& T) {
+    const int K = T.K;
+    T.fac.clear();
+    T.resets.clear();
+    T.fwd.clear();
+    T.bwd.clear();
+    T.chk.clear();
+    int maxdepth = 0;
+    for (int k = 0; k < K; ++k) maxdepth = std::max(maxdepth, T.depth[k]);
+
+    // ---- forward pass: gamma_k and phi^k ------------------------------------------------
+    std::vector<int> flev(K, 0);
+    int nfl = 1;
+    for (int k = 1; k < K; ++k) {
+        const int p = T.parent[k];
+        flev[k] = (p == 0 || !T.free_[p]) ? 0 : flev[p] + 1;
+        nfl = std::max(nfl, flev[k] + 1);
+    }
+    T.fwd.assign(nfl, Level());
+    for (int k = 1; k < K; ++k) {
+        const int p = T.parent[k];
+        Task t = blank_task();
+        if (!T.free_[p]) {
+            // phi^p (.) gamma_p (.) beta^{C_p \ k} = mu^p / beta_k
+            t.src = ps_of(T, p);
+            t.sf0 = (int)T.fac.size();
+            add_factor(T, T.sets[p].mu_f, nullptr, 0);
+            add_factor(T, T.beta[k], T.beta_sc(k), 1);
+            t.snf = 2;
+        } else {
+            src_general(T, t, p, k, false, 1);
+        }
+        edge_grids(T, t, k, T.rawf[k]);
+        t.tgt = ps_of(T, k);
+        t.mode = T.free_[k] ? EPI_PHI_FREE : EPI_PHI;
+        tgt_children(T, t, k, false);
+        t.mu_f = T.sets[k].mu_f;
+        t.mu_d = T.sets[k].mu_d;
+        t.out = T.gam[k];
+        t.out_sc = T.gam_sc(k);
+        t.phi = T.phi[k];
+        t.phi_sc = T.phi_sc(k);
+        T.fwd[flev[k]].src.push_back(t);
+        T.fwd[flev[k]].tgt.push_back(t);
+    }
+    {   // root step: mass and root violation of the last iterate, then phi^1
+        Task t = blank_task();
+        t.tgt = ps_of(T, 0);
+        t.mode = EPI_ROOT;
+        t.free_node = T.free_[0];
+        tgt_children(T, t, 0, false);
+        t.mu_f = T.sets[0].mu_f;
+        t.mu_d = T.sets[0].mu_d;
+        t.phi = T.phi[0];
+        t.phi_sc = T.phi_sc(0);
+        T.fwd[0].tgt.push_back(t);
+    }
+    // duties of the first launch of an iteration: save / reset the scaling records, reset
+    // the gamma records, bump the iteration counter (done by the kernel flag)
+    {
+        size_t r0 = T.resets.size();
+        for (int k = 0; k < K; ++k) T.resets.push_back(T.phi_sc(k));
+        for (int k = 1; k < K; ++k) T.resets.push_back(T.gam_sc(k));
+        Task& t0 = T.fwd[0].src.empty() ? T.fwd[0].tgt[0] : T.fwd[0].src[0];
+        t0.reset_n = (int)(T.resets.size() - r0);
+        t0.reset_list = (VecScale* const*)(uintptr_t)r0;   // resolved to a device pointer later
+        t0.save_prev = 1;
+    }
+
+    // ---- backward pass: beta_k from the deepest level up ---------------------------------
+    T.bwd.assign(std::max(maxdepth, 1), Level());
+    for (int k = K - 1; k >= 1; --k) {
+        Task t = blank_task();
+        src_general(T, t, k, -1, true, 0);
+        edge_grids(T, t, k, T.rawb[k]);
+        t.tgt = ps_of(T, T.parent[k]);
+        t.mode = EPI_MSG;
+        t.out = T.beta[k];
+        t.out_sc = T.beta_sc(k);
+        size_t r0 = T.resets.size();
+        T.resets.push_back(T.beta_sc(k));
+        t.reset_n = 1;
+        t.reset_list = (VecScale* const*)(uintptr_t)r0;
+        const int lev = maxdepth - T.depth[k];       // deepest first
+        T.bwd[lev].src.push_back(t);
+        T.bwd[lev].tgt.push_back(t);
+    }
+
+    // ---- check pass: exact marginals at the current scalings (Theorem 4.1) ----------------
+    T.chk.assign(std::max(maxdepth, 1), Level());
+    for (int k = 1; k < K; ++k) {
+        const int p = T.parent[k];
+        Task t = blank_task();
+        src_general(T, t, p, k, true, 2);
+        edge_grids(T, t, k, T.rawc[k]);
+        t.tgt = ps_of(T, k);
+        t.mode = EPI_MARG;
+        tgt_children(T, t, k, true);
+        t.mu_d = T.free_[k] ? nullptr : T.sets[k].mu_d;
+        t.out = T.gex[k];
+        t.out_sc = T.gex_sc(k);
+        t.phi = T.phi[k];
+        t.phi_sc = T.phi_sc(k);
+        t.acc_node = T.acc_node + 3 * k;
+        T.chk[T.depth[k] - 1].src.push_back(t);
+        T.chk[T.depth[k] - 1].tgt.push_back(t);
+    }
+    {
+        Task t = blank_task();
+        t.tgt = ps_of(T, 0);
+        t.mode = EPI_MARG;
+        tgt_children(T, t, 0, true);
+        t.mu_d = T.free_[0] ? nullptr : T.sets[0].mu_d;
+        t.phi = T.phi[0];
+        t.phi_sc = T.phi_sc(0);
+        t.acc_node = T.acc_node;
+        T.chk[0].tgt.push_back(t);
+        size_t r0 = T.resets.size();
+        for (int k = 1; k < K; ++k) T.resets.push_back(T.gex_sc(k));
+        Task& t0 = T.chk[0].src[0];
+        t0.reset_n = (int)(T.resets.size() - r0);
+        t0.reset_list = (VecScale* const*)(uintptr_t)r0;
+        t0.zero_d = T.acc_node;
+        t0.zero_n = 3 * K;
+    }
+}
+
+// Copy task arrays to the device, resolving reset-list offsets to device pointers.
+int upload_tasks(TreePlan& T, cudaStream_t st) {
+    if (T.fac.size() > (size_t)16 * T.K + 8 * (size_t)T.K * 4 + 64 * (size_t)T.K) return MOT_EUNSUPPORTED;
+    CK(cudaMemcpyAsync(T.d_fac, T.fac.data(), sizeof(Factor) * T.fac.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(T.d_resets, T.resets.data(), sizeof(VecScale*) * T.resets.size(), cudaMemcpyHostToDevice, st));
+    std::vector<Task> all;
+    auto place = [&](std::vector<Level>& levels) {
+        for (auto& L : levels) {
+            for (auto* v : {&L.src, &L.tgt}) {
+                for (auto& t : *v)
+                    if (t.reset_n > 0) t.reset_list = T.d_resets + (uintptr_t)t.reset_list;
+            }
+        }
+    };
+    place(T.fwd);
+    place(T.bwd);
+    place(T.chk);
+    std::vector<std::pair<Level*, int>> slots;
+    for (auto* lv : {&T.fwd, &T.bwd, &T.chk})
+        for (auto& L : *lv) {
+            slots.push_back({&L, 0});
+            for (auto& t : L.src) all.push_back(t);
+            slots.push_back({&L, 1});
+            for (auto& t : L.tgt) all.push_back(t);
+        }
+    if (all.size() > 16 * (size_t)T.K + 16) return MOT_EUNSUPPORTED;
+    CK(cudaMemcpyAsync(T.d_tasks, all.data(), sizeof(Task) * all.size(), cudaMemcpyHostToDevice, st));
+    size_t off = 0;
+    for (auto* lv : {&T.fwd, &T.bwd, &T.chk})
+        for (auto& L : *lv) {
+            L.d_src = T.d_tasks + off;
+            off += L.src.size();
+            L.d_tgt = T.d_tasks + off;
+            off += L.tgt.size();
+            int ms = 1, mt = 1, maxn = 1;
+            for (auto& t : L.src) ms = std::max(ms, t.src.maxsub);
+            for (auto& t : L.tgt) {
+                mt = std::max(mt, t.hgrid ? t.tgt.maxsub : (t.tgt.n + 255) / 256);
+                maxn = std::max(maxn, t.tgt.n);
+            }
+            L.grid_src = std::min(ms, 1024);
+            L.grid_tgt = std::min(mt, 1024);
+            if (T.path != MOT_PATH_NFFT) {
+                L.grid_tgt = std::min((maxn + 255) / 256, 1024);
+                L.ntb = (maxn + 511) / 512;
+                int ns = (int)L.src.size();
+                int target = 4 * 152;
+                int split = target / std::max(1, L.ntb * std::max(ns, 1));
+                L.nsplit = std::max(1, std::min(split, 64));
+            }
+        }
+    T.G.iter = T.iter;
+    T.G.acc = T.acc;
+    T.G.R = kRing;
+    T.G.floor_ = 1e-30f;
+    T.G.n_grid = T.g.n;
+    T.G.M = T.g.M;
+    T.G.fac = T.d_fac;
+    return MOT_OK;
+}
+
+// ---- launching --------------------------------------------------------------------------
+struct Timer {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+    int begin(int cls, cudaEvent_t* a) {
+        if (!on) return 0;
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, st));
+        ev.push_back({cls, {e0, e1}});
+        *a = e1;
+        return 0;
+    }
+    int end(cudaEvent_t e1) {
+        if (!on) return 0;
+        CK(cudaEventRecord(e1, st));
+        return 0;
+    }
+    int collect(mot_result* r) {
+        if (!on) return 0;
+        CK(cudaStreamSynchronize(st));
+        for (auto& x : ev) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, x.second.first, x.second.second));
+            if (r) {
+                r->kernel_ms[x.first] += ms;
+                r->kernel_launches[x.first] += 1;
+            }
+            cudaEventDestroy(x.second.first);
+            cudaEventDestroy(x.second.second);
+        }
+        ev.clear();
+        return 0;
+    }
+};
+
+int run_level(TreePlan& T, Level& L, int bump, cudaStream_t st, Timer& tm, long long& nl) {
+    cudaEvent_t e = nullptr;
+    if (T.path == MOT_PATH_NFFT) {
+        if (!L.src.empty()) {
+            RET(tm.begin(MOT_K_SPREAD, &e));
+            CK(launch_spread(T.d, L.d_src, (int)L.src.size(), L.grid_src, T.G, bump, st));
+            RET(tm.end(e));
+            int nf = 0;
+            RET(tm.begin(MOT_K_FFTCONV, &e));
+            CK(launch_fftconv(T.d, L.d_src, (int)L.src.size(), T.G, st, &nf));
+            RET(tm.end(e));
+            nl += 1 + nf;
+        }
+        RET(tm.begin(MOT_K_GATHER, &e));
+        CK(launch_gather(T.d, L.d_tgt, (int)L.tgt.size(), L.grid_tgt, T.G, st));
+        RET(tm.end(e));
+        nl += 1;
+    } else {
+        if (!L.src.empty()) {
+            RET(tm.begin(MOT_K_DENSE, &e));
+            CK(launch_dense(T.d, L.d_src, (int)L.src.size(), L.ntb, L.nsplit, T.G, bump, st));
+            RET(tm.end(e));
+            nl += 1;
+        }
+        RET(tm.begin(MOT_K_NODE, &e));
+        CK(launch_epi(T.d, L.d_tgt, (int)L.tgt.size(), L.grid_tgt, T.G, st));
+        RET(tm.end(e));
+        nl += 1;
+    }
+    return MOT_OK;
+}
+
+int run_iteration(TreePlan& T, cudaStream_t st, Timer& tm, long long& nl) {
+    for (size_t l = 0; l < T.fwd.size(); ++l) RET(run_level(T, T.fwd[l], l == 0 ? 1 : 0, st, tm, nl));
+    for (auto& L : T.bwd) RET(run_level(T, L, 0, st, tm, nl));
+    return MOT_OK;
+}
+
+int run_check(TreePlan& T, cudaStream_t st, Timer& tm, long long& nl) {
+    for (auto& L : T.chk) RET(run_level(T, L, 0, st, tm, nl));
+    return MOT_OK;
+}
+
+int run_iterations(TreePlan& T, int count, cudaStream_t st, Timer& tm, long long& nl, bool graphs) {
+    if (count <= 0) return MOT_OK;
+    if (graphs && !tm.on && st != nullptr) {
+        if (T.gexec == nullptr || T.graph_iters != count) {
+            if (T.gexec) {
+                cudaGraphExecDestroy(T.gexec);
+                T.gexec = nullptr;
+            }
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            long long dummy = 0;
+            int rc = MOT_OK;
+            for (int i = 0; i < count && rc == MOT_OK; ++i) rc = run_iteration(T, st, tm, dummy);
+            cudaError_t ce = cudaStreamEndCapture(st, &graph);
+            if (rc != MOT_OK) return rc;
+            CK(ce);
+            CK(cudaGraphInstantiate(&T.gexec, graph, 0));
+            cudaGraphDestroy(graph);
+            T.graph_iters = count;
+            T.launches_per_iter = dummy / count;
+        }
+        CK(cudaGraphLaunch(T.gexec, st));
+        nl += T.launches_per_iter * count;
+        return MOT_OK;
+    }
+    for (int i = 0; i < count; ++i) RET(run_iteration(T, st, tm, nl));
+    return MOT_OK;
+}
+
+struct Stats {
+    std::vector<char> buf;
+    const IterAcc* acc() const { return reinterpret_cast<const IterAcc*>(buf.data()); }
+    const double* node(int K) const { (void)K; return reinterpret_cast<const double*>(buf.data() + sizeof(IterAcc) * kRing); }
+    const VecScale* sc(int K) const {
+        return reinterpret_cast<const VecScale*>(buf.data() + sizeof(IterAcc) * kRing + sizeof(double) * 3 * K);
+    }
+    int err() const { return *reinterpret_cast<const int*>(buf.data() + buf.size() - 16); }
+};
+
+int read_stats(TreePlan& T, Stats& S, cudaStream_t st) {
+    S.buf.resize(T.stats_bytes);
+    CK(cudaMemcpyAsync(S.buf.data(), T.stats_begin, T.stats_bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return MOT_OK;
+}
+
+int tree_plan_setup(const mot_problem* P, const mot_options& o, TreePlan& T, void* ws, size_t ws_bytes,
+                    bool measure_only, size_t* need, cudaStream_t st) {
+    RET(tree_structure(P, T));
+    T.d = P->d;
+    T.eta = P->eta;
+    T.path = o.path;
+    T.o = o;
+    if (T.path != MOT_PATH_NFFT && T.path != MOT_PATH_DENSE) return MOT_EUNSUPPORTED;
+    // eta_e = eta / w_e
+    double emin = 1e300, emax = 0.0;
+    for (int k = 1; k < T.K; ++k) {
+        double e = T.eta / T.w[k];
+        emin = std::min(emin, e);
+        emax = std::max(emax, e);
+    }
+    if (measure_only) {
+        // the grid size depends on the data radius only through the choice of n; lay out for
+        // the largest grid the options allow
+        T.g = GridChoice();
+        if (o.n_grid > 0) {
+            T.g.n = o.n_grid;
+        } else {
+            T.g.n = max_grid(T.d);
+        }
+        T.g.M = T.g.n / 4;
+        Arena A;
+        A.measure = true;
+        layout_tree(A, T);
+        *need = A.off + 256;
+        return MOT_OK;
+    }
+    // lay out with the largest grid first (matches the workspace query), then choose
+    GridChoice gmax;
+    gmax.n = o.n_grid > 0 ? o.n_grid : max_grid(T.d);
+    gmax.M = gmax.n / 4;
+    T.g = gmax;
+    Arena A;
+    A.measure = false;
+    A.base = reinterpret_cast<char*>(ws);
+    A.cap = ws_bytes;
+    layout_tree(A, T);
+    if (A.off > ws_bytes) return MOT_ENOMEM;
+    // measure the data and choose the grid (<= the laid-out maximum)
+    std::vector<PrepSet> sets;
+    for (int k = 0; k < T.K; ++k) sets.push_back(prepset_of(T.sets[k], P->x[T.order[k]], P->mu[T.order[k]]));
+    GridChoice g;
+    RET(measure_and_choose(sets, T.d_sets, T.box_scratch, T.box_out, T.d, emin, emax, o, g, st));
+    if (g.n > gmax.n) g.n = gmax.n;
+    g.M = g.n / 4;
+    T.g = g;
+    // prep: normalise, bin, sort
+    CK(cudaMemsetAsync(T.stats_begin, 0, T.stats_bytes, st));
+    {
+        // rebuild the set descriptors for the chosen grid (tile counts depend on n)
+        std::vector<PrepSet> s2;
+        for (int k = 0; k < T.K; ++k) {
+            T.sets[k].maxsub = (T.n[k] + mot_sub_points(T.d) - 1) / mot_sub_points(T.d) + mot_ntiles(T.d, g.n);
+            s2.push_back(prepset_of(T.sets[k], P->x[T.order[k]], P->mu[T.order[k]]));
+        }
+        CK(cudaMemcpyAsync(T.d_sets, s2.data(), sizeof(PrepSet) * s2.size(), cudaMemcpyHostToDevice, st));
+        CK(launch_prep(T.d_sets, s2.data(), T.K, T.d, g.n, g.c, g.s, T.err, st));
+    }
+    // spectral multipliers per edge, grids zeroed
+    if (T.path == MOT_PATH_NFFT) {
+        CK(prepare_fftconv(T.d, g.n));
+        size_t gsz = 1;
+        for (int t = 0; t < T.d; ++t) gsz *= g.n;
+        for (int k = 1; k < T.K; ++k) {
+            double eta_n = (T.eta / T.w[k]) / (g.s * g.s);
+            RET(make_D_for(eta_n, g, T.d, o, T.dscr_a, T.dscr_b, T.D[k], st));
+            CK(cudaMemsetAsync(T.grid[k], 0, gsz * sizeof(float), st));
+        }
+    } else {
+        for (int k = 1; k < T.K; ++k) {
+            CK(cudaMemsetAsync(T.rawf[k], 0, sizeof(float) * T.n[k], st));
+            CK(cudaMemsetAsync(T.rawb[k], 0, sizeof(float) * T.n[T.parent[k]], st));
+            CK(cudaMemsetAsync(T.rawc[k], 0, sizeof(float) * T.n[k], st));
+        }
+    }
+    build_tasks(T);
+    RET(upload_tasks(T, st));
+    return MOT_OK;
+}
+
+int tree_solve(const mot_problem* P, const mot_options& o, void* ws, size_t ws_bytes, const double* const* u_warm,
+               mot_result* res, cudaStream_t st) {
+    TreePlan T;
+    RET(tree_plan_setup(P, o, T, ws, ws_bytes, false, nullptr, st));
+    Timer tm;
+    tm.on = o.timing != 0;
+    tm.st = st;
+    long long nl = 0;
+    const int K = T.K;
+    // initial scalings, iteration counter, accumulators
+    {
+        int minus1 = -1;
+        CK(cudaMemcpyAsync(T.iter, &minus1, sizeof(int), cudaMemcpyHostToDevice, st));
+        for (int k = 0; k < K; ++k) {
+            const double* uw = (u_warm && !T.free_[k]) ? u_warm[T.order[k]] : nullptr;
+            CK(launch_init_phi(T.phi[k], T.phi_sc(k), T.sets[k].perm, T.sets[k].mu_d, T.n[k], uw, T.eta,
+                               &T.acc[0].logphi, T.box_scratch, st));
+            nl += uw ? 2 : 1;
+        }
+    }
+    // initial beta sweep (Algorithm 2, steps 3-5)
+    for (auto& L : T.bwd) RET(run_level(T, L, 0, st, tm, nl));
+
+    const bool graphs = o.use_graphs > 0;
+    const bool want_viol = o.tol_viol >= 0.0;
+    int iters = 0, status = MOT_OK;
+    Stats S;
+    double viol = INFINITY, S_last = NAN, S_prev = NAN;
+    bool met = false;
+    while (true) {
+        int chunk = std::min(o.check_every, o.max_iter - iters);
+        if (chunk <= 0) break;
+        RET(run_iterations(T, chunk, st, tm, nl, graphs));
+        iters += chunk;
+        RET(run_check(T, st, tm, nl));
+        RET(read_stats(T, S, st));
+        RET(tm.collect(res));
+        if (S.err() & 1) return MOT_ENUMERIC;
+        if (S.err() & 2) return MOT_ENUMERIC;
+        viol = 0.0;
+        for (int k = 0; k < K; ++k)
+            if (!T.free_[k]) viol = std::max(viol, S.node(K)[3 * k]);
+        // S^(r) = eta (logphi^(r) - mass^(r)), r = iters-1 and iters-2 complete
+        auto Sval = [&](int r) { const IterAcc& a = S.acc()[r % kRing]; return T.eta * (a.logphi - a.mass); };
+        if (iters >= 1) S_last = Sval(iters - 1);
+        if (iters >= 2) S_prev = Sval(iters - 2);
+        if (!std::isfinite(viol)) return MOT_ENUMERIC;
+        if (iters >= o.min_iter) {
+            if (want_viol && viol <= o.tol_viol) { met = true; break; }
+            if (o.delta_S > 0.0 && iters >= 2 && std::fabs(S_last - S_prev) < o.delta_S) { met = true; break; }
+        }
+        if (iters >= o.max_iter) break;
+    }
+    if (!met && (want_viol || o.delta_S > 0.0)) status = MOT_ENOCONV;
+    // outputs
+    if (res) {
+        const double* node = S.node(K);
+        double mass = node[2];
+        double plogphi = 0.0;
+        for (int k = 0; k < K; ++k) plogphi += node[3 * k + 1];
+        const IterAcc& cur = S.acc()[iters % kRing];
+        res->violation = viol;
+        res->mass = mass;
+        res->cost_dual = T.eta * (cur.logphi - mass);
+        res->cost_primal = T.eta * (plogphi - mass);
+        res->S_last = S_last;
+        res->S_prev = S_prev;
+        res->iters = iters;
+        long long cl = 0;
+        const VecScale* scs = S.sc(K);
+        for (int i = 0; i < 4 * K; ++i) cl += scs[i].clamped;
+        res->clamped = cl;
+        res->scale = T.g.s;
+        res->eta_norm = T.eta / (T.g.s * T.g.s);
+        res->n_grid = T.path == MOT_PATH_NFFT ? T.g.n : 0;
+        res->M = T.path == MOT_PATH_NFFT ? T.g.M : 0;
+        if (res->u) {
+            for (int k = 0; k < K; ++k) {
+                if (!res->u[T.order[k]]) continue;
+                CK(launch_output(T.phi[k], T.phi_sc(k), T.sets[k].perm, T.n[k], T.eta, res->u[T.order[k]], st));
+                nl += 1;
+            }
+        }
+        res->launches = nl;
+        res->status = status;
+    }
+    CK(cudaStreamSynchronize(st));
+    if (T.gexec) cudaGraphExecDestroy(T.gexec);
+    return status;
+}
+
+}  // namespace
+
+// =============================================================================================
+// fast summation on its own
+// =============================================================================================
+namespace {
+
+struct FsPlan {
+    SetBufs src, tgt;
+    std::vector<float*> grid, hgrid, raw;
+    std::vector<float2*> spec;
+    float* D = nullptr;
+    float* a_sorted = nullptr;   // [nrhs][n_src]
+    float* b_sorted = nullptr;   // [nrhs][n_tgt]
+    PrepSet* d_sets = nullptr;
+    float* box_scratch = nullptr;
+    float* box_out = nullptr;
+    double* dscr_a = nullptr;
+    double* dscr_b = nullptr;
+    Task* d_tasks = nullptr;
+    int* err = nullptr;
+    int* iter = nullptr;
+    IterAcc* acc = nullptr;
+};
+
+void layout_fs(Arena& A, FsPlan& F, int d, int64_t ns, int64_t nt, int nrhs, int path, int ng) {
+    const int M = ng / 4;
+    layout_set(A, F.src, (int)ns, d, ng, false);
+    layout_set(A, F.tgt, (int)nt, d, ng, false);
+    size_t gsz = 1;
+    for (int t = 0; t < d; ++t) gsz *= ng;
+    F.grid.assign(nrhs, nullptr);
+    F.hgrid.assign(nrhs, nullptr);
+    F.spec.assign(nrhs, nullptr);
+    F.raw.assign(nrhs, nullptr);
+    for (int r = 0; r < nrhs; ++r) {
+        if (path == MOT_PATH_NFFT) {
+            F.grid[r] = A.take<float>(gsz);
+            F.hgrid[r] = A.take<float>(gsz);
+            if (d == 3) F.spec[r] = A.take<float2>((size_t)ng * (2 * M + 1) * (M + 1));
+        } else {
+            F.raw[r] = A.take<float>(nt);
+        }
+    }
+    if (path == MOT_PATH_NFFT) {
+        F.D = A.take<float>(D_floats(d, M));
+        size_t s = make_D_scratch_doubles(d, M);
+        F.dscr_a = A.take<double>(s);
+        F.dscr_b = A.take<double>(s);
+    }
+    F.a_sorted = A.take<float>((size_t)nrhs * ns);
+    F.b_sorted = A.take<float>((size_t)nrhs * nt);
+    F.d_sets = A.take<PrepSet>(2);
+    F.box_scratch = A.take<float>(8);
+    F.box_out = A.take<float>(8);
+    F.d_tasks = A.take<Task>(nrhs);
+    F.err = A.take<int>(4);
+    F.iter = F.err + 1;
+    F.acc = A.take<IterAcc>(2);
+}
+
+int fastsum_impl(int d, double eta, const float* x_src, int64_t n_src, const float* x_tgt, int64_t n_tgt,
+                 const float* alpha, int nrhs, float* beta, const mot_options& o, void* ws, size_t ws_bytes,
+                 double* scale_out, cudaStream_t st, bool measure, size_t* need) {
+    if (d < 1 || d > 3 || n_src < 1 || n_tgt < 1 || nrhs < 1 || nrhs > 65535) return MOT_EINVAL;
+    if (n_src > (1 << 26) || n_tgt > (1 << 26)) return MOT_EINVAL;
+    if (!(eta > 0.0) || !std::isfinite(eta)) return MOT_EINVAL;
+    if (o.path != MOT_PATH_NFFT && o.path != MOT_PATH_DENSE) return MOT_EUNSUPPORTED;
+    const int ngmax = o.n_grid > 0 ? o.n_grid : max_grid(d);
+    if (ngmax < 16 || ngmax > max_grid(d) || (ngmax & (ngmax - 1))) return MOT_EINVAL;
+    FsPlan F;
+    Arena A;
+    A.measure = measure;
+    A.base = reinterpret_cast<char*>(ws);
+    A.cap = ws_bytes;
+    layout_fs(A, F, d, n_src, n_tgt, nrhs, o.path, ngmax);
+    if (measure) {
+        *need = A.off + 256;
+        return MOT_OK;
+    }
+    if (!x_src || !x_tgt || !alpha || !beta || !ws) return MOT_EINVAL;
+    if (A.off > ws_bytes) return MOT_ENOMEM;
+    CK(cudaMemsetAsync(F.err, 0, sizeof(int) * 4, st));
+    std::vector<PrepSet> sets = {prepset_of(F.src, x_src, nullptr), prepset_of(F.tgt, x_tgt, nullptr)};
+    GridChoice g;
+    RET(measure_and_choose(sets, F.d_sets, F.box_scratch, F.box_out, d, eta, eta, o, g, st));
+    if (g.n > ngmax) {
+        g.n = ngmax;
+        g.M = g.n / 4;
+    }
+    if (scale_out) *scale_out = g.s;
+    F.src.maxsub = (F.src.n + mot_sub_points(d) - 1) / mot_sub_points(d) + mot_ntiles(d, g.n);
+    F.tgt.maxsub = (F.tgt.n + mot_sub_points(d) - 1) / mot_sub_points(d) + mot_ntiles(d, g.n);
+    sets = {prepset_of(F.src, x_src, nullptr), prepset_of(F.tgt, x_tgt, nullptr)};
+    CK(cudaMemcpyAsync(F.d_sets, sets.data(), sizeof(PrepSet) * 2, cudaMemcpyHostToDevice, st));
+    CK(launch_prep(F.d_sets, sets.data(), 2, d, g.n, g.c, g.s, F.err, st));
+    const double eta_n = eta / (g.s * g.s);
+    size_t gsz = 1;
+    for (int t = 0; t < d; ++t) gsz *= g.n;
+    if (o.path == MOT_PATH_NFFT) {
+        CK(prepare_fftconv(d, g.n));
+        RET(make_D_for(eta_n, g, d, o, F.dscr_a, F.dscr_b, F.D, st));
+        for (int r = 0; r < nrhs; ++r) CK(cudaMemsetAsync(F.grid[r], 0, gsz * sizeof(float), st));
+    } else {
+        for (int r = 0; r < nrhs; ++r) CK(cudaMemsetAsync(F.raw[r], 0, sizeof(float) * n_tgt, st));
+    }
+    for (int r = 0; r < nrhs; ++r)
+        CK(launch_permute_in(alpha + (size_t)r * n_src, F.src.perm, (int)n_src, F.a_sorted + (size_t)r * n_src, st));
+    std::vector<Task> tasks(nrhs);
+    for (int r = 0; r < nrhs; ++r) {
+        Task t = blank_task();
+        t.src = pointset_of(F.src);
+        t.alpha = F.a_sorted + (size_t)r * n_src;
+        t.grid = F.grid[r];
+        t.hgrid = F.hgrid[r];
+        t.spec = F.spec[r];
+        t.D = F.D;
+        t.raw = F.raw[r];
+        t.eta_u = (float)(eta_n * (double)g.n * (double)g.n);
+        t.tgt = pointset_of(F.tgt);
+        t.mode = EPI_RAW;
+        t.out = F.b_sorted + (size_t)r * n_tgt;
+        tasks[r] = t;
+    }
+    CK(cudaMemcpyAsync(F.d_tasks, tasks.data(), sizeof(Task) * nrhs, cudaMemcpyHostToDevice, st));
+    Globals G;
+    G.iter = F.iter;
+    G.acc = F.acc;
+    G.R = 2;
+    G.floor_ = 0.f;
+    G.n_grid = g.n;
+    G.M = g.M;
+    G.fac = nullptr;
+    if (o.path == MOT_PATH_NFFT) {
+        int gx = std::min(F.src.maxsub, 1024), gt = std::min(F.tgt.maxsub, 1024);
+        CK(launch_spread(d, F.d_tasks, nrhs, gx, G, 0, st));
+        CK(launch_fftconv(d, F.d_tasks, nrhs, G, st, nullptr));
+        CK(launch_gather(d, F.d_tasks, nrhs, gt, G, st));
+    } else {
+        int ntb = (int)((n_tgt + 511) / 512);
+        int split = std::max(1, std::min(64, 4 * 152 / std::max(1, ntb * nrhs)));
+        CK(launch_dense(d, F.d_tasks, nrhs, ntb, split, G, 0, st));
+        CK(launch_epi(d, F.d_tasks, nrhs, std::min((int)((n_tgt + 255) / 256), 1024), G, st));
+    }
+    for (int r = 0; r < nrhs; ++r)
+        CK(launch_permute_out(F.b_sorted + (size_t)r * n_tgt, F.tgt.perm, (int)n_tgt, beta + (size_t)r * n_tgt, st));
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, F.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (err) return MOT_ENUMERIC;
+    return MOT_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
+// C ABI
+// =============================================================================================
+extern "C" {
+
+void mot_options_default(mot_options* o) {
+    if (!o) return;
+    fill_defaults(*o, nullptr);
+    o->n_grid = 0;
+}
+
+const char* mot_strerror(int s) {
+    switch (s) {
+    case MOT_OK: return "ok";
+    case MOT_EINVAL: return "invalid argument";
+    case MOT_ENOTTREE: return "edges do not form a tree";
+    case MOT_ENOMEM: return "workspace too small";
+    case MOT_ENUMERIC: return "non-finite input or negative weight";
+    case MOT_ENOCONV: return "stop test not met within max_iter";
+    case MOT_ETIMEOUT: return "bounded device wait timed out";
+    case MOT_ECUDA: return "CUDA runtime error";
+    case MOT_EUNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+    }
+}
+
+const char* mot_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+int mot_abi_version(void) { return MOT_ABI_VERSION; }
+
+int mot_workspace_bytes(const mot_problem* prob, const mot_options* opt, size_t* bytes) {
+    if (!bytes) return MOT_EINVAL;
+    RET(validate_problem(prob));
+    mot_options o;
+    fill_defaults(o, opt);
+    if (o.n_grid && (o.n_grid < 16 || o.n_grid > max_grid(prob->d) || (o.n_grid & (o.n_grid - 1)))) return MOT_EINVAL;
+    if (o.m != 4) return MOT_EUNSUPPORTED;
+    if (prob->topology != MOT_TREE) return MOT_EUNSUPPORTED;
+    TreePlan T;
+    return tree_plan_setup(prob, o, T, nullptr, 0, true, bytes, nullptr);
+}
+
+int mot_solve(const mot_problem* prob, const mot_options* opt, void* ws, size_t ws_bytes,
+              const double* const* u_warm, mot_result* res, void* stream) {
+    g_cuda_err.clear();
+    RET(validate_problem(prob));
+    mot_options o;
+    fill_defaults(o, opt);
+    if (o.n_grid && (o.n_grid < 16 || o.n_grid > max_grid(prob->d) || (o.n_grid & (o.n_grid - 1)))) return MOT_EINVAL;
+    if (o.m != 4) return MOT_EUNSUPPORTED;
+    if (!ws) return MOT_EINVAL;
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return MOT_EINVAL;
+    if (res) {
+        double* const* u = res->u;
+        std::memset(res, 0, sizeof(*res));
+        *const_cast<double* const**>(&res->u) = u;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (prob->topology == MOT_TREE) {
+        int rc = tree_solve(prob, o, ws, ws_bytes, u_warm, res, st);
+        if (res) res->status = rc;
+        return rc;
+    }
+    return MOT_EUNSUPPORTED;
+}
+
+int mot_fastsum_workspace_bytes(int d, int64_t n_src, int64_t n_tgt, int nrhs, const mot_options* opt,
+                                size_t* bytes) {
+    if (!bytes) return MOT_EINVAL;
+    mot_options o;
+    fill_defaults(o, opt);
+    return fastsum_impl(d, 1.0, nullptr, n_src, nullptr, n_tgt, nullptr, nrhs, nullptr, o, nullptr, 0, nullptr,
+                        nullptr, true, bytes);
+}
+
+int mot_fastsum(int d, double eta, const float* x_src, int64_t n_src, const float* x_tgt, int64_t n_tgt,
+                const float* alpha, int nrhs, float* beta, const mot_options* opt, void* ws, size_t ws_bytes,
+                double* scale_out, void* stream) {
+    g_cuda_err.clear();
+    mot_options o;
+    fill_defaults(o, opt);
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return MOT_EINVAL;
+    return fastsum_impl(d, eta, x_src, n_src, x_tgt, n_tgt, alpha, nrhs, beta, o, ws, ws_bytes, scale_out,
+                        reinterpret_cast<cudaStream_t>(stream), false, nullptr);
+}
+
+}  // extern "C"

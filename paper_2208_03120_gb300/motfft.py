@@ -1,0 +1,279 @@
+"""Thin ctypes binding of libmotfft (include/motfft.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module turns torch tensors into
+the pointers and sizes of the C ABI, allocates the caller-owned workspace and
+outputs with torch, and raises :class:`MotError` for a non-zero status.  There is
+no fallback: if ``libmotfft.so`` is missing or cannot be loaded, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmotfft.so")
+
+MOT_OK, MOT_EINVAL, MOT_ENOTTREE, MOT_ENOMEM, MOT_ENUMERIC, MOT_ENOCONV, MOT_ETIMEOUT, MOT_ECUDA, MOT_EUNSUPPORTED = range(9)
+MOT_TREE, MOT_CIRCLE = 0, 1
+MOT_PATH_NFFT, MOT_PATH_DENSE, MOT_PATH_DENSE_BF16X3 = 0, 1, 2
+MOT_NKCLASS = 8
+KERNEL_CLASSES = ["spread", "fftconv", "gather", "dense", "node", "setup", "circle", "spare"]
+
+
+class MotError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({strerror(status)}){' ' + detail if detail else ''}")
+
+
+class Problem(C.Structure):
+    _fields_ = [
+        ("K", C.c_int), ("d", C.c_int),
+        ("n", C.POINTER(C.c_int64)),
+        ("x", C.POINTER(C.c_void_p)),
+        ("mu", C.POINTER(C.c_void_p)),
+        ("topology", C.c_int),
+        ("edges", C.POINTER(C.c_int)),
+        ("edge_w", C.POINTER(C.c_double)),
+        ("free_nodes", C.POINTER(C.c_ubyte)),
+        ("eta", C.c_double),
+        ("root", C.c_int),
+    ]
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("path", C.c_int), ("max_iter", C.c_int),
+        ("tol_viol", C.c_double), ("delta_S", C.c_double),
+        ("check_every", C.c_int), ("min_iter", C.c_int),
+        ("n_grid", C.c_int), ("m", C.c_int), ("p", C.c_int),
+        ("eps_B", C.c_double),
+        ("use_graphs", C.c_int), ("timing", C.c_int),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("u", C.POINTER(C.c_void_p)),
+        ("violation", C.c_double), ("cost_dual", C.c_double), ("cost_primal", C.c_double),
+        ("mass", C.c_double), ("S_last", C.c_double), ("S_prev", C.c_double),
+        ("iters", C.c_int), ("status", C.c_int),
+        ("clamped", C.c_longlong), ("launches", C.c_longlong),
+        ("scale", C.c_double), ("eta_norm", C.c_double),
+        ("n_grid", C.c_int), ("M", C.c_int),
+        ("kernel_ms", C.c_double * MOT_NKCLASS),
+        ("kernel_launches", C.c_longlong * MOT_NKCLASS),
+    ]
+
+
+_lib_handle = None
+
+
+def lib() -> C.CDLL:
+    """Load libmotfft.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} not built; run __graft_entry__.build() first")
+        h = C.CDLL(LIB_PATH)
+        h.mot_strerror.restype = C.c_char_p
+        h.mot_strerror.argtypes = [C.c_int]
+        h.mot_last_cuda_error.restype = C.c_char_p
+        h.mot_abi_version.restype = C.c_int
+        h.mot_options_default.argtypes = [C.POINTER(Options)]
+        h.mot_workspace_bytes.argtypes = [C.POINTER(Problem), C.POINTER(Options), C.POINTER(C.c_size_t)]
+        h.mot_solve.argtypes = [C.POINTER(Problem), C.POINTER(Options), C.c_void_p, C.c_size_t,
+                                C.POINTER(C.c_void_p), C.POINTER(Result), C.c_void_p]
+        h.mot_fastsum_workspace_bytes.argtypes = [C.c_int, C.c_int64, C.c_int64, C.c_int, C.POINTER(Options),
+                                                  C.POINTER(C.c_size_t)]
+        h.mot_fastsum.argtypes = [C.c_int, C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                                  C.c_int, C.c_void_p, C.POINTER(Options), C.c_void_p, C.c_size_t,
+                                  C.POINTER(C.c_double), C.c_void_p]
+        _lib_handle = h
+    return _lib_handle
+
+
+def strerror(status: int) -> str:
+    try:
+        return lib().mot_strerror(status).decode()
+    except Exception:  # noqa: BLE001 - message only
+        return "?"
+
+
+def _check(status: int, where: str, allow=(MOT_OK,)):
+    if status not in allow:
+        detail = lib().mot_last_cuda_error().decode() if status == MOT_ECUDA else ""
+        raise MotError(status, where, detail)
+    return status
+
+
+def options(**kw) -> Options:
+    o = Options()
+    lib().mot_options_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _check_tensor(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+# ----------------------------------------------------------------------------------------
+# kernel matrix-vector product
+# ----------------------------------------------------------------------------------------
+
+def mot_fastsum_workspace_bytes(d: int, n_src: int, n_tgt: int, nrhs: int = 1, opt: Optional[Options] = None) -> int:
+    nb = C.c_size_t(0)
+    _check(lib().mot_fastsum_workspace_bytes(d, n_src, n_tgt, nrhs, C.byref(opt or options()), C.byref(nb)),
+           "mot_fastsum_workspace_bytes")
+    return nb.value
+
+
+def mot_fastsum(x_src, x_tgt, alpha, eta: float, opt: Optional[Options] = None, workspace=None, stream=None,
+                out=None):
+    """beta = K alpha with K_ij = exp(-||x_tgt[i] - x_src[j]||^2 / eta) (Eq. fastsum-sum).
+
+    x_src: (n_src, d) float32 CUDA; x_tgt: (n_tgt, d); alpha: (n_src,) or (nrhs, n_src) float32.
+    Returns (beta, scale) with beta shaped like alpha over the targets.
+    """
+    import torch
+    opt = opt or options()
+    _check_tensor(x_src, torch.float32, "x_src")
+    _check_tensor(x_tgt, torch.float32, "x_tgt")
+    _check_tensor(alpha, torch.float32, "alpha")
+    d = x_src.shape[1]
+    if x_tgt.shape[1] != d:
+        raise ValueError("dimension mismatch")
+    a2 = alpha.reshape(-1, x_src.shape[0])
+    nrhs = a2.shape[0]
+    n_src, n_tgt = x_src.shape[0], x_tgt.shape[0]
+    if workspace is None:
+        nb = mot_fastsum_workspace_bytes(d, n_src, n_tgt, nrhs, opt)
+        workspace = torch.empty(nb, dtype=torch.uint8, device=x_src.device)
+    beta = out if out is not None else torch.empty((nrhs, n_tgt), dtype=torch.float32, device=x_src.device)
+    scale = C.c_double(0.0)
+    _check(lib().mot_fastsum(d, float(eta), x_src.data_ptr(), n_src, x_tgt.data_ptr(), n_tgt, a2.data_ptr(), nrhs,
+                             beta.data_ptr(), C.byref(opt), workspace.data_ptr(), workspace.numel(),
+                             C.byref(scale), _stream_ptr(stream)), "mot_fastsum")
+    if alpha.dim() == 1:
+        beta = beta.reshape(n_tgt)
+    return beta, scale.value
+
+
+# ----------------------------------------------------------------------------------------
+# Sinkhorn
+# ----------------------------------------------------------------------------------------
+
+class _ProblemHolder:
+    """Keeps the ctypes arrays referenced by a Problem alive."""
+
+    def __init__(self, x: Sequence, mu: Sequence, eta: float, topology: int, edges=None, edge_w=None,
+                 free_nodes=None, root: int = 0):
+        import torch
+        K = len(x)
+        if len(mu) != K:
+            raise ValueError("x and mu lengths differ")
+        for k in range(K):
+            _check_tensor(x[k], torch.float32, f"x[{k}]")
+            _check_tensor(mu[k], torch.float64, f"mu[{k}]")
+        self.x = list(x)
+        self.mu = list(mu)
+        self.n_arr = (C.c_int64 * K)(*[int(t.shape[0]) for t in x])
+        self.x_arr = (C.c_void_p * K)(*[t.data_ptr() for t in x])
+        self.mu_arr = (C.c_void_p * K)(*[t.data_ptr() for t in mu])
+        p = Problem()
+        p.K = K
+        p.d = int(x[0].shape[1])
+        p.n = self.n_arr
+        p.x = self.x_arr
+        p.mu = self.mu_arr
+        p.topology = topology
+        if edges is not None:
+            flat = [int(v) for e in edges for v in e]
+            self.e_arr = (C.c_int * len(flat))(*flat)
+            p.edges = self.e_arr
+        if edge_w is not None:
+            self.w_arr = (C.c_double * len(edge_w))(*[float(v) for v in edge_w])
+            p.edge_w = self.w_arr
+        if free_nodes is not None:
+            self.f_arr = (C.c_ubyte * K)(*[1 if v else 0 for v in free_nodes])
+            p.free_nodes = self.f_arr
+        p.eta = float(eta)
+        p.root = int(root)
+        self.p = p
+
+
+def mot_workspace_bytes(x, mu, eta, topology=MOT_TREE, edges=None, edge_w=None, free_nodes=None, root=0,
+                        opt: Optional[Options] = None) -> int:
+    h = _ProblemHolder(x, mu, eta, topology, edges, edge_w, free_nodes, root)
+    nb = C.c_size_t(0)
+    _check(lib().mot_workspace_bytes(C.byref(h.p), C.byref(opt or options()), C.byref(nb)), "mot_workspace_bytes")
+    return nb.value
+
+
+class SolveOutput:
+    def __init__(self, u: List, res: Result):
+        self.u = u
+        self.violation = res.violation
+        self.cost_dual = res.cost_dual
+        self.cost_primal = res.cost_primal
+        self.mass = res.mass
+        self.S_last = res.S_last
+        self.S_prev = res.S_prev
+        self.iters = res.iters
+        self.status = res.status
+        self.clamped = res.clamped
+        self.launches = res.launches
+        self.scale = res.scale
+        self.eta_norm = res.eta_norm
+        self.n_grid = res.n_grid
+        self.M = res.M
+        self.kernel_ms = {KERNEL_CLASSES[i]: res.kernel_ms[i] for i in range(MOT_NKCLASS)}
+        self.kernel_launches = {KERNEL_CLASSES[i]: res.kernel_launches[i] for i in range(MOT_NKCLASS)}
+
+
+def mot_solve(x, mu, eta, topology=MOT_TREE, edges=None, edge_w=None, free_nodes=None, root=0,
+              opt: Optional[Options] = None, u_warm=None, workspace=None, stream=None, u_out=None,
+              allow_noconv: bool = True) -> SolveOutput:
+    """Sinkhorn for a tree (Algorithm 2) or circle (Algorithm 3); returns u^k = eta log phi^k (FP64)."""
+    import torch
+    opt = opt or options()
+    h = _ProblemHolder(x, mu, eta, topology, edges, edge_w, free_nodes, root)
+    dev = x[0].device
+    if workspace is None:
+        nb = C.c_size_t(0)
+        _check(lib().mot_workspace_bytes(C.byref(h.p), C.byref(opt), C.byref(nb)), "mot_workspace_bytes")
+        workspace = torch.empty(nb.value, dtype=torch.uint8, device=dev)
+    K = len(x)
+    u = u_out if u_out is not None else [torch.empty(int(t.shape[0]), dtype=torch.float64, device=dev) for t in x]
+    u_arr = (C.c_void_p * K)(*[t.data_ptr() for t in u])
+    res = Result()
+    res.u = u_arr
+    warm = None
+    if u_warm is not None:
+        warm = (C.c_void_p * K)(*[t.data_ptr() for t in u_warm])
+    allow = (MOT_OK, MOT_ENOCONV) if allow_noconv else (MOT_OK,)
+    _check(lib().mot_solve(C.byref(h.p), C.byref(opt), workspace.data_ptr(), workspace.numel(), warm, C.byref(res),
+                           _stream_ptr(stream)), "mot_solve", allow)
+    return SolveOutput(u, res)
+
+
+# C-ABI entry points declared in include/motfft.h (checked by the test-suite).
+EXPORTED = ["mot_options_default", "mot_strerror", "mot_last_cuda_error", "mot_abi_version",
+            "mot_workspace_bytes", "mot_solve", "mot_fastsum_workspace_bytes", "mot_fastsum"]
