@@ -42,7 +42,9 @@ __global__ void __launch_bounds__(DENSE_TPB) k_dense(const Task* __restrict__ ta
     const float c = -1.4426950408889634f / T.eta_u;
     const int chunk = (Ns + nsplit - 1) / nsplit;
     const int s0 = sp * chunk, s1 = min(Ns, s0 + chunk);
-    float acc0 = 0.f, acc1 = 0.f;
+    // Two-level summation: FP32 partial sums over 16 sources, added to a compensated
+    // (Kahan) FP32 accumulator, so the rounding error does not grow with the source count.
+    float acc0 = 0.f, acc1 = 0.f, cmp0 = 0.f, cmp1 = 0.f;
     for (int base = s0; base < s1; base += DENSE_CHUNK) {
         const int cnt = min(DENSE_CHUNK, s1 - base);
         for (int q = threadIdx.x; q < cnt; q += DENSE_TPB) {
@@ -52,19 +54,29 @@ __global__ void __launch_bounds__(DENSE_TPB) k_dense(const Task* __restrict__ ta
             s_v[q] = T.alpha ? T.alpha[j] : eval_prod(fc, j);
         }
         __syncthreads();
+        for (int q0 = 0; q0 < cnt; q0 += 16) {
+            const int qe = min(cnt, q0 + 16);
+            float p0 = 0.f, p1 = 0.f;
 #pragma unroll 4
-        for (int q = 0; q < cnt; ++q) {
-            float da = 0.f, db = 0.f;
+            for (int q = q0; q < qe; ++q) {
+                float da = 0.f, db = 0.f;
 #pragma unroll
-            for (int t = 0; t < D; ++t) {
-                const float y = s_u[t][q];
-                const float ea = xa[t] - y, eb = xb[t] - y;
-                da = fmaf(ea, ea, da);
-                db = fmaf(eb, eb, db);
+                for (int t = 0; t < D; ++t) {
+                    const float y = s_u[t][q];
+                    const float ea = xa[t] - y, eb = xb[t] - y;
+                    da = fmaf(ea, ea, da);
+                    db = fmaf(eb, eb, db);
+                }
+                const float v = s_v[q];
+                p0 = fmaf(v, ex2_approx(c * da), p0);
+                p1 = fmaf(v, ex2_approx(c * db), p1);
             }
-            const float v = s_v[q];
-            acc0 = fmaf(v, ex2_approx(c * da), acc0);
-            acc1 = fmaf(v, ex2_approx(c * db), acc1);
+            float y0 = p0 - cmp0, t0 = acc0 + y0;
+            cmp0 = (t0 - acc0) - y0;
+            acc0 = t0;
+            float y1 = p1 - cmp1, t1 = acc1 + y1;
+            cmp1 = (t1 - acc1) - y1;
+            acc1 = t1;
         }
         __syncthreads();
     }

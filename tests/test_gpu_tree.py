@@ -92,8 +92,8 @@ def test_random_trees_to_tolerance(M, path, shape, d, n, eta):
     rng = np.random.default_rng(zlib.crc32(f"{shape}-{d}-{n}".encode()))
     prob = W.random_problem(rng, W.TREE, 6, d, n, eta, shape=shape)
     prob.root = int(rng.integers(0, 6))
-    out, u = gpu_solve(M, prob, path=path, tol_viol=1e-7, max_iter=3000)
-    assert out.status == 0
+    out, u = gpu_solve(M, prob, path=path, tol_viol=1e-6, max_iter=3000)
+    assert out.status == 0, (out.iters, out.violation)
     u_or, _ = oracle_solve(prob, 3000 if eta < 0.05 else 1500)
     rep_g, rep_o = exact_report(prob, u), exact_report(prob, u_or)
     assert_parity(prob, u, u_or, rep_g, rep_o, out)
@@ -102,8 +102,8 @@ def test_random_trees_to_tolerance(M, path, shape, d, n, eta):
 def test_star_workload_reduced(M):
     """Star tree (centre + 8 leaves), d = 3, uniform ball, eta = 0.02, N = 1000 per marginal."""
     prob = W.star9_d3(n=1000)
-    out, u = gpu_solve(M, prob, tol_viol=1e-7, max_iter=3000)
-    assert out.status == 0
+    out, u = gpu_solve(M, prob, tol_viol=1e-6, max_iter=3000)
+    assert out.status == 0, (out.iters, out.violation)
     u_or, _ = oracle_solve(prob, 1000)
     rep_g, rep_o = exact_report(prob, u), exact_report(prob, u_or)
     assert_parity(prob, u, u_or, rep_g, rep_o, out)
@@ -130,7 +130,7 @@ def test_star_workload_full_size_paths_agree(M):
     prob = W.star9_d3()
     o1, u1 = gpu_solve(M, prob, tol_viol=1e-6, max_iter=3000)
     o2, u2 = gpu_solve(M, prob, path=1, tol_viol=1e-6, max_iter=3000)
-    assert o1.status == 0 and o2.status == 0
+    assert o1.status == 0 and o2.status == 0, (o1.iters, o1.violation, o2.iters, o2.violation)
     assert abs(o1.cost_dual - o2.cost_dual) <= REL * abs(o2.cost_dual)
     a, b = OS.gauge_fix(u1, prob.mu), OS.gauge_fix(u2, prob.mu)
     scale = max(float(np.max(np.abs(v))) for v in b)
@@ -143,11 +143,12 @@ def test_warm_start_resumes(M):
     import torch
     rng = np.random.default_rng(77)
     prob = W.random_problem(rng, W.TREE, 5, 2, 700, 0.03, shape="tree-random")
-    out, u = gpu_solve(M, prob, tol_viol=1e-7, max_iter=3000)
+    out, u = gpu_solve(M, prob, tol_viol=1e-6, max_iter=3000)
+    assert out.status == 0, (out.iters, out.violation)
     x, mu = problem_tensors(prob)
     warm = [torch.from_numpy(a).cuda() for a in u]
-    out2 = M.mot_solve(x, mu, prob.eta, M.MOT_TREE, edges=prob.edges, opt=M.options(tol_viol=1e-7), u_warm=warm)
-    assert out2.iters <= 10
+    out2 = M.mot_solve(x, mu, prob.eta, M.MOT_TREE, edges=prob.edges, opt=M.options(tol_viol=1e-6), u_warm=warm)
+    assert out2.iters <= 10, (out2.iters, out2.violation)
     u2 = [t.cpu().numpy() for t in out2.u]
     a, b = OS.gauge_fix(u, prob.mu), OS.gauge_fix(u2, prob.mu)
     for va, vb in zip(a, b):
