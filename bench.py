@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense comparison (profiling runs)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["path10_d2", "star9_d3", "path3_d1"],
+                    help="profiling runs only: the reported line is defined on path10_d2")
+    ap.add_argument("--n", type=int, default=0, help="profiling runs only: points per marginal")
+    ap.add_argument("--max-iter", type=int, default=5000, help="profiling runs only: iteration cap")
     return ap.parse_args()
 
 
@@ -224,11 +228,12 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build.build()
-    prob = W.path10_d2()
+    prob = W.WORKLOADS[args.workload](n=args.n) if args.n else W.WORKLOADS[args.workload]()
     x = [torch.from_numpy(a).to(dev) for a in prob.x]
     mu = [torch.from_numpy(m).to(dev) for m in prob.mu]
     stream = torch.cuda.Stream(device=dev)
-    opt = M.options(path=M.MOT_PATH_NFFT, tol_viol=TOL, max_iter=5000)
+    tol = TOL if args.max_iter >= 5000 else -1.0
+    opt = M.options(path=M.MOT_PATH_NFFT, tol_viol=tol, max_iter=args.max_iter)
     ws = torch.empty(M.mot_workspace_bytes(x, mu, prob.eta, M.MOT_TREE, edges=prob.edges, opt=opt),
                      dtype=torch.uint8, device=dev)
     u = [torch.empty(n, dtype=torch.float64, device=dev) for n in prob.n]
@@ -264,7 +269,7 @@ def main():
         times.append(e0.elapsed_time(e1) / 1e3)
         iters += out.iters
         launches += out.launches
-        if out.status != 0:
+        if out.status != 0 and tol > 0:
             raise SystemExit(f"solve did not converge: status {out.status}, violation {out.violation}")
     torch.cuda.synchronize()
     barrier()
@@ -282,7 +287,7 @@ def main():
     last = out
 
     # ---- per-kernel durations (events around each launch on the launching stream) -------
-    topt = M.options(path=M.MOT_PATH_NFFT, tol_viol=TOL, max_iter=5000, timing=1)
+    topt = M.options(path=M.MOT_PATH_NFFT, tol_viol=tol, max_iter=args.max_iter, timing=1)
     kms = {k: 0.0 for k in M.KERNEL_CLASSES}
     kls = {k: 0 for k in M.KERNEL_CLASSES}
     for _ in range(max(1, min(args.steps, 3))):
@@ -309,7 +314,7 @@ def main():
     # ---- dense comparison on the same workload -------------------------------------------
     dense = None
     if not args.no_dense:
-        dopt = M.options(path=M.MOT_PATH_DENSE, tol_viol=TOL, max_iter=5000)
+        dopt = M.options(path=M.MOT_PATH_DENSE, tol_viol=tol, max_iter=args.max_iter)
         dws = torch.empty(M.mot_workspace_bytes(x, mu, prob.eta, M.MOT_TREE, edges=prob.edges, opt=dopt),
                           dtype=torch.uint8, device=dev)
         dt, di = 0.0, 0
