@@ -168,6 +168,25 @@ int mot_fastsum(int d, double eta, const float* x_src, int64_t n_src, const floa
                 const mot_options* opt, void* ws, size_t ws_bytes, double* scale_out,
                 void* stream);
 
+/*
+ * Allocation-free variant of mot_fastsum (the paper has no counterpart: this serves callers
+ * that cannot allocate GPU memory or pass a workspace, e.g. code that must not allocate while
+ * a CUDA graph is being captured, or plug-ins whose host application owns all device memory).
+ * Same arguments and result as mot_fastsum, without ws / ws_bytes: the scratch is a static
+ * device array of MOT_STATIC_SCRATCH_BYTES per GPU, held from library load until exit.
+ *   - A request whose mot_fastsum_workspace_bytes exceeds MOT_STATIC_SCRATCH_BYTES returns
+ *     MOT_ENOMEM before any GPU work (pass opt->n_grid = 64 for large d = 3 problems).
+ *   - The first call on a device (with that device current) looks up the array's address;
+ *     make it before any stream capture.
+ *   - All calls on a device share the array: calls that overlap on the GPU race and must be
+ *     serialised by the caller.  What must start at zero is cleared by every call.
+ *   - Calls no cudaMalloc / cudaFree or any allocating routine.
+ */
+#define MOT_STATIC_SCRATCH_BYTES (32u << 20)
+int mot_fastsum_static(int d, double eta, const float* x_src, int64_t n_src, const float* x_tgt,
+                       int64_t n_tgt, const float* alpha, int nrhs, float* beta,
+                       const mot_options* opt, double* scale_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,6 +90,9 @@ def lib() -> C.CDLL:
         h.mot_fastsum.argtypes = [C.c_int, C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                                   C.c_int, C.c_void_p, C.POINTER(Options), C.c_void_p, C.c_size_t,
                                   C.POINTER(C.c_double), C.c_void_p]
+        h.mot_fastsum_static.argtypes = [C.c_int, C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                         C.c_void_p, C.c_int, C.c_void_p, C.POINTER(Options),
+                                         C.POINTER(C.c_double), C.c_void_p]
         _lib_handle = h
     return _lib_handle
 
@@ -173,6 +176,32 @@ def mot_fastsum(x_src, x_tgt, alpha, eta: float, opt: Optional[Options] = None, 
                              C.byref(scale), _stream_ptr(stream)), "mot_fastsum")
     if alpha.dim() == 1:
         beta = beta.reshape(n_tgt)
+    return beta, scale.value
+
+
+MOT_STATIC_SCRATCH_BYTES = 32 << 20
+
+
+def mot_fastsum_static(x_src, x_tgt, alpha, eta: float, opt: Optional[Options] = None, stream=None, out=None):
+    """mot_fastsum without a workspace: for callers that cannot allocate GPU memory (the
+    library uses its own static device scratch of MOT_STATIC_SCRATCH_BYTES; calls that
+    overlap on the GPU must be serialised).  Only ``out`` (optional) is allocated here."""
+    import torch
+    opt = opt or options()
+    _check_tensor(x_src, torch.float32, "x_src")
+    _check_tensor(x_tgt, torch.float32, "x_tgt")
+    _check_tensor(alpha, torch.float32, "alpha")
+    d = x_src.shape[1]
+    a2 = alpha.reshape(-1, x_src.shape[0])
+    nrhs = a2.shape[0]
+    beta = out if out is not None else torch.empty((nrhs, x_tgt.shape[0]), dtype=torch.float32,
+                                                   device=x_src.device)
+    scale = C.c_double(0.0)
+    _check(lib().mot_fastsum_static(d, float(eta), x_src.data_ptr(), x_src.shape[0], x_tgt.data_ptr(),
+                                    x_tgt.shape[0], a2.data_ptr(), nrhs, beta.data_ptr(), C.byref(opt),
+                                    C.byref(scale), _stream_ptr(stream)), "mot_fastsum_static")
+    if alpha.dim() == 1:
+        beta = beta.reshape(x_tgt.shape[0])
     return beta, scale.value
 
 
@@ -276,4 +305,5 @@ def mot_solve(x, mu, eta, topology=MOT_TREE, edges=None, edge_w=None, free_nodes
 
 # C-ABI entry points declared in include/motfft.h (checked by the test-suite).
 EXPORTED = ["mot_options_default", "mot_strerror", "mot_last_cuda_error", "mot_abi_version",
-            "mot_workspace_bytes", "mot_solve", "mot_fastsum_workspace_bytes", "mot_fastsum"]
+            "mot_workspace_bytes", "mot_solve", "mot_fastsum_workspace_bytes", "mot_fastsum",
+            "mot_fastsum_static"]
