@@ -118,20 +118,6 @@ __device__ __forceinline__ double factor_L(const Factor& f) {
     return f.inv ? -L : L;
 }
 
-// Kaiser-Bessel window normalised to 1 at 0, as a function of the distance delta (grid units):
-//   psi(delta) = (a/r) sinh(b r) / sinh(a b),  r = sqrt(a^2 - delta^2),  |delta| <= a.
-__device__ __forceinline__ float kb_window(float delta) {
-    const float a = (float)(MOT_WHALF + 1);
-    const float b = 4.71238898038469f;           // pi * (2 - 1/2)
-    float t = a * a - delta * delta;
-    if (t <= 0.f) return 0.f;
-    float r = sqrtf(t);
-    float e = expf(b * (r - a));                 // e^{b r} / e^{a b}
-    float br2 = 2.f * b * r;
-    float f = (br2 < 1e-3f) ? (2.f * b * (1.f - b * r)) : (1.f - expf(-br2)) / r;
-    return a * e * f;                            // (1 - e^{-2ab}) ~ 1 - 3e-21 omitted
-}
-
 __device__ __forceinline__ void atomic_max_pos(unsigned int* addr, float v) {
     // valid for v >= 0 (FP32 order equals unsigned order of the bits)
     atomicMax(addr, __float_as_uint(v));

@@ -21,14 +21,14 @@ constexpr int DENSE_CHUNK = 1024;          // sources staged per round
 
 template <int D>
 __global__ void __launch_bounds__(DENSE_TPB) k_dense(const Task* __restrict__ tasks, Globals G, int ntb,
-                                                     int nsplit, int bump_iter) {
+                                                     int nsplit) {
     __shared__ Task T;
     __shared__ FacCache fc;
     __shared__ float s_u[D][DENSE_CHUNK];
     __shared__ float s_v[DENSE_CHUNK];
     if (threadIdx.x == 0) T = tasks[blockIdx.y];
     __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) task_resets(T, G, bump_iter && blockIdx.y == 0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) task_resets(T, G, 0);
     if (T.alpha == nullptr) load_factors(fc, G.fac, T.sf0, T.snf);
     const int tb = blockIdx.x % ntb, sp = blockIdx.x / ntb;
     const int Nt = T.tgt.n, Ns = T.src.n;
@@ -118,13 +118,13 @@ __global__ void __launch_bounds__(256) k_epi(const Task* __restrict__ tasks, Glo
 }  // namespace
 
 cudaError_t launch_dense(int d, const Task* tasks, int ntask, int ntb, int nsplit, const Globals& G,
-                         int bump_iter, cudaStream_t st) {
+                         cudaStream_t st) {
     if (ntask <= 0) return cudaSuccess;
     dim3 grid(ntb * nsplit, ntask);
     switch (d) {
-    case 1: k_dense<1><<<grid, DENSE_TPB, 0, st>>>(tasks, G, ntb, nsplit, bump_iter); break;
-    case 2: k_dense<2><<<grid, DENSE_TPB, 0, st>>>(tasks, G, ntb, nsplit, bump_iter); break;
-    default: k_dense<3><<<grid, DENSE_TPB, 0, st>>>(tasks, G, ntb, nsplit, bump_iter); break;
+    case 1: k_dense<1><<<grid, DENSE_TPB, 0, st>>>(tasks, G, ntb, nsplit); break;
+    case 2: k_dense<2><<<grid, DENSE_TPB, 0, st>>>(tasks, G, ntb, nsplit); break;
+    default: k_dense<3><<<grid, DENSE_TPB, 0, st>>>(tasks, G, ntb, nsplit); break;
     }
     return cudaGetLastError();
 }

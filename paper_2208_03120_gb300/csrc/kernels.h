@@ -19,17 +19,26 @@ inline __host__ __device__ int mot_ntiles(int d, int n) {
 
 // ---- fast summation (nfft.cu) -------------------------------------------------------
 // All take a device array of `ntask` tasks and launch on `st`.
-cudaError_t launch_spread(int d, const Task* tasks, int ntask, int grid_x, const Globals& G, int bump_iter,
-                          cudaStream_t st);
+cudaError_t launch_spread(int d, const Task* tasks, int ntask, int grid_x, const Globals& G, cudaStream_t st);
 cudaError_t launch_fftconv(int d, const Task* tasks, int ntask, const Globals& G, cudaStream_t st, int* nlaunch);
 // Configure the shared-memory limits of the FFT kernels for grid length n (call before launching / capturing).
 cudaError_t prepare_fftconv(int d, int n);
 cudaError_t launch_gather(int d, const Task* tasks, int ntask, int grid_x, const Globals& G, cudaStream_t st);
 int spread_smem_bytes(int d, int n);
+// Window coefficients to constant memory (once per device; call before launching / capturing).
+cudaError_t prepare_window();
+// Fused 2-D fast summation (one thread-block cluster per task) for grids n <= 64.
+cudaError_t prepare_fused2d();
+bool fused2d_supported(int d, int n);
+int fused2d_cluster_size();
+cudaError_t launch_fused2d(const Task* tasks, int ntask, const Globals& G, cudaStream_t st);
+// One-block iteration prologue (resets, iteration counter, accumulators).
+cudaError_t launch_prologue(VecScale* const* list, int nlist, int save_prev, int bump, double* zero_d, int zero_n,
+                            const Globals& G, cudaStream_t st);
 
 // ---- dense direct summation (dense.cu) ----------------------------------------------
 cudaError_t launch_dense(int d, const Task* tasks, int ntask, int ntb, int nsplit, const Globals& G,
-                         int bump_iter, cudaStream_t st);
+                         cudaStream_t st);
 cudaError_t launch_epi(int d, const Task* tasks, int ntask, int grid_x, const Globals& G, cudaStream_t st);
 
 // ---- set-up (prep.cu) ---------------------------------------------------------------

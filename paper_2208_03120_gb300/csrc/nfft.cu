@@ -7,12 +7,16 @@
 // Points are binned into tiles of the periodic grid; one CTA handles one subproblem (<= P
 // points of one tile) and accumulates into a padded tile in shared memory, which is then added
 // to the L2-resident grid.  The window has 2m+2 = 10 taps per dimension.
+#include <cooperative_groups.h>
+#include <mutex>
+#include <vector>
+#include <cmath>
+
 #include "kernels.h"
 #include "fft_smem.cuh"
+#include "window.cuh"
 
 namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
 
 template <int D>
 __device__ __forceinline__ void tile_origin(int tile, int ntd, int TS, int* o) {
@@ -37,16 +41,16 @@ __device__ __forceinline__ int tile_to_global(int idx, int P, const int* o, int 
 }
 
 // ------------------------------------------------------------------------------------------
-// spread
+// spread: one thread per source point, 10^d taps into the padded tile in shared memory
 // ------------------------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, Globals G, int bump_iter) {
+__global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, Globals G) {
     __shared__ Task T;
     __shared__ FacCache fc;
     extern __shared__ float tile[];
     if (threadIdx.x == 0) T = tasks[blockIdx.y];
     __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) task_resets(T, G, bump_iter && blockIdx.y == 0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) task_resets(T, G, 0);
     if (T.alpha == nullptr) load_factors(fc, G.fac, T.sf0, T.snf);
 
     const int n = G.n_grid;
@@ -56,7 +60,6 @@ __global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, 
     if (D >= 3) npad *= P;
     const int N = T.src.n;
     const int nsub = *T.src.nsub;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
     for (int s = blockIdx.x; s < nsub; s += gridDim.x) {
         const Sub sb = T.src.subs[s];
@@ -65,43 +68,42 @@ __global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, 
         for (int i = threadIdx.x; i < npad; i += blockDim.x) tile[i] = 0.f;
         __syncthreads();
         const int j1 = sb.start + sb.len;
-        if (D == 1) {
-            for (int j = sb.start + threadIdx.x; j < j1; j += blockDim.x) {
-                const float v = T.alpha ? T.alpha[j] : eval_prod(fc, j);
-                const float u = T.src.u[j];
+        for (int j = sb.start + threadIdx.x; j < j1; j += blockDim.x) {
+            const float v = T.alpha ? T.alpha[j] : eval_prod(fc, j);
+            float w[D][MOT_W];
+            int base = 0, stride = 1;
+#pragma unroll
+            for (int t = 0; t < D; ++t) {
+                const float u = T.src.u[t * N + j];
                 const float fl = floorf(u);
-                const int b0 = (int)fl - MOT_WHALF - o[0];
-#pragma unroll
-                for (int a = 0; a < MOT_W; ++a)
-                    atomicAdd(&tile[b0 + a], v * kb_window(u - (fl - MOT_WHALF + a)));
+                window_taps(u - fl, w[t]);
+                base += ((int)fl - MOT_WHALF - o[t]) * stride;
+                stride *= P;
             }
-        } else {
-            for (int j = sb.start + warp; j < j1; j += nwarps) {
-                const float v = T.alpha ? T.alpha[j] : eval_prod(fc, j);
-                float wt[D];
-                int b[D];
+            if (D == 1) {
 #pragma unroll
-                for (int t = 0; t < D; ++t) {
-                    const float u = T.src.u[t * N + j];
-                    const float fl = floorf(u);
-                    b[t] = (int)fl - MOT_WHALF - o[t];
-                    wt[t] = lane < MOT_W ? kb_window(u - (fl - MOT_WHALF + lane)) : 0.f;
+                for (int a = 0; a < MOT_W; ++a) atomicAdd(&tile[base + a], v * w[0][a]);
+            } else if (D == 2) {
+#pragma unroll
+                for (int b = 0; b < MOT_W; ++b) {
+                    const float vb = v * w[1][b];
+                    float* row = tile + base + b * P;
+#pragma unroll
+                    for (int a = 0; a < MOT_W; ++a) atomicAdd(row + a, vb * w[0][a]);
                 }
+            } else {
+                // the z taps are consumed from the front of w[D-1], shifted each step, so the
+                // rolled loop indexes registers statically
+                for (int c = 0; c < MOT_W; ++c) {
+                    const float vc = v * w[D - 1][0];
 #pragma unroll
-                for (int it = 0; it < (MOT_W * MOT_W + 31) / 32; ++it) {
-                    const int tap = it * 32 + lane;
-                    const int a = tap % MOT_W;
-                    const int bb = min(tap / MOT_W, MOT_W - 1);
-                    const float wab = v * __shfl_sync(FULL, wt[0], a) * __shfl_sync(FULL, wt[1], bb);
-                    const bool ok = tap < MOT_W * MOT_W;
-                    if (D == 2) {
-                        if (ok) atomicAdd(&tile[(b[1] + bb) * P + b[0] + a], wab);
-                    } else {
+                    for (int q = 0; q < MOT_W - 1; ++q) w[D - 1][q] = w[D - 1][q + 1];
 #pragma unroll
-                        for (int c = 0; c < MOT_W; ++c) {
-                            const float wc = __shfl_sync(FULL, wt[D - 1], c);
-                            if (ok) atomicAdd(&tile[((b[D - 1] + c) * P + b[1] + bb) * P + b[0] + a], wab * wc);
-                        }
+                    for (int b = 0; b < MOT_W; ++b) {
+                        const float vb = vc * w[1][b];
+                        float* row = tile + base + (c * P + b) * P;
+#pragma unroll
+                        for (int a = 0; a < MOT_W; ++a) atomicAdd(row + a, vb * w[0][a]);
                     }
                 }
             }
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, 
 }
 
 // ------------------------------------------------------------------------------------------
-// gather + epilogue
+// gather + epilogue: one thread per target point
 // ------------------------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, Globals G) {
@@ -150,7 +152,6 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
         if (D >= 3) npad *= P;
         const int N = T.tgt.n;
         const int nsub = *T.tgt.nsub;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
         for (int s = blockIdx.x; s < nsub; s += gridDim.x) {
             const Sub sb = T.tgt.subs[s];
             int o[3];
@@ -158,53 +159,271 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
             for (int i = threadIdx.x; i < npad; i += blockDim.x) tile[i] = __ldg(&T.hgrid[tile_to_global<D>(i, P, o, n)]);
             __syncthreads();
             const int j1 = sb.start + sb.len;
-            if (D == 1) {
-                for (int j = sb.start + threadIdx.x; j < j1; j += blockDim.x) {
-                    const float u = T.tgt.u[j];
+            for (int j = sb.start + threadIdx.x; j < j1; j += blockDim.x) {
+                float w[D][MOT_W];
+                int base = 0, stride = 1;
+#pragma unroll
+                for (int t = 0; t < D; ++t) {
+                    const float u = T.tgt.u[t * N + j];
                     const float fl = floorf(u);
-                    const int b0 = (int)fl - MOT_WHALF - o[0];
-                    float acc = 0.f;
-#pragma unroll
-                    for (int a = 0; a < MOT_W; ++a) acc += tile[b0 + a] * kb_window(u - (fl - MOT_WHALF + a));
-                    epilogue_point(T, tf, Lsrc, G.floor_, j, acc, ep);
+                    window_taps(u - fl, w[t]);
+                    base += ((int)fl - MOT_WHALF - o[t]) * stride;
+                    stride *= P;
                 }
-            } else {
-                for (int j = sb.start + warp; j < j1; j += nwarps) {
-                    float wt[D];
-                    int b[D];
+                float acc = 0.f;
+                if (D == 1) {
 #pragma unroll
-                    for (int t = 0; t < D; ++t) {
-                        const float u = T.tgt.u[t * N + j];
-                        const float fl = floorf(u);
-                        b[t] = (int)fl - MOT_WHALF - o[t];
-                        wt[t] = lane < MOT_W ? kb_window(u - (fl - MOT_WHALF + lane)) : 0.f;
+                    for (int a = 0; a < MOT_W; ++a) acc = fmaf(tile[base + a], w[0][a], acc);
+                } else if (D == 2) {
+#pragma unroll
+                    for (int b = 0; b < MOT_W; ++b) {
+                        const float* row = tile + base + b * P;
+                        float r = 0.f;
+#pragma unroll
+                        for (int a = 0; a < MOT_W; ++a) r = fmaf(row[a], w[0][a], r);
+                        acc = fmaf(r, w[1][b], acc);
                     }
-                    float acc = 0.f;
+                } else {
+                    for (int c = 0; c < MOT_W; ++c) {
+                        float pc = 0.f;
 #pragma unroll
-                    for (int it = 0; it < (MOT_W * MOT_W + 31) / 32; ++it) {
-                        const int tap = it * 32 + lane;
-                        const int a = tap % MOT_W;
-                        const int bb = min(tap / MOT_W, MOT_W - 1);
-                        const float wab = __shfl_sync(FULL, wt[0], a) * __shfl_sync(FULL, wt[1], bb);
-                        const bool ok = tap < MOT_W * MOT_W;
-                        if (D == 2) {
-                            if (ok) acc += tile[(b[1] + bb) * P + b[0] + a] * wab;
-                        } else {
+                        for (int b = 0; b < MOT_W; ++b) {
+                            const float* row = tile + base + (c * P + b) * P;
+                            float r = 0.f;
 #pragma unroll
-                            for (int c = 0; c < MOT_W; ++c) {
-                                const float wc = __shfl_sync(FULL, wt[D - 1], c);
-                                if (ok) acc += tile[((b[D - 1] + c) * P + b[1] + bb) * P + b[0] + a] * (wab * wc);
-                            }
+                            for (int a = 0; a < MOT_W; ++a) r = fmaf(row[a], w[0][a], r);
+                            pc = fmaf(r, w[1][b], pc);
                         }
+                        acc = fmaf(pc, w[D - 1][0], acc);
+#pragma unroll
+                        for (int q = 0; q < MOT_W - 1; ++q) w[D - 1][q] = w[D - 1][q + 1];
                     }
-                    acc = warp_sum(acc);
-                    if (lane == 0) epilogue_point(T, tf, Lsrc, G.floor_, j, acc, ep);
                 }
+                epilogue_point(T, tf, Lsrc, G.floor_, j, acc, ep);
             }
             __syncthreads();
         }
     }
     epi_block_finish(T, G, tf, Lsrc, ep);
+}
+
+// ------------------------------------------------------------------------------------------
+// Fused 2-D fast summation for grids n <= 64: one thread-block cluster per task.
+//
+//   1. each CTA spreads 1/CS of the sources into a private n x n grid in shared memory;
+//   2. CTA r sums rows [rR, rR+R) over the cluster (distributed shared memory) and
+//      transforms them along x, keeping k_x in [0, M];
+//   3. CTA r takes the columns k_x = r, r+CS, ...: DFT along y for k_y in [-M, M], multiply by
+//      D, inverse DFT back to all y;
+//   4. CTA r forms rows [rR, rR+R) of h by the inverse x transform (real part);
+//   5. every CTA copies the whole h into its own shared memory and interpolates 1/CS of the
+//      targets, followed by the epilogue.
+// The DFTs are direct sums over the pruned frequency set (|k_t| <= M = n/4): on these grids
+// they are cheaper than radix-2 FFT stages separated by barriers.
+// ------------------------------------------------------------------------------------------
+#define F2_N 64
+#define F2_M 16
+#define F2_MAXR 8          // rows per CTA (n / CS) for CS >= 8
+#define F2_MAXC 3          // columns per CTA (ceil((M+1) / CS)) for CS >= 8
+
+__global__ void __launch_bounds__(256) k_fastsum2d(const Task* __restrict__ tasks, Globals G) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ Task T;
+    __shared__ FacCache fc, tf;
+    __shared__ double sLsrc;
+    __shared__ float Gs[F2_N * F2_N];
+    __shared__ float Grow[F2_MAXR * F2_N];
+    __shared__ float2 Gx[F2_MAXR * (F2_M + 1)];
+    __shared__ float2 Ycol[F2_MAXC][F2_N];
+    __shared__ float2 Hk[F2_MAXC][2 * F2_M + 1];
+    __shared__ float2 Acol[F2_MAXC][F2_N];
+    __shared__ float2 Arow[F2_MAXR * (F2_M + 1)];
+    __shared__ float Hrow[F2_MAXR * F2_N];
+    __shared__ float2 tw[F2_N];
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int CS = (int)cluster.num_blocks();
+    const int r = (int)cluster.block_rank();
+    if (tid == 0) T = tasks[blockIdx.y];
+    __syncthreads();
+    if (r == 0 && tid == 0) task_resets(T, G, 0);
+    if (T.alpha == nullptr) load_factors(fc, G.fac, T.sf0, T.snf);
+    load_factors(tf, G.fac, T.tf0, T.tnf);
+    if (tid == 0) sLsrc = T.alpha == nullptr ? fc.L : 0.0;
+    const int n = G.n_grid, M = G.M, mask = n - 1;
+    const bool fast = T.hgrid != nullptr;
+    for (int i = tid; i < n * n; i += nt) Gs[i] = 0.f;
+    for (int k = tid; k < n; k += nt) {
+        float sn, cs;
+        sincospif(2.f * (float)k / (float)n, &sn, &cs);
+        tw[k] = make_float2(cs, -sn);                  // e^{-2 pi i k / n}
+    }
+    __syncthreads();
+    EpiPartial ep;
+    epi_zero(ep);
+    const double Lsrc = sLsrc;
+
+    if (fast) {
+        // ---- 1. spread -------------------------------------------------------------------
+        const int Ns = T.src.n;
+        const int j0 = (int)((long long)r * Ns / CS), j1 = (int)((long long)(r + 1) * Ns / CS);
+        for (int j = j0 + tid; j < j1; j += nt) {
+            const float v = T.alpha ? T.alpha[j] : eval_prod(fc, j);
+            const float ux = T.src.u[j], uy = T.src.u[Ns + j];
+            const float fx = floorf(ux), fy = floorf(uy);
+            float wx[MOT_W], wy[MOT_W];
+            window_taps(ux - fx, wx);
+            window_taps(uy - fy, wy);
+            const int lx = (int)fx - MOT_WHALF, ly = (int)fy - MOT_WHALF;
+#pragma unroll
+            for (int b = 0; b < MOT_W; ++b) {
+                float* row = Gs + ((ly + b) & mask) * n;
+                const float vb = v * wy[b];
+#pragma unroll
+                for (int a = 0; a < MOT_W; ++a) atomicAdd(row + ((lx + a) & mask), vb * wx[a]);
+            }
+        }
+        cluster.sync();
+        // ---- 2. reduce owned rows, DFT along x ---------------------------------------------
+        const int R = n / CS;
+        const int y0 = r * R;
+        for (int i = tid; i < R * n; i += nt) {
+            float s = 0.f;
+            for (int q = 0; q < CS; ++q) s += cluster.map_shared_rank(Gs, q)[y0 * n + i];
+            Grow[i] = s;
+        }
+        __syncthreads();
+        for (int i = tid; i < R * (M + 1); i += nt) {
+            const int yy = i / (M + 1), kx = i - yy * (M + 1);
+            float2 acc = make_float2(0.f, 0.f);
+            const float* g = Grow + yy * n;
+            for (int x = 0; x < n; ++x) {
+                const float2 e = tw[(kx * x) & mask];
+                acc.x = fmaf(g[x], e.x, acc.x);
+                acc.y = fmaf(g[x], e.y, acc.y);
+            }
+            Gx[i] = acc;
+        }
+        cluster.sync();
+        // ---- 3. owned columns: DFT along y, multiply by D, inverse DFT -------------------
+        int ncols = 0;
+        int kxs[F2_MAXC];
+        for (int kx = r; kx <= M; kx += CS) kxs[ncols++] = kx;
+        for (int i = tid; i < ncols * n; i += nt) {
+            const int c = i / n, y = i - c * n;
+            const int owner = y / R;
+            Ycol[c][y] = cluster.map_shared_rank(Gx, owner)[(y - owner * R) * (M + 1) + kxs[c]];
+        }
+        __syncthreads();
+        for (int i = tid; i < ncols * (2 * M + 1); i += nt) {
+            const int c = i / (2 * M + 1), kyo = i - c * (2 * M + 1);
+            const int ky = kyo - M;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int y = 0; y < n; ++y) {
+                const float2 e = tw[(ky * y) & mask];       // e^{-2 pi i ky y / n}
+                const float2 a = Ycol[c][y];
+                acc.x = fmaf(a.x, e.x, fmaf(-a.y, e.y, acc.x));
+                acc.y = fmaf(a.x, e.y, fmaf(a.y, e.x, acc.y));
+            }
+            const float dd = T.D[kyo * (M + 1) + kxs[c]];
+            Hk[c][kyo] = make_float2(acc.x * dd, acc.y * dd);
+        }
+        __syncthreads();
+        for (int i = tid; i < ncols * n; i += nt) {
+            const int c = i / n, y = i - c * n;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int kyo = 0; kyo <= 2 * M; ++kyo) {
+                const float2 e = tw[((kyo - M) * y) & mask];  // conj: e^{+2 pi i ky y / n}
+                const float2 h = Hk[c][kyo];
+                acc.x = fmaf(h.x, e.x, fmaf(h.y, e.y, acc.x));
+                acc.y = fmaf(h.y, e.x, fmaf(-h.x, e.y, acc.y));
+            }
+            Acol[c][y] = acc;
+        }
+        cluster.sync();
+        // ---- 4. owned rows of h: inverse DFT along x (real part) -------------------------
+        for (int i = tid; i < R * (M + 1); i += nt) {
+            const int yy = i / (M + 1), kx = i - yy * (M + 1);
+            const int owner = kx % CS, slot = kx / CS;
+            Arow[i] = cluster.map_shared_rank(&Acol[0][0], owner)[slot * F2_N + y0 + yy];
+        }
+        __syncthreads();
+        for (int i = tid; i < R * n; i += nt) {
+            const int yy = i / n, x = i - yy * n;
+            float acc = 0.f;
+            for (int kx = 0; kx <= M; ++kx) {
+                const float2 e = tw[(kx * x) & mask];
+                const float2 a = Arow[yy * (M + 1) + kx];
+                acc = fmaf(a.x, e.x, fmaf(a.y, e.y, acc));   // Re(a e^{+i..}) with e = e^{-i..}
+            }
+            Hrow[i] = acc;
+        }
+        cluster.sync();
+        // ---- 5. copy h, interpolate ----------------------------------------------------
+        for (int i = tid; i < n * n; i += nt) {
+            const int y = i / n;
+            const int owner = y / R;
+            Gs[i] = cluster.map_shared_rank(Hrow, owner)[(y - owner * R) * n + (i - y * n)];
+        }
+        cluster.sync();      // peers may now leave; Hrow / Gs of this CTA are no longer read
+        const int Nt = T.tgt.n;
+        const int i0 = (int)((long long)r * Nt / CS), i1 = (int)((long long)(r + 1) * Nt / CS);
+        for (int i = i0 + tid; i < i1; i += nt) {
+            const float ux = T.tgt.u[i], uy = T.tgt.u[Nt + i];
+            const float fx = floorf(ux), fy = floorf(uy);
+            float wx[MOT_W], wy[MOT_W];
+            window_taps(ux - fx, wx);
+            window_taps(uy - fy, wy);
+            const int lx = (int)fx - MOT_WHALF, ly = (int)fy - MOT_WHALF;
+            float acc = 0.f;
+#pragma unroll
+            for (int b = 0; b < MOT_W; ++b) {
+                const float* row = Gs + ((ly + b) & mask) * n;
+                float s = 0.f;
+#pragma unroll
+                for (int a = 0; a < MOT_W; ++a) s = fmaf(row[(lx + a) & mask], wx[a], s);
+                acc = fmaf(s, wy[b], acc);
+            }
+            epilogue_point(T, tf, Lsrc, G.floor_, i, acc, ep);
+        }
+    } else {
+        // node step without a kernel product; the cluster barrier orders the reset above
+        cluster.sync();
+        const int Nt = T.tgt.n;
+        const int i0 = (int)((long long)r * Nt / CS), i1 = (int)((long long)(r + 1) * Nt / CS);
+        for (int i = i0 + tid; i < i1; i += nt) epilogue_point(T, tf, Lsrc, G.floor_, i, 1.f, ep);
+    }
+    epi_block_finish(T, G, tf, Lsrc, ep);
+}
+
+// ------------------------------------------------------------------------------------------
+// One-block iteration prologue: bump the iteration counter, zero the accumulators of the
+// next iterate, keep the previous scale of the scalings and reset the records that this
+// iteration produces.  Runs alone, so every later kernel of the iteration sees it.
+// ------------------------------------------------------------------------------------------
+__global__ void k_prologue(VecScale* const* __restrict__ list, int nlist, int save_prev, int bump,
+                           double* zero_d, int zero_n, Globals G) {
+    const int t = threadIdx.x;
+    for (int i = t; i < nlist; i += blockDim.x) {
+        VecScale* s = list[i];
+        if (save_prev) {
+            s->ls_prev = s->ls;
+            s->mx_prev_bits = s->mx_bits;
+        }
+        s->mx_bits = 0u;
+        s->clamped = 0u;
+    }
+    for (int i = t; i < zero_n; i += blockDim.x) zero_d[i] = 0.0;
+    if (bump && t == 0) {
+        const int it = *G.iter + 1;
+        *G.iter = it;
+        IterAcc* a = G.acc + ((it + 1) % G.R);
+        a->logphi = 0.0;
+        a->mass = 0.0;
+        a->rootviol = 0.0;
+        a->pad = 0.0;
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -418,15 +637,14 @@ int spread_smem_bytes(int d, int n) {
     return np * (int)sizeof(float);
 }
 
-cudaError_t launch_spread(int d, const Task* tasks, int ntask, int grid_x, const Globals& G, int bump_iter,
-                          cudaStream_t st) {
+cudaError_t launch_spread(int d, const Task* tasks, int ntask, int grid_x, const Globals& G, cudaStream_t st) {
     if (ntask <= 0) return cudaSuccess;
     dim3 grid(grid_x, ntask);
     int sm = spread_smem_bytes(d, G.n_grid);
     switch (d) {
-    case 1: k_spread<1><<<grid, 256, sm, st>>>(tasks, G, bump_iter); break;
-    case 2: k_spread<2><<<grid, 256, sm, st>>>(tasks, G, bump_iter); break;
-    default: k_spread<3><<<grid, 256, sm, st>>>(tasks, G, bump_iter); break;
+    case 1: k_spread<1><<<grid, 256, sm, st>>>(tasks, G); break;
+    case 2: k_spread<2><<<grid, 256, sm, st>>>(tasks, G); break;
+    default: k_spread<3><<<grid, 256, sm, st>>>(tasks, G); break;
     }
     return cudaGetLastError();
 }
@@ -490,4 +708,125 @@ cudaError_t launch_fftconv(int d, const Task* tasks, int ntask, const Globals& G
         if (nlaunch) *nlaunch += 3;
     }
     return cudaGetLastError();
+}
+
+// ---- fused 2-D path -------------------------------------------------------------------------
+namespace {
+int g_cluster_size = 0;
+}
+
+int fused2d_cluster_size() { return g_cluster_size; }
+
+bool fused2d_supported(int d, int n) { return d == 2 && n >= 16 && n <= F2_N && g_cluster_size > 0; }
+
+cudaError_t prepare_fused2d() {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (g_cluster_size != 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_fastsum2d, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) cudaGetLastError();
+    for (int cs : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs, 1, 1);
+        cfg.blockDim = dim3(256, 1, 1);
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = cs;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        e = cudaOccupancyMaxActiveClusters(&nclusters, k_fastsum2d, &cfg);
+        if (e == cudaSuccess && nclusters > 0) {
+            g_cluster_size = cs;
+            return cudaSuccess;
+        }
+        cudaGetLastError();
+    }
+    g_cluster_size = -1;
+    return cudaSuccess;
+}
+
+cudaError_t launch_fused2d(const Task* tasks, int ntask, const Globals& G, cudaStream_t st) {
+    if (ntask <= 0) return cudaSuccess;
+    const int cs = g_cluster_size;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, ntask, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = cs;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_fastsum2d, tasks, G);
+}
+
+cudaError_t launch_prologue(VecScale* const* list, int nlist, int save_prev, int bump, double* zero_d, int zero_n,
+                            const Globals& G, cudaStream_t st) {
+    k_prologue<<<1, 256, 0, st>>>(list, nlist, save_prev, bump, zero_d, zero_n, G);
+    return cudaGetLastError();
+}
+
+// ---- window coefficients ----------------------------------------------------------------------
+// Degree-8 interpolation of the normalised Kaiser-Bessel window on each tap's unit interval at
+// Chebyshev nodes, solved as a Vandermonde system in FP64 (host), uploaded once per device.
+static double kb_exact(double delta) {
+    const double a = MOT_WHALF + 1, b = 1.5 * 3.14159265358979323846;
+    const double t = a * a - delta * delta;
+    if (t <= 0.0) return 0.0;
+    const double r = std::sqrt(t);
+    if (r < 1e-12) return a * b / std::sinh(a * b);
+    return (a / r) * std::sinh(b * r) / std::sinh(a * b);
+}
+
+cudaError_t prepare_window() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    const int K = MOT_WDEG + 1;
+    float coef[MOT_W][MOT_WDEG + 1];
+    for (int j = 0; j < MOT_W; ++j) {
+        std::vector<double> A(K * K), f(K), c(K);
+        for (int i = 0; i < K; ++i) {
+            const double x = 0.5 + 0.5 * std::cos((2.0 * i + 1.0) * 3.14159265358979323846 / (2.0 * K));
+            double pw = 1.0;
+            for (int k = 0; k < K; ++k) {
+                A[i * K + k] = pw;
+                pw *= x;
+            }
+            f[i] = kb_exact(x + MOT_WHALF - j);
+        }
+        for (int col = 0; col < K; ++col) {              // Gaussian elimination, partial pivoting
+            int piv = col;
+            for (int rr = col + 1; rr < K; ++rr)
+                if (std::fabs(A[rr * K + col]) > std::fabs(A[piv * K + col])) piv = rr;
+            if (piv != col) {
+                for (int k = 0; k < K; ++k) std::swap(A[col * K + k], A[piv * K + k]);
+                std::swap(f[col], f[piv]);
+            }
+            for (int rr = col + 1; rr < K; ++rr) {
+                const double m = A[rr * K + col] / A[col * K + col];
+                for (int k = col; k < K; ++k) A[rr * K + k] -= m * A[col * K + k];
+                f[rr] -= m * f[col];
+            }
+        }
+        for (int rr = K - 1; rr >= 0; --rr) {
+            double s = f[rr];
+            for (int k = rr + 1; k < K; ++k) s -= A[rr * K + k] * c[k];
+            c[rr] = s / A[rr * K + rr];
+        }
+        for (int k = 0; k < K; ++k) coef[j][k] = (float)c[k];
+    }
+    e = cudaMemcpyToSymbol(c_win, coef, sizeof(coef));
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+    return e;
 }

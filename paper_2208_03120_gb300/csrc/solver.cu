@@ -289,6 +289,9 @@ struct TreePlan {
     std::vector<Factor> fac;
     std::vector<VecScale*> resets;
     std::vector<Level> fwd, bwd, chk;
+    size_t it_reset0 = 0, it_reset_n = 0;     // iteration prologue: phi (prev kept) and gamma records
+    size_t ck_reset0 = 0, ck_reset_n = 0;     // check prologue: gamma-ex records (+ acc_node zeroed)
+    bool fused = false;                        // 2-D grids <= 64: one cluster kernel per level
     Globals G;
     // graph
     cudaGraphExec_t gexec = nullptr;
@@ -540,17 +543,12 @@ void build_tasks(TreePlan& T) {
         t.phi_sc = T.phi_sc(0);
         T.fwd[0].tgt.push_back(t);
     }
-    // duties of the first launch of an iteration: save / reset the scaling records, reset
-    // the gamma records, bump the iteration counter (done by the kernel flag)
-    {
-        size_t r0 = T.resets.size();
-        for (int k = 0; k < K; ++k) T.resets.push_back(T.phi_sc(k));
-        for (int k = 1; k < K; ++k) T.resets.push_back(T.gam_sc(k));
-        Task& t0 = T.fwd[0].src.empty() ? T.fwd[0].tgt[0] : T.fwd[0].src[0];
-        t0.reset_n = (int)(T.resets.size() - r0);
-        t0.reset_list = (VecScale* const*)(uintptr_t)r0;   // resolved to a device pointer later
-        t0.save_prev = 1;
-    }
+    // iteration prologue: keep the scale of the last scalings (root mass), reset the scaling
+    // and gamma records that the forward pass produces
+    T.it_reset0 = T.resets.size();
+    for (int k = 0; k < K; ++k) T.resets.push_back(T.phi_sc(k));
+    for (int k = 1; k < K; ++k) T.resets.push_back(T.gam_sc(k));
+    T.it_reset_n = T.resets.size() - T.it_reset0;
 
     // ---- backward pass: beta_k from the deepest level up ---------------------------------
     T.bwd.assign(std::max(maxdepth, 1), Level());
@@ -600,13 +598,9 @@ void build_tasks(TreePlan& T) {
         t.phi_sc = T.phi_sc(0);
         t.acc_node = T.acc_node;
         T.chk[0].tgt.push_back(t);
-        size_t r0 = T.resets.size();
+        T.ck_reset0 = T.resets.size();
         for (int k = 1; k < K; ++k) T.resets.push_back(T.gex_sc(k));
-        Task& t0 = T.chk[0].src[0];
-        t0.reset_n = (int)(T.resets.size() - r0);
-        t0.reset_list = (VecScale* const*)(uintptr_t)r0;
-        t0.zero_d = T.acc_node;
-        t0.zero_n = 3 * K;
+        T.ck_reset_n = T.resets.size() - T.ck_reset0;
     }
 }
 
@@ -709,12 +703,17 @@ struct Timer {
     }
 };
 
-int run_level(TreePlan& T, Level& L, int bump, cudaStream_t st, Timer& tm, long long& nl) {
+int run_level(TreePlan& T, Level& L, cudaStream_t st, Timer& tm, long long& nl) {
     cudaEvent_t e = nullptr;
-    if (T.path == MOT_PATH_NFFT) {
+    if (T.path == MOT_PATH_NFFT && T.fused) {
+        RET(tm.begin(MOT_K_GATHER, &e));
+        CK(launch_fused2d(L.d_tgt, (int)L.tgt.size(), T.G, st));
+        RET(tm.end(e));
+        nl += 1;
+    } else if (T.path == MOT_PATH_NFFT) {
         if (!L.src.empty()) {
             RET(tm.begin(MOT_K_SPREAD, &e));
-            CK(launch_spread(T.d, L.d_src, (int)L.src.size(), L.grid_src, T.G, bump, st));
+            CK(launch_spread(T.d, L.d_src, (int)L.src.size(), L.grid_src, T.G, st));
             RET(tm.end(e));
             int nf = 0;
             RET(tm.begin(MOT_K_FFTCONV, &e));
@@ -729,7 +728,7 @@ int run_level(TreePlan& T, Level& L, int bump, cudaStream_t st, Timer& tm, long 
     } else {
         if (!L.src.empty()) {
             RET(tm.begin(MOT_K_DENSE, &e));
-            CK(launch_dense(T.d, L.d_src, (int)L.src.size(), L.ntb, L.nsplit, T.G, bump, st));
+            CK(launch_dense(T.d, L.d_src, (int)L.src.size(), L.ntb, L.nsplit, T.G, st));
             RET(tm.end(e));
             nl += 1;
         }
@@ -742,13 +741,23 @@ int run_level(TreePlan& T, Level& L, int bump, cudaStream_t st, Timer& tm, long 
 }
 
 int run_iteration(TreePlan& T, cudaStream_t st, Timer& tm, long long& nl) {
-    for (size_t l = 0; l < T.fwd.size(); ++l) RET(run_level(T, T.fwd[l], l == 0 ? 1 : 0, st, tm, nl));
-    for (auto& L : T.bwd) RET(run_level(T, L, 0, st, tm, nl));
+    cudaEvent_t e = nullptr;
+    RET(tm.begin(MOT_K_NODE, &e));
+    CK(launch_prologue(T.d_resets + T.it_reset0, (int)T.it_reset_n, 1, 1, nullptr, 0, T.G, st));
+    RET(tm.end(e));
+    nl += 1;
+    for (auto& L : T.fwd) RET(run_level(T, L, st, tm, nl));
+    for (auto& L : T.bwd) RET(run_level(T, L, st, tm, nl));
     return MOT_OK;
 }
 
 int run_check(TreePlan& T, cudaStream_t st, Timer& tm, long long& nl) {
-    for (auto& L : T.chk) RET(run_level(T, L, 0, st, tm, nl));
+    cudaEvent_t e = nullptr;
+    RET(tm.begin(MOT_K_NODE, &e));
+    CK(launch_prologue(T.d_resets + T.ck_reset0, (int)T.ck_reset_n, 0, 0, T.acc_node, 3 * T.K, T.G, st));
+    RET(tm.end(e));
+    nl += 1;
+    for (auto& L : T.chk) RET(run_level(T, L, st, tm, nl));
     return MOT_OK;
 }
 
@@ -862,7 +871,10 @@ int tree_plan_setup(const mot_problem* P, const mot_options& o, TreePlan& T, voi
     }
     // spectral multipliers per edge, grids zeroed
     if (T.path == MOT_PATH_NFFT) {
+        CK(prepare_window());
         CK(prepare_fftconv(T.d, g.n));
+        CK(prepare_fused2d());
+        T.fused = fused2d_supported(T.d, g.n);
         size_t gsz = 1;
         for (int t = 0; t < T.d; ++t) gsz *= g.n;
         for (int k = 1; k < T.K; ++k) {
@@ -903,7 +915,7 @@ int tree_solve(const mot_problem* P, const mot_options& o, void* ws, size_t ws_b
         }
     }
     // initial beta sweep (Algorithm 2, steps 3-5)
-    for (auto& L : T.bwd) RET(run_level(T, L, 0, st, tm, nl));
+    for (auto& L : T.bwd) RET(run_level(T, L, st, tm, nl));
 
     const bool graphs = o.use_graphs > 0;
     const bool want_viol = o.tol_viol >= 0.0;
@@ -1073,6 +1085,7 @@ int fastsum_impl(int d, double eta, const float* x_src, int64_t n_src, const flo
     size_t gsz = 1;
     for (int t = 0; t < d; ++t) gsz *= g.n;
     if (o.path == MOT_PATH_NFFT) {
+        CK(prepare_window());
         CK(prepare_fftconv(d, g.n));
         RET(make_D_for(eta_n, g, d, o, F.dscr_a, F.dscr_b, F.D, st));
         for (int r = 0; r < nrhs; ++r) CK(cudaMemsetAsync(F.grid[r], 0, gsz * sizeof(float), st));
@@ -1108,13 +1121,13 @@ int fastsum_impl(int d, double eta, const float* x_src, int64_t n_src, const flo
     G.fac = nullptr;
     if (o.path == MOT_PATH_NFFT) {
         int gx = std::min(F.src.maxsub, 1024), gt = std::min(F.tgt.maxsub, 1024);
-        CK(launch_spread(d, F.d_tasks, nrhs, gx, G, 0, st));
+        CK(launch_spread(d, F.d_tasks, nrhs, gx, G, st));
         CK(launch_fftconv(d, F.d_tasks, nrhs, G, st, nullptr));
         CK(launch_gather(d, F.d_tasks, nrhs, gt, G, st));
     } else {
         int ntb = (int)((n_tgt + 511) / 512);
         int split = std::max(1, std::min(64, 4 * 152 / std::max(1, ntb * nrhs)));
-        CK(launch_dense(d, F.d_tasks, nrhs, ntb, split, G, 0, st));
+        CK(launch_dense(d, F.d_tasks, nrhs, ntb, split, G, st));
         CK(launch_epi(d, F.d_tasks, nrhs, std::min((int)((n_tgt + 255) / 256), 1024), G, st));
     }
     for (int r = 0; r < nrhs; ++r)
