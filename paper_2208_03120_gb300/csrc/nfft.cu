@@ -225,8 +225,17 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
 #define F2_M 16
 #define F2_MAXR 8          // rows per CTA (n / CS) for CS >= 8
 #define F2_MAXC 3          // columns per CTA (ceil((M+1) / CS)) for CS >= 8
+#define F2_THREADS 512
 
-__global__ void __launch_bounds__(256) k_fastsum2d(const Task* __restrict__ tasks, Globals G) {
+// Sum of `v` over groups of G consecutive lanes (G a power of two <= 32).
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict__ tasks, Globals G) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     __shared__ Task T;
@@ -241,8 +250,11 @@ __global__ void __launch_bounds__(256) k_fastsum2d(const Task* __restrict__ task
     __shared__ float2 Arow[F2_MAXR * (F2_M + 1)];
     __shared__ float Hrow[F2_MAXR * F2_N];
     __shared__ float2 tw[F2_N];
+    __shared__ float cw[MOT_W][MOT_WDEG + 1];     // window coefficients (per-lane rows)
 
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+    for (int i = tid; i < MOT_W * (MOT_WDEG + 1); i += nt) (&cw[0][0])[i] = (&c_win[0][0])[i];
     const int CS = (int)cluster.num_blocks();
     const int r = (int)cluster.block_rank();
     if (tid == 0) T = tasks[blockIdx.y];
@@ -265,27 +277,31 @@ __global__ void __launch_bounds__(256) k_fastsum2d(const Task* __restrict__ task
     const double Lsrc = sLsrc;
 
     if (fast) {
-        // ---- 1. spread -------------------------------------------------------------------
+        // ---- 1. spread: one warp per point, lanes over the 100 taps (distinct addresses) --
         const int Ns = T.src.n;
         const int j0 = (int)((long long)r * Ns / CS), j1 = (int)((long long)(r + 1) * Ns / CS);
-        for (int j = j0 + tid; j < j1; j += nt) {
+        for (int j = j0 + warp; j < j1; j += nwarps) {
             const float v = T.alpha ? T.alpha[j] : eval_prod(fc, j);
             const float ux = T.src.u[j], uy = T.src.u[Ns + j];
             const float fx = floorf(ux), fy = floorf(uy);
-            float wx[MOT_W], wy[MOT_W];
-            window_taps(ux - fx, wx);
-            window_taps(uy - fy, wy);
+            // lanes 0..9: x taps, lanes 10..19: y taps
+            const int tap = lane < MOT_W ? lane : (lane < 2 * MOT_W ? lane - MOT_W : 0);
+            const float f = lane < MOT_W ? ux - fx : uy - fy;
+            float w = cw[tap][MOT_WDEG];
+#pragma unroll
+            for (int k = MOT_WDEG - 1; k >= 0; --k) w = fmaf(w, f, cw[tap][k]);
             const int lx = (int)fx - MOT_WHALF, ly = (int)fy - MOT_WHALF;
 #pragma unroll
-            for (int b = 0; b < MOT_W; ++b) {
-                float* row = Gs + ((ly + b) & mask) * n;
-                const float vb = v * wy[b];
-#pragma unroll
-                for (int a = 0; a < MOT_W; ++a) atomicAdd(row + ((lx + a) & mask), vb * wx[a]);
+            for (int it = 0; it < (MOT_W * MOT_W + 31) / 32; ++it) {
+                const int t = it * 32 + lane;
+                const int a = t % MOT_W, b = min(t / MOT_W, MOT_W - 1);
+                const float wa = __shfl_sync(0xffffffffu, w, a);
+                const float wb = __shfl_sync(0xffffffffu, w, MOT_W + b);
+                if (t < MOT_W * MOT_W) atomicAdd(&Gs[((ly + b) & mask) * n + ((lx + a) & mask)], v * wa * wb);
             }
         }
         cluster.sync();
-        // ---- 2. reduce owned rows, DFT along x ---------------------------------------------
+        // ---- 2. reduce owned rows, DFT along x (4 lanes per output) ---------------------
         const int R = n / CS;
         const int y0 = r * R;
         for (int i = tid; i < R * n; i += nt) {
@@ -294,16 +310,24 @@ __global__ void __launch_bounds__(256) k_fastsum2d(const Task* __restrict__ task
             Grow[i] = s;
         }
         __syncthreads();
-        for (int i = tid; i < R * (M + 1); i += nt) {
-            const int yy = i / (M + 1), kx = i - yy * (M + 1);
-            float2 acc = make_float2(0.f, 0.f);
-            const float* g = Grow + yy * n;
-            for (int x = 0; x < n; ++x) {
-                const float2 e = tw[(kx * x) & mask];
-                acc.x = fmaf(g[x], e.x, acc.x);
-                acc.y = fmaf(g[x], e.y, acc.y);
+        {
+            const int nout = R * (M + 1);
+            for (int base = 0; base < nout * 4; base += nt) {
+                const int gi = base + tid, o = gi >> 2, sub = gi & 3;
+                float2 acc = make_float2(0.f, 0.f);
+                if (o < nout) {
+                    const int yy = o / (M + 1), kx = o - yy * (M + 1);
+                    const float* g = Grow + yy * n;
+                    for (int x = sub; x < n; x += 4) {
+                        const float2 e = tw[(kx * x) & mask];
+                        acc.x = fmaf(g[x], e.x, acc.x);
+                        acc.y = fmaf(g[x], e.y, acc.y);
+                    }
+                }
+                acc.x = group_sum<4>(acc.x);
+                acc.y = group_sum<4>(acc.y);
+                if (o < nout && sub == 0) Gx[o] = acc;
             }
-            Gx[i] = acc;
         }
         cluster.sync();
         // ---- 3. owned columns: DFT along y, multiply by D, inverse DFT -------------------
@@ -316,57 +340,84 @@ __global__ void __launch_bounds__(256) k_fastsum2d(const Task* __restrict__ task
             Ycol[c][y] = cluster.map_shared_rank(Gx, owner)[(y - owner * R) * (M + 1) + kxs[c]];
         }
         __syncthreads();
-        for (int i = tid; i < ncols * (2 * M + 1); i += nt) {
-            const int c = i / (2 * M + 1), kyo = i - c * (2 * M + 1);
-            const int ky = kyo - M;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int y = 0; y < n; ++y) {
-                const float2 e = tw[(ky * y) & mask];       // e^{-2 pi i ky y / n}
-                const float2 a = Ycol[c][y];
-                acc.x = fmaf(a.x, e.x, fmaf(-a.y, e.y, acc.x));
-                acc.y = fmaf(a.x, e.y, fmaf(a.y, e.x, acc.y));
+        {
+            const int nout = ncols * (2 * M + 1);
+            for (int base = 0; base < nout * 4; base += nt) {
+                const int gi = base + tid, o = gi >> 2, sub = gi & 3;
+                float2 acc = make_float2(0.f, 0.f);
+                int c = 0, kyo = 0;
+                if (o < nout) {
+                    c = o / (2 * M + 1);
+                    kyo = o - c * (2 * M + 1);
+                    const int ky = kyo - M;
+                    for (int y = sub; y < n; y += 4) {
+                        const float2 e = tw[(ky * y) & mask];
+                        const float2 a = Ycol[c][y];
+                        acc.x = fmaf(a.x, e.x, fmaf(-a.y, e.y, acc.x));
+                        acc.y = fmaf(a.x, e.y, fmaf(a.y, e.x, acc.y));
+                    }
+                }
+                acc.x = group_sum<4>(acc.x);
+                acc.y = group_sum<4>(acc.y);
+                if (o < nout && sub == 0) {
+                    const float dd = T.D[kyo * (M + 1) + kxs[c]];
+                    Hk[c][kyo] = make_float2(acc.x * dd, acc.y * dd);
+                }
             }
-            const float dd = T.D[kyo * (M + 1) + kxs[c]];
-            Hk[c][kyo] = make_float2(acc.x * dd, acc.y * dd);
         }
         __syncthreads();
-        for (int i = tid; i < ncols * n; i += nt) {
-            const int c = i / n, y = i - c * n;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int kyo = 0; kyo <= 2 * M; ++kyo) {
-                const float2 e = tw[((kyo - M) * y) & mask];  // conj: e^{+2 pi i ky y / n}
-                const float2 h = Hk[c][kyo];
-                acc.x = fmaf(h.x, e.x, fmaf(h.y, e.y, acc.x));
-                acc.y = fmaf(h.y, e.x, fmaf(-h.x, e.y, acc.y));
+        {
+            const int nout = ncols * n;
+            for (int base = 0; base < nout * 4; base += nt) {
+                const int gi = base + tid, o = gi >> 2, sub = gi & 3;
+                float2 acc = make_float2(0.f, 0.f);
+                if (o < nout) {
+                    const int c = o / n, y = o - c * n;
+                    for (int kyo = sub; kyo <= 2 * M; kyo += 4) {
+                        const float2 e = tw[((kyo - M) * y) & mask];   // conj: e^{+2 pi i ky y / n}
+                        const float2 h = Hk[c][kyo];
+                        acc.x = fmaf(h.x, e.x, fmaf(h.y, e.y, acc.x));
+                        acc.y = fmaf(h.y, e.x, fmaf(-h.x, e.y, acc.y));
+                    }
+                }
+                acc.x = group_sum<4>(acc.x);
+                acc.y = group_sum<4>(acc.y);
+                if (o < nout && sub == 0) Acol[o / n][o % n] = acc;
             }
-            Acol[c][y] = acc;
         }
         cluster.sync();
-        // ---- 4. owned rows of h: inverse DFT along x (real part) -------------------------
+        // ---- 4. owned rows of h: inverse DFT along x (real part), 2 lanes per output -----
         for (int i = tid; i < R * (M + 1); i += nt) {
             const int yy = i / (M + 1), kx = i - yy * (M + 1);
             const int owner = kx % CS, slot = kx / CS;
             Arow[i] = cluster.map_shared_rank(&Acol[0][0], owner)[slot * F2_N + y0 + yy];
         }
         __syncthreads();
-        for (int i = tid; i < R * n; i += nt) {
-            const int yy = i / n, x = i - yy * n;
-            float acc = 0.f;
-            for (int kx = 0; kx <= M; ++kx) {
-                const float2 e = tw[(kx * x) & mask];
-                const float2 a = Arow[yy * (M + 1) + kx];
-                acc = fmaf(a.x, e.x, fmaf(a.y, e.y, acc));   // Re(a e^{+i..}) with e = e^{-i..}
+        {
+            const int nout = R * n;
+            for (int base = 0; base < nout * 2; base += nt) {
+                const int gi = base + tid, o = gi >> 1, sub = gi & 1;
+                float acc = 0.f;
+                if (o < nout) {
+                    const int yy = o / n, x = o - yy * n;
+                    for (int kx = sub; kx <= M; kx += 2) {
+                        const float2 e = tw[(kx * x) & mask];
+                        const float2 a = Arow[yy * (M + 1) + kx];
+                        acc = fmaf(a.x, e.x, fmaf(a.y, e.y, acc));
+                    }
+                }
+                acc = group_sum<2>(acc);
+                if (o < nout && sub == 0) Hrow[o] = acc;
             }
-            Hrow[i] = acc;
         }
         cluster.sync();
-        // ---- 5. copy h, interpolate ----------------------------------------------------
+        // ---- 5. copy h, interpolate (one thread per target) ------------------------------
         for (int i = tid; i < n * n; i += nt) {
             const int y = i / n;
             const int owner = y / R;
             Gs[i] = cluster.map_shared_rank(Hrow, owner)[(y - owner * R) * n + (i - y * n)];
         }
-        cluster.sync();      // peers may now leave; Hrow / Gs of this CTA are no longer read
+        cluster.sync();      // peers may now leave; Hrow of this CTA is no longer read
         const int Nt = T.tgt.n;
         const int i0 = (int)((long long)r * Nt / CS), i1 = (int)((long long)(r + 1) * Nt / CS);
         for (int i = i0 + tid; i < i1; i += nt) {
@@ -380,10 +431,10 @@ __global__ void __launch_bounds__(256) k_fastsum2d(const Task* __restrict__ task
 #pragma unroll
             for (int b = 0; b < MOT_W; ++b) {
                 const float* row = Gs + ((ly + b) & mask) * n;
-                float s = 0.f;
+                float s2 = 0.f;
 #pragma unroll
-                for (int a = 0; a < MOT_W; ++a) s = fmaf(row[(lx + a) & mask], wx[a], s);
-                acc = fmaf(s, wy[b], acc);
+                for (int a = 0; a < MOT_W; ++a) s2 = fmaf(row[(lx + a) & mask], wx[a], s2);
+                acc = fmaf(s2, wy[b], acc);
             }
             epilogue_point(T, tf, Lsrc, G.floor_, i, acc, ep);
         }
@@ -728,7 +779,7 @@ cudaError_t prepare_fused2d() {
     for (int cs : {16, 8}) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cs, 1, 1);
-        cfg.blockDim = dim3(256, 1, 1);
+        cfg.blockDim = dim3(F2_THREADS, 1, 1);
         cudaLaunchAttribute attr;
         attr.id = cudaLaunchAttributeClusterDimension;
         attr.val.clusterDim.x = cs;
@@ -753,7 +804,7 @@ cudaError_t launch_fused2d(const Task* tasks, int ntask, const Globals& G, cudaS
     const int cs = g_cluster_size;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, ntask, 1);
-    cfg.blockDim = dim3(256, 1, 1);
+    cfg.blockDim = dim3(F2_THREADS, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cudaLaunchAttribute attr;
