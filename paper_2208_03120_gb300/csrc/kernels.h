@@ -10,6 +10,11 @@ inline __host__ __device__ int mot_tile_size(int d, int n) {
     return t < n ? t : n;
 }
 inline __host__ __device__ int mot_sub_points(int d) { return d == 1 ? 1024 : 256; }
+inline __host__ __device__ int mot_ncells(int d, int n) {
+    int t = 1;
+    for (int i = 0; i < d; ++i) t *= n;
+    return t;
+}
 inline __host__ __device__ int mot_ntiles(int d, int n) {
     int per = n / mot_tile_size(d, n);
     int t = 1;
@@ -48,8 +53,8 @@ struct PrepSet {                 // one point set to normalise and bin
     int n;
     float* u_tmp;                // [d][n] scratch
     int* tile_of;                // [n] scratch
-    int* counts;                 // [ntiles] scratch
-    int* cursor;                 // [ntiles] scratch
+    int* counts;                 // [n_grid^d] scratch (points per grid cell)
+    int* cursor;                 // [n_grid^d] scratch
     float* u;                    // [d][n] sorted coordinates (grid units)
     int* perm;                   // [n] sorted position -> caller index
     float* mu_f;                 // [n] or NULL

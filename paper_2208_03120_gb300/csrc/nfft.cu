@@ -41,14 +41,85 @@ __device__ __forceinline__ int tile_to_global(int idx, int P, const int* o, int 
 }
 
 // ------------------------------------------------------------------------------------------
-// spread: one thread per source point, 10^d taps into the padded tile in shared memory
+// spread.  Points are sorted by grid cell inside each tile.  A warp walks a contiguous run of
+// points; its lanes own the taps of the window (2-D: 100 taps, 4 per lane; 3-D: 100 (x, y)
+// pairs x 10 z taps, 40 per lane), accumulate consecutive points of the same cell in
+// registers, and add them to shared memory only when the cell changes (distinct addresses
+// per instruction, one atomic per tap per occupied cell instead of per point).
 // ------------------------------------------------------------------------------------------
+template <int D>
+struct RunSpread {
+    static constexpr int NI = D == 1 ? 1 : 4;       // tap groups per lane
+    static constexpr int NC = D == 3 ? MOT_W : 1;   // z taps per group
+    float acc[NI][NC];
+    int a[NI], b[NI];
+    bool ok[NI];
+    int lane;
+
+    __device__ __forceinline__ void init(int lane_) {
+        lane = lane_;
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int q = lane + 32 * i;
+            if (D == 1) {
+                ok[i] = lane < MOT_W;
+                a[i] = lane < MOT_W ? lane : 0;
+                b[i] = 0;
+            } else {
+                ok[i] = q < MOT_W * MOT_W;
+                a[i] = q % MOT_W;
+                b[i] = min(q / MOT_W, MOT_W - 1);
+            }
+        }
+        zero();
+    }
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[i][c] = 0.f;
+    }
+    // Lane-distributed window weights: lane L < 10 D holds tap (L % 10) of dimension L / 10.
+    __device__ __forceinline__ float lane_weight(const float (*cw)[MOT_WDEG + 1], const float* f) const {
+        const int dim = lane / MOT_W, tap = lane % MOT_W;
+        if (dim >= D) return 0.f;
+        const float fl = dim == 0 ? f[0] : (dim == 1 ? f[D > 1 ? 1 : 0] : f[D - 1]);
+        float w = cw[tap][MOT_WDEG];
+#pragma unroll
+        for (int k = MOT_WDEG - 1; k >= 0; --k) w = fmaf(w, fl, cw[tap][k]);
+        return w;
+    }
+    __device__ __forceinline__ void add(float v, float w) {
+        if (D == 1) {
+            acc[0][0] = fmaf(v, w, acc[0][0]);
+        } else {
+            float wab[NI];
+#pragma unroll
+            for (int i = 0; i < NI; ++i)
+                wab[i] = v * __shfl_sync(0xffffffffu, w, a[i]) * __shfl_sync(0xffffffffu, w, MOT_W + b[i]);
+            if (D == 2) {
+#pragma unroll
+                for (int i = 0; i < NI; ++i) acc[i][0] += wab[i];
+            } else {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const float wc = __shfl_sync(0xffffffffu, w, 2 * MOT_W + c);
+#pragma unroll
+                    for (int i = 0; i < NI; ++i) acc[i][c] = fmaf(wab[i], wc, acc[i][c]);
+                }
+            }
+        }
+    }
+};
+
 template <int D>
 __global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, Globals G) {
     __shared__ Task T;
     __shared__ FacCache fc;
+    __shared__ float cw[MOT_W][MOT_WDEG + 1];
     extern __shared__ float tile[];
     if (threadIdx.x == 0) T = tasks[blockIdx.y];
+    for (int i = threadIdx.x; i < MOT_W * (MOT_WDEG + 1); i += blockDim.x) (&cw[0][0])[i] = (&c_win[0][0])[i];
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) task_resets(T, G, 0);
     if (T.alpha == nullptr) load_factors(fc, G.fac, T.sf0, T.snf);
@@ -60,6 +131,7 @@ __global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, 
     if (D >= 3) npad *= P;
     const int N = T.src.n;
     const int nsub = *T.src.nsub;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
     for (int s = blockIdx.x; s < nsub; s += gridDim.x) {
         const Sub sb = T.src.subs[s];
@@ -67,46 +139,42 @@ __global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, 
         tile_origin<D>(sb.tile, ntd, TS, o);
         for (int i = threadIdx.x; i < npad; i += blockDim.x) tile[i] = 0.f;
         __syncthreads();
-        const int j1 = sb.start + sb.len;
-        for (int j = sb.start + threadIdx.x; j < j1; j += blockDim.x) {
+        const int chunk = (sb.len + nwarps - 1) / nwarps;
+        const int j0 = sb.start + min(sb.len, warp * chunk), j1 = sb.start + min(sb.len, (warp + 1) * chunk);
+        RunSpread<D> rs;
+        rs.init(lane);
+        int cur = -1;
+        for (int j = j0; j < j1; ++j) {
             const float v = T.alpha ? T.alpha[j] : eval_prod(fc, j);
-            float w[D][MOT_W];
+            float f[D];
             int base = 0, stride = 1;
 #pragma unroll
             for (int t = 0; t < D; ++t) {
                 const float u = T.src.u[t * N + j];
                 const float fl = floorf(u);
-                window_taps(u - fl, w[t]);
+                f[t] = u - fl;
                 base += ((int)fl - MOT_WHALF - o[t]) * stride;
                 stride *= P;
             }
-            if (D == 1) {
+            if (base != cur) {
+                if (cur >= 0) {
 #pragma unroll
-                for (int a = 0; a < MOT_W; ++a) atomicAdd(&tile[base + a], v * w[0][a]);
-            } else if (D == 2) {
+                    for (int i = 0; i < RunSpread<D>::NI; ++i)
 #pragma unroll
-                for (int b = 0; b < MOT_W; ++b) {
-                    const float vb = v * w[1][b];
-                    float* row = tile + base + b * P;
-#pragma unroll
-                    for (int a = 0; a < MOT_W; ++a) atomicAdd(row + a, vb * w[0][a]);
+                        for (int c = 0; c < RunSpread<D>::NC; ++c)
+                            if (rs.ok[i]) atomicAdd(&tile[cur + (c * P + rs.b[i]) * (D >= 2 ? P : 0) + rs.a[i]], rs.acc[i][c]);
+                    rs.zero();
                 }
-            } else {
-                // the z taps are consumed from the front of w[D-1], shifted each step, so the
-                // rolled loop indexes registers statically
-                for (int c = 0; c < MOT_W; ++c) {
-                    const float vc = v * w[D - 1][0];
-#pragma unroll
-                    for (int q = 0; q < MOT_W - 1; ++q) w[D - 1][q] = w[D - 1][q + 1];
-#pragma unroll
-                    for (int b = 0; b < MOT_W; ++b) {
-                        const float vb = vc * w[1][b];
-                        float* row = tile + base + (c * P + b) * P;
-#pragma unroll
-                        for (int a = 0; a < MOT_W; ++a) atomicAdd(row + a, vb * w[0][a]);
-                    }
-                }
+                cur = base;
             }
+            rs.add(v, rs.lane_weight(cw, f));
+        }
+        if (cur >= 0) {
+#pragma unroll
+            for (int i = 0; i < RunSpread<D>::NI; ++i)
+#pragma unroll
+                for (int c = 0; c < RunSpread<D>::NC; ++c)
+                    if (rs.ok[i]) atomicAdd(&tile[cur + (c * P + rs.b[i]) * (D >= 2 ? P : 0) + rs.a[i]], rs.acc[i][c]);
         }
         __syncthreads();
         for (int i = threadIdx.x; i < npad; i += blockDim.x) {
@@ -277,27 +345,39 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
     const double Lsrc = sLsrc;
 
     if (fast) {
-        // ---- 1. spread: one warp per point, lanes over the 100 taps (distinct addresses) --
+        // ---- 1. spread: warps walk contiguous runs of cell-sorted points ----------------------
         const int Ns = T.src.n;
         const int j0 = (int)((long long)r * Ns / CS), j1 = (int)((long long)(r + 1) * Ns / CS);
-        for (int j = j0 + warp; j < j1; j += nwarps) {
-            const float v = T.alpha ? T.alpha[j] : eval_prod(fc, j);
-            const float ux = T.src.u[j], uy = T.src.u[Ns + j];
-            const float fx = floorf(ux), fy = floorf(uy);
-            // lanes 0..9: x taps, lanes 10..19: y taps
-            const int tap = lane < MOT_W ? lane : (lane < 2 * MOT_W ? lane - MOT_W : 0);
-            const float f = lane < MOT_W ? ux - fx : uy - fy;
-            float w = cw[tap][MOT_WDEG];
+        {
+            const int chunk = (j1 - j0 + nwarps - 1) / nwarps;
+            const int w0 = j0 + min(j1 - j0, warp * chunk), w1 = j0 + min(j1 - j0, (warp + 1) * chunk);
+            RunSpread<2> rs;
+            rs.init(lane);
+            int cur = -1, clx = 0, cly = 0;
+            for (int j = w0; j < w1; ++j) {
+                const float v = T.alpha ? T.alpha[j] : eval_prod(fc, j);
+                const float ux = T.src.u[j], uy = T.src.u[Ns + j];
+                const float fx = floorf(ux), fy = floorf(uy);
+                const int lx = (int)fx - MOT_WHALF, ly = (int)fy - MOT_WHALF;
+                const int key = ((ly & mask) << 8) | (lx & mask);
+                if (key != cur) {
+                    if (cur >= 0) {
 #pragma unroll
-            for (int k = MOT_WDEG - 1; k >= 0; --k) w = fmaf(w, f, cw[tap][k]);
-            const int lx = (int)fx - MOT_WHALF, ly = (int)fy - MOT_WHALF;
+                        for (int i = 0; i < 4; ++i)
+                            if (rs.ok[i]) atomicAdd(&Gs[((cly + rs.b[i]) & mask) * n + ((clx + rs.a[i]) & mask)], rs.acc[i][0]);
+                        rs.zero();
+                    }
+                    cur = key;
+                    clx = lx;
+                    cly = ly;
+                }
+                const float f[2] = {ux - fx, uy - fy};
+                rs.add(v, rs.lane_weight(cw, f));
+            }
+            if (cur >= 0) {
 #pragma unroll
-            for (int it = 0; it < (MOT_W * MOT_W + 31) / 32; ++it) {
-                const int t = it * 32 + lane;
-                const int a = t % MOT_W, b = min(t / MOT_W, MOT_W - 1);
-                const float wa = __shfl_sync(0xffffffffu, w, a);
-                const float wb = __shfl_sync(0xffffffffu, w, MOT_W + b);
-                if (t < MOT_W * MOT_W) atomicAdd(&Gs[((ly + b) & mask) * n + ((lx + a) & mask)], v * wa * wb);
+                for (int i = 0; i < 4; ++i)
+                    if (rs.ok[i]) atomicAdd(&Gs[((cly + rs.b[i]) & mask) * n + ((clx + rs.a[i]) & mask)], rs.acc[i][0]);
             }
         }
         cluster.sync();

@@ -66,8 +66,10 @@ struct PrepArgs {
 __global__ void k_prep_points(const PrepSet* __restrict__ sets, PrepArgs A, int* err) {
     const PrepSet S = sets[blockIdx.y];
     const double half = 0.5 * A.n_grid;
+    int tcells = 1;
+    for (int t = 0; t < A.d; ++t) tcells *= A.TS;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S.n; j += gridDim.x * blockDim.x) {
-        int tile = 0, mult = 1;
+        int tile = 0, mult = 1, local = 0, lmult = 1;
         for (int t = 0; t < A.d; ++t) {
             float xf = S.x[(size_t)j * A.d + t];
             if (!isfinite(xf)) atomicOr(err, 1);
@@ -83,9 +85,13 @@ __global__ void k_prep_points(const PrepSet* __restrict__ sets, PrepArgs A, int*
             int cell = min((int)floorf(uf), A.n_grid - 1);
             tile += (cell / A.TS) * mult;
             mult *= A.ntd;
+            local += (cell % A.TS) * lmult;
+            lmult *= A.TS;
         }
-        S.tile_of[j] = tile;
-        atomicAdd(&S.counts[tile], 1);
+        // sort key: tile-major, then the cell inside the tile
+        const int key = tile * tcells + local;
+        S.tile_of[j] = key;
+        atomicAdd(&S.counts[key], 1);
         if (S.mu) {
             double m = S.mu[j];
             if (!(m >= 0.0) || isinf(m)) atomicOr(err, 2);
@@ -93,27 +99,49 @@ __global__ void k_prep_points(const PrepSet* __restrict__ sets, PrepArgs A, int*
     }
 }
 
-// Exclusive scan of the tile counts and the subproblem list (one thread per set: the tile
-// count is at most a few thousand and this runs once per solve).
-__global__ void k_prep_scan(const PrepSet* __restrict__ sets, int ntiles, int psub) {
+// Exclusive scan of the per-cell counts (one block per set), then the subproblem list: every
+// tile's points are contiguous and split into runs of at most psub points.
+__global__ void __launch_bounds__(1024) k_prep_scan(const PrepSet* __restrict__ sets, int ncells, int tcells,
+                                                    int psub) {
     const PrepSet S = sets[blockIdx.x];
-    if (threadIdx.x != 0) return;
-    int off = 0, ns = 0;
-    for (int t = 0; t < ntiles; ++t) {
-        int c = S.counts[t];
-        S.cursor[t] = off;
-        for (int s = 0; s < c; s += psub) {
+    __shared__ int part[1024];
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int chunk = (ncells + nt - 1) / nt;
+    const int c0 = min(ncells, t * chunk), c1 = min(ncells, c0 + chunk);
+    int local = 0;
+    for (int c = c0; c < c1; ++c) local += S.counts[c];
+    part[t] = local;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {          // inclusive Hillis-Steele scan
+        int v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = part[t] - local;                        // exclusive prefix of this chunk
+    for (int c = c0; c < c1; ++c) {
+        const int cnt = S.counts[c];
+        S.cursor[c] = run;
+        run += cnt;
+    }
+    __syncthreads();
+    if (t != 0) return;
+    const int ntiles = ncells / tcells;
+    int ns = 0;
+    for (int tile = 0; tile < ntiles; ++tile) {
+        const int start = S.cursor[tile * tcells];
+        const int end = tile + 1 < ntiles ? S.cursor[(tile + 1) * tcells] : S.n;
+        for (int s = start; s < end; s += psub) {
             if (ns < S.maxsub) {
                 Sub sb;
-                sb.tile = t;
-                sb.start = off + s;
-                sb.len = min(psub, c - s);
+                sb.tile = tile;
+                sb.start = s;
+                sb.len = min(psub, end - s);
                 sb.pad = 0;
                 S.subs[ns] = sb;
             }
             ++ns;
         }
-        off += c;
     }
     *S.nsub = min(ns, S.maxsub);
 }
@@ -333,16 +361,18 @@ cudaError_t launch_prep(const PrepSet* sets_dev, const PrepSet* sets_host, int n
     A.psub = mot_sub_points(d);
     for (int t = 0; t < 3; ++t) A.c[t] = t < d ? c[t] : 0.0;
     A.inv_s = 1.0 / s;
-    const int ntiles = mot_ntiles(d, n_grid);
+    const int ncells = mot_ncells(d, n_grid);
+    int tcells = 1;
+    for (int t = 0; t < d; ++t) tcells *= A.TS;
     int maxn = 1;
     for (int k = 0; k < nsets; ++k) {
-        cudaError_t e = cudaMemsetAsync(sets_host[k].counts, 0, sizeof(int) * ntiles, st);
+        cudaError_t e = cudaMemsetAsync(sets_host[k].counts, 0, sizeof(int) * ncells, st);
         if (e != cudaSuccess) return e;
         if (sets_host[k].n > maxn) maxn = sets_host[k].n;
     }
     const int bx = blocks_for(maxn, 256, 1024);
     k_prep_points<<<dim3(bx, nsets), 256, 0, st>>>(sets_dev, A, err_flag);
-    k_prep_scan<<<nsets, 32, 0, st>>>(sets_dev, ntiles, A.psub);
+    k_prep_scan<<<nsets, 1024, 0, st>>>(sets_dev, ncells, tcells, A.psub);
     k_prep_scatter<<<dim3(bx, nsets), 256, 0, st>>>(sets_dev, d);
     return cudaGetLastError();
 }

@@ -44,7 +44,7 @@ void set_cuda_error(cudaError_t e, const char* what) {
         if (_r != MOT_OK) return _r;             \
     } while (0)
 
-int max_grid(int d) { return d == 1 ? 4096 : 128; }
+int max_grid(int d) { return d == 1 ? 4096 : (d == 2 ? 128 : 64); }
 
 GridChoice choose_grid(int d, double R, double eta_min, double eta_max, int n_grid_opt, double epsB) {
     GridChoice g;
@@ -173,8 +173,8 @@ void layout_set(Arena& A, SetBufs& S, int n, int d, int n_grid, bool with_mu) {
     }
     S.u_tmp = A.take<float>((size_t)d * n);
     S.tile_of = A.take<int>(n);
-    S.counts = A.take<int>(ntiles);
-    S.cursor = A.take<int>(ntiles);
+    S.counts = A.take<int>(mot_ncells(d, n_grid));
+    S.cursor = A.take<int>(mot_ncells(d, n_grid));
 }
 
 PointSet pointset_of(const SetBufs& S) {
