@@ -144,13 +144,25 @@ __global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, 
         RunSpread<D> rs;
         rs.init(lane);
         int cur = -1;
-        for (int j = j0; j < j1; ++j) {
-            const float v = T.alpha ? T.alpha[j] : eval_prod(fc, j);
+        for (int jb = j0; jb < j1; jb += 32) {
+          // coalesced prefetch of 32 points, then broadcast one at a time
+          const int jl = jb + lane;
+          float pv = 0.f, pu[D];
+#pragma unroll
+          for (int t = 0; t < D; ++t) pu[t] = 0.f;
+          if (jl < j1) {
+              pv = T.alpha ? T.alpha[jl] : eval_prod(fc, jl);
+#pragma unroll
+              for (int t = 0; t < D; ++t) pu[t] = T.src.u[t * N + jl];
+          }
+          const int cnt = min(32, j1 - jb);
+          for (int k = 0; k < cnt; ++k) {
+            const float v = __shfl_sync(0xffffffffu, pv, k);
             float f[D];
             int base = 0, stride = 1;
 #pragma unroll
             for (int t = 0; t < D; ++t) {
-                const float u = T.src.u[t * N + j];
+                const float u = __shfl_sync(0xffffffffu, pu[t], k);
                 const float fl = floorf(u);
                 f[t] = u - fl;
                 base += ((int)fl - MOT_WHALF - o[t]) * stride;
@@ -168,6 +180,7 @@ __global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, 
                 cur = base;
             }
             rs.add(v, rs.lane_weight(cw, f));
+          }
         }
         if (cur >= 0) {
 #pragma unroll
@@ -354,9 +367,18 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
             RunSpread<2> rs;
             rs.init(lane);
             int cur = -1, clx = 0, cly = 0;
-            for (int j = w0; j < w1; ++j) {
-                const float v = T.alpha ? T.alpha[j] : eval_prod(fc, j);
-                const float ux = T.src.u[j], uy = T.src.u[Ns + j];
+            for (int jb = w0; jb < w1; jb += 32) {
+              const int jl = jb + lane;
+              float pv = 0.f, px = 0.f, py = 0.f;
+              if (jl < w1) {
+                  pv = T.alpha ? T.alpha[jl] : eval_prod(fc, jl);
+                  px = T.src.u[jl];
+                  py = T.src.u[Ns + jl];
+              }
+              const int cnt = min(32, w1 - jb);
+              for (int k = 0; k < cnt; ++k) {
+                const float v = __shfl_sync(0xffffffffu, pv, k);
+                const float ux = __shfl_sync(0xffffffffu, px, k), uy = __shfl_sync(0xffffffffu, py, k);
                 const float fx = floorf(ux), fy = floorf(uy);
                 const int lx = (int)fx - MOT_WHALF, ly = (int)fy - MOT_WHALF;
                 const int key = ((ly & mask) << 8) | (lx & mask);
@@ -373,6 +395,7 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
                 }
                 const float f[2] = {ux - fx, uy - fy};
                 rs.add(v, rs.lane_weight(cw, f));
+              }
             }
             if (cur >= 0) {
 #pragma unroll
@@ -384,10 +407,19 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
         // ---- 2. reduce owned rows, DFT along x (4 lanes per output) ---------------------
         const int R = n / CS;
         const int y0 = r * R;
-        for (int i = tid; i < R * n; i += nt) {
-            float s = 0.f;
-            for (int q = 0; q < CS; ++q) s += cluster.map_shared_rank(Gs, q)[y0 * n + i];
-            Grow[i] = s;
+        {
+            const float* peer[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) peer[q] = cluster.map_shared_rank(Gs, q < CS ? q : 0);
+            for (int i = tid; i < R * n; i += nt) {
+                float part[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) part[q] = q < CS ? peer[q][y0 * n + i] : 0.f;
+                float s = 0.f;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) s += part[q];
+                Grow[i] = s;
+            }
         }
         __syncthreads();
         {
@@ -492,10 +524,21 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
         }
         cluster.sync();
         // ---- 5. copy h, interpolate (one thread per target) ------------------------------
-        for (int i = tid; i < n * n; i += nt) {
-            const int y = i / n;
-            const int owner = y / R;
-            Gs[i] = cluster.map_shared_rank(Hrow, owner)[(y - owner * R) * n + (i - y * n)];
+        for (int i0 = tid; i0 < n * n; i0 += 4 * nt) {
+            float vals[4];
+#pragma unroll
+            for (int u4 = 0; u4 < 4; ++u4) {
+                const int i = i0 + u4 * nt;
+                vals[u4] = 0.f;
+                if (i < n * n) {
+                    const int y = i / n;
+                    const int owner = y / R;
+                    vals[u4] = cluster.map_shared_rank(Hrow, owner)[(y - owner * R) * n + (i - y * n)];
+                }
+            }
+#pragma unroll
+            for (int u4 = 0; u4 < 4; ++u4)
+                if (i0 + u4 * nt < n * n) Gs[i0 + u4 * nt] = vals[u4];
         }
         cluster.sync();      // peers may now leave; Hrow of this CTA is no longer read
         const int Nt = T.tgt.n;
