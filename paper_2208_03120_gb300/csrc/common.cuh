@@ -112,9 +112,10 @@ __device__ __forceinline__ double ls_of(const VecScale* s, int use_prev) {
     return use_prev ? s->ls_prev : s->ls;
 }
 
-// Normalised log-scale of one factor: ls + log(mx), signed by inv.
+// Normalised log-scale of one factor: ls + log(mx), signed by inv (log of the FP32 maximum in
+// FP32: its rounding is that of the FP32 mantissas themselves).
 __device__ __forceinline__ double factor_L(const Factor& f) {
-    double L = ls_of(f.sc, f.use_prev) + log((double)mx_of(f.sc, f.use_prev));
+    double L = ls_of(f.sc, f.use_prev) + (double)logf(mx_of(f.sc, f.use_prev));
     return f.inv ? -L : L;
 }
 

@@ -91,17 +91,20 @@ __global__ void __launch_bounds__(256) k_epi(const Task* __restrict__ tasks, Glo
     __shared__ Task T;
     __shared__ FacCache tf;
     __shared__ double sLsrc;
+    __shared__ EpiConst sC;
     if (threadIdx.x == 0) T = tasks[blockIdx.y];
     __syncthreads();
     load_factors(tf, G.fac, T.tf0, T.tnf);
-    if (threadIdx.x == 0) {
-        double L = 0.0;
-        if (T.alpha == nullptr)
-            for (int f = 0; f < T.snf; ++f) L += factor_L(G.fac[T.sf0 + f]);
-        sLsrc = L;
+    if (threadIdx.x < 32) {
+        const double L = T.alpha == nullptr ? factors_L_warp(G.fac, T.sf0, T.snf) : 0.0;
+        if (threadIdx.x == 0) {
+            sLsrc = L;
+            epi_prepare(T, tf, L, sC);
+        }
     }
     __syncthreads();
     const double Lsrc = sLsrc;
+    const EpiConst C = sC;
     EpiPartial ep;
     epi_zero(ep);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.tgt.n; i += gridDim.x * blockDim.x) {
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(256) k_epi(const Task* __restrict__ tasks, Glo
             raw = T.raw[i];
             T.raw[i] = 0.f;
         }
-        epilogue_point(T, tf, Lsrc, G.floor_, i, raw, ep);
+        epilogue_point(T, tf, C, G.floor_, i, raw, ep);
     }
     epi_block_finish(T, G, tf, Lsrc, ep);
 }

@@ -21,6 +21,13 @@ struct FacCache {
     double L;           // log-scale of the normalised product
 };
 
+// Log-scale of a factor list, summed by warp 0 (lanes in parallel); valid on lane 0.
+__device__ __forceinline__ double factors_L_warp(const Factor* F, int f0, int nf) {
+    double L = 0.0;
+    for (int t = threadIdx.x; t < nf; t += 32) L += factor_L(F[f0 + t]);
+    return warp_sum_d(L);
+}
+
 __device__ __forceinline__ void load_factors(FacCache& fc, const Factor* F, int f0, int nf) {
     for (int t = threadIdx.x; t < nf; t += blockDim.x) {
         Factor f = F[f0 + t];
@@ -28,14 +35,23 @@ __device__ __forceinline__ void load_factors(FacCache& fc, const Factor* F, int 
         fc.scale[t] = 1.f / mx_of(f.sc, f.use_prev);
         fc.inv[t] = f.inv;
     }
-    if (threadIdx.x == 0) {
-        double L = 0.0;
-        for (int t = 0; t < nf; ++t) L += factor_L(F[f0 + t]);
-        fc.nf = nf;
-        fc.L = L;
+    if (threadIdx.x < 32) {
+        const double L = factors_L_warp(F, f0, nf);
+        if (threadIdx.x == 0) {
+            fc.nf = nf;
+            fc.L = L;
+        }
     }
     __syncthreads();
 }
+
+// Per-block constants of an epilogue (computed once by thread 0, read by all threads).
+struct EpiConst {
+    double lsphi;      // log-scale of the scalings written (EPI_PHI / EPI_ROOT)
+    double E;          // exp(total log-scale) of P_i = raw_i T_i e^{L} (EPI_MARG / EPI_ROOT)
+    double ls_phi_k;   // log-scale of the node's current scaling (EPI_MARG)
+    float inv_mx_old;  // 1 / mx of the previous root scaling (EPI_ROOT)
+};
 
 __device__ __forceinline__ float eval_prod(const FacCache& fc, int i) {
     float v = 1.f;
@@ -83,9 +99,24 @@ __device__ __forceinline__ double phi_logscale(const Task& T, const FacCache& tf
     return T.mode == EPI_ROOT ? -tf.L : -(Lsrc + tf.L);
 }
 
-__device__ __forceinline__ void epilogue_point(const Task& T, const FacCache& tf, double Lsrc,
+// Thread 0: fill the per-block constants (the only FP64 transcendentals of an epilogue).
+__device__ __forceinline__ void epi_prepare(const Task& T, const FacCache& tf, double Lsrc, EpiConst& C) {
+    C.lsphi = phi_logscale(T, tf, Lsrc);
+    C.E = 1.0;
+    C.ls_phi_k = 0.0;
+    C.inv_mx_old = 1.f;
+    if (T.mode == EPI_MARG) {
+        C.E = exp(Lsrc + tf.L);
+        C.ls_phi_k = ls_of(T.phi_sc, 0);
+    } else if (T.mode == EPI_ROOT) {
+        const double Lold = ls_of(T.phi_sc, 1) + (double)logf(mx_of(T.phi_sc, 1));
+        C.E = exp(Lold + tf.L);
+        C.inv_mx_old = 1.f / mx_of(T.phi_sc, 1);
+    }
+}
+
+__device__ __forceinline__ void epilogue_point(const Task& T, const FacCache& tf, const EpiConst& C,
                                                float floor_, int i, float raw, EpiPartial& ep) {
-    const double lsphi = phi_logscale(T, tf, Lsrc);
     switch (T.mode) {
     case EPI_RAW:
         T.out[i] = raw;
@@ -101,11 +132,12 @@ __device__ __forceinline__ void epilogue_point(const Task& T, const FacCache& tf
         float g = raw;
         if (!(g >= floor_)) { g = floor_; ep.clamps++; }
         if (T.out) T.out[i] = g;
-        float t = eval_prod(tf, i);
-        float ph = T.mu_f[i] / (g * t);
+        const float t = eval_prod(tf, i);
+        const float ph = T.mu_f[i] / (g * t);
         T.phi[i] = ph;
         ep.mx_phi = fmaxf(ep.mx_phi, ph);
-        if (T.mu_d[i] > 0.0) ep.logphi += T.mu_d[i] * (log((double)ph) + lsphi);
+        const double m = T.mu_d[i];
+        if (m > 0.0) ep.logphi += m * ((double)logf(ph) + C.lsphi);
         break;
     }
     case EPI_PHI_FREE:
@@ -120,19 +152,19 @@ __device__ __forceinline__ void epilogue_point(const Task& T, const FacCache& tf
         break;
     case EPI_ROOT: {
         // mass and violation of the last iterate (scale record prev), then the update
-        float t = eval_prod(tf, i);
-        double Lold = ls_of(T.phi_sc, 1) + log((double)mx_of(T.phi_sc, 1));
-        float old = T.phi[i] / mx_of(T.phi_sc, 1);
-        double P = (double)old * (double)t * exp(Lold + tf.L);
+        const float t = eval_prod(tf, i);
+        const float old = T.phi[i] * C.inv_mx_old;
+        const double P = (double)(old * t) * C.E;
         ep.mass += P;
         if (T.free_node) {
             ep.mx_phi = 1.f;
         } else {
             ep.viol += fabs(P - T.mu_d[i]);
-            float ph = T.mu_f[i] / t;
+            const float ph = T.mu_f[i] / t;
             T.phi[i] = ph;
             ep.mx_phi = fmaxf(ep.mx_phi, ph);
-            if (T.mu_d[i] > 0.0) ep.logphi += T.mu_d[i] * (log((double)ph) + lsphi);
+            const double m = T.mu_d[i];
+            if (m > 0.0) ep.logphi += m * ((double)logf(ph) + C.lsphi);
         }
         break;
     }
@@ -141,11 +173,11 @@ __device__ __forceinline__ void epilogue_point(const Task& T, const FacCache& tf
         if (!(g >= floor_)) { g = floor_; ep.clamps++; }
         if (T.out) T.out[i] = g;
         ep.mx_out = fmaxf(ep.mx_out, g);
-        float t = eval_prod(tf, i);            // phi^k and the children's messages
-        double P = (double)g * (double)t * exp(Lsrc + tf.L);
+        const float t = eval_prod(tf, i);            // phi^k and the children's messages
+        const double P = (double)(g * t) * C.E;
         ep.mass += P;
         if (T.mu_d) ep.viol += fabs(P - T.mu_d[i]);
-        if (P > 0.0) ep.plogphi += P * (log((double)T.phi[i]) + ls_of(T.phi_sc, 0));
+        if (P > 0.0) ep.plogphi += P * ((double)logf(T.phi[i]) + C.ls_phi_k);
         break;
     }
     default:

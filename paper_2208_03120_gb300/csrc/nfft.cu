@@ -206,25 +206,28 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
     __shared__ Task T;
     __shared__ FacCache tf;
     __shared__ double sLsrc;
+    __shared__ EpiConst sC;
     extern __shared__ float tile[];
     if (threadIdx.x == 0) T = tasks[blockIdx.y];
     __syncthreads();
     load_factors(tf, G.fac, T.tf0, T.tnf);
-    if (threadIdx.x == 0) {
-        double L = 0.0;
-        if (T.alpha == nullptr)
-            for (int f = 0; f < T.snf; ++f) L += factor_L(G.fac[T.sf0 + f]);
-        sLsrc = L;
+    if (threadIdx.x < 32) {
+        const double L = T.alpha == nullptr ? factors_L_warp(G.fac, T.sf0, T.snf) : 0.0;
+        if (threadIdx.x == 0) {
+            sLsrc = L;
+            epi_prepare(T, tf, L, sC);
+        }
     }
     __syncthreads();
     const double Lsrc = sLsrc;
+    const EpiConst C = sC;
     EpiPartial ep;
     epi_zero(ep);
 
     if (T.hgrid == nullptr) {
         // node step without a kernel product (root update / root marginal)
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.tgt.n; i += gridDim.x * blockDim.x)
-            epilogue_point(T, tf, Lsrc, G.floor_, i, 1.f, ep);
+            epilogue_point(T, tf, C, G.floor_, i, 1.f, ep);
     } else {
         const int n = G.n_grid;
         const int TS = mot_tile_size(D, n), P = TS + MOT_W - 1, ntd = n / TS;
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
                         for (int q = 0; q < MOT_W - 1; ++q) w[D - 1][q] = w[D - 1][q + 1];
                     }
                 }
-                epilogue_point(T, tf, Lsrc, G.floor_, j, acc, ep);
+                epilogue_point(T, tf, C, G.floor_, j, acc, ep);
             }
             __syncthreads();
         }
@@ -322,6 +325,7 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
     __shared__ Task T;
     __shared__ FacCache fc, tf;
     __shared__ double sLsrc;
+    __shared__ EpiConst sC;
     __shared__ float Gs[F2_N * F2_N];
     __shared__ float Grow[F2_MAXR * F2_N];
     __shared__ float2 Gx[F2_MAXR * (F2_M + 1)];
@@ -343,7 +347,10 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
     if (r == 0 && tid == 0) task_resets(T, G, 0);
     if (T.alpha == nullptr) load_factors(fc, G.fac, T.sf0, T.snf);
     load_factors(tf, G.fac, T.tf0, T.tnf);
-    if (tid == 0) sLsrc = T.alpha == nullptr ? fc.L : 0.0;
+    if (tid == 0) {
+        sLsrc = T.alpha == nullptr ? fc.L : 0.0;
+        epi_prepare(T, tf, sLsrc, sC);
+    }
     const int n = G.n_grid, M = G.M, mask = n - 1;
     const bool fast = T.hgrid != nullptr;
     for (int i = tid; i < n * n; i += nt) Gs[i] = 0.f;
@@ -356,6 +363,7 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
     EpiPartial ep;
     epi_zero(ep);
     const double Lsrc = sLsrc;
+    const EpiConst C = sC;
 
     if (fast) {
         // ---- 1. spread: warps walk contiguous runs of cell-sorted points ----------------------
@@ -559,14 +567,14 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
                 for (int a = 0; a < MOT_W; ++a) s2 = fmaf(row[(lx + a) & mask], wx[a], s2);
                 acc = fmaf(s2, wy[b], acc);
             }
-            epilogue_point(T, tf, Lsrc, G.floor_, i, acc, ep);
+            epilogue_point(T, tf, C, G.floor_, i, acc, ep);
         }
     } else {
         // node step without a kernel product; the cluster barrier orders the reset above
         cluster.sync();
         const int Nt = T.tgt.n;
         const int i0 = (int)((long long)r * Nt / CS), i1 = (int)((long long)(r + 1) * Nt / CS);
-        for (int i = i0 + tid; i < i1; i += nt) epilogue_point(T, tf, Lsrc, G.floor_, i, 1.f, ep);
+        for (int i = i0 + tid; i < i1; i += nt) epilogue_point(T, tf, C, G.floor_, i, 1.f, ep);
     }
     epi_block_finish(T, G, tf, Lsrc, ep);
 }
