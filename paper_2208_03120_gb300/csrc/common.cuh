@@ -144,3 +144,11 @@ __device__ __forceinline__ int wrap_idx(int l, int n) {
     l %= n;
     return l < 0 ? l + n : l;
 }
+
+// Copy a task descriptor into shared memory with all threads of the block (word by word).
+__device__ __forceinline__ void load_task(Task& dst, const Task* src) {
+    static_assert(sizeof(Task) % 4 == 0, "Task is copied in 32-bit words");
+    const unsigned int* s = reinterpret_cast<const unsigned int*>(src);
+    unsigned int* d = reinterpret_cast<unsigned int*>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(Task) / 4); i += blockDim.x) d[i] = __ldg(s + i);
+}

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(DENSE_TPB) k_dense(const Task* __restrict__ ta
     __shared__ FacCache fc;
     __shared__ float s_u[D][DENSE_CHUNK];
     __shared__ float s_v[DENSE_CHUNK];
-    if (threadIdx.x == 0) T = tasks[blockIdx.y];
+    load_task(T, tasks + blockIdx.y);
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) task_resets(T, G, 0);
     if (T.alpha == nullptr) load_factors(fc, G.fac, T.sf0, T.snf);
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) k_epi(const Task* __restrict__ tasks, Glo
     __shared__ FacCache tf;
     __shared__ double sLsrc;
     __shared__ EpiConst sC;
-    if (threadIdx.x == 0) T = tasks[blockIdx.y];
+    load_task(T, tasks + blockIdx.y);
     __syncthreads();
     load_factors(tf, G.fac, T.tf0, T.tnf);
     if (threadIdx.x < 32) {

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, 
     __shared__ FacCache fc;
     __shared__ float cw[MOT_W][MOT_WDEG + 1];
     extern __shared__ float tile[];
-    if (threadIdx.x == 0) T = tasks[blockIdx.y];
+    load_task(T, tasks + blockIdx.y);
     for (int i = threadIdx.x; i < MOT_W * (MOT_WDEG + 1); i += blockDim.x) (&cw[0][0])[i] = (&c_win[0][0])[i];
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) task_resets(T, G, 0);
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
     __shared__ double sLsrc;
     __shared__ EpiConst sC;
     extern __shared__ float tile[];
-    if (threadIdx.x == 0) T = tasks[blockIdx.y];
+    load_task(T, tasks + blockIdx.y);
     __syncthreads();
     load_factors(tf, G.fac, T.tf0, T.tnf);
     if (threadIdx.x < 32) {
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
     for (int i = tid; i < MOT_W * (MOT_WDEG + 1); i += nt) (&cw[0][0])[i] = (&c_win[0][0])[i];
     const int CS = (int)cluster.num_blocks();
     const int r = (int)cluster.block_rank();
-    if (tid == 0) T = tasks[blockIdx.y];
+    load_task(T, tasks + blockIdx.y);
     __syncthreads();
     if (r == 0 && tid == 0) task_resets(T, G, 0);
     if (T.alpha == nullptr) load_factors(fc, G.fac, T.sf0, T.snf);
