@@ -57,6 +57,7 @@ enum EpiMode : int {
     EPI_MARG = 3,      // store raw as message; P_i = raw_i T_i e^{L}; accumulate violation
     EPI_ROOT = 4,      // raw = 1: mass / root violation from the last iterate, then phi update
     EPI_PHI_FREE = 5,  // phi_i = 1 (node without marginal constraint)
+    EPI_CROOT = 6,     // circle root: mass / violation of the last iterate from raw, phi = mu / raw
 };
 
 // Accumulators of one iteration (FP64).

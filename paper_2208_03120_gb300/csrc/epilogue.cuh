@@ -96,6 +96,7 @@ __device__ __forceinline__ void task_resets(const Task& T, const Globals& G, int
 // lsphi: log-scale of the scaling written by EPI_PHI (-(Lsrc + tf.L)) or EPI_ROOT (-tf.L).
 __device__ __forceinline__ double phi_logscale(const Task& T, const FacCache& tf, double Lsrc) {
     if (T.mode == EPI_PHI_FREE || (T.mode == EPI_ROOT && T.free_node)) return 0.0;
+    if (T.mode == EPI_CROOT) return -Lsrc;
     return T.mode == EPI_ROOT ? -tf.L : -(Lsrc + tf.L);
 }
 
@@ -108,9 +109,9 @@ __device__ __forceinline__ void epi_prepare(const Task& T, const FacCache& tf, d
     if (T.mode == EPI_MARG) {
         C.E = exp(Lsrc + tf.L);
         C.ls_phi_k = ls_of(T.phi_sc, 0);
-    } else if (T.mode == EPI_ROOT) {
+    } else if (T.mode == EPI_ROOT || T.mode == EPI_CROOT) {
         const double Lold = ls_of(T.phi_sc, 1) + (double)logf(mx_of(T.phi_sc, 1));
-        C.E = exp(Lold + tf.L);
+        C.E = exp(Lold + (T.mode == EPI_ROOT ? tf.L : Lsrc));
         C.inv_mx_old = 1.f / mx_of(T.phi_sc, 1);
     }
 }
@@ -168,6 +169,21 @@ __device__ __forceinline__ void epilogue_point(const Task& T, const FacCache& tf
         }
         break;
     }
+    case EPI_CROOT: {
+        // raw = sum over the root's column of the circle product (normalised factors)
+        const float old = T.phi[i] * C.inv_mx_old;
+        const double P = (double)(old * raw) * C.E;
+        ep.mass += P;
+        ep.viol += fabs(P - T.mu_d[i]);
+        float g = raw;
+        if (!(g >= floor_)) { g = floor_; ep.clamps++; }
+        const float ph = T.mu_f[i] / g;
+        T.phi[i] = ph;
+        ep.mx_phi = fmaxf(ep.mx_phi, ph);
+        const double m = T.mu_d[i];
+        if (m > 0.0) ep.logphi += m * ((double)logf(ph) + C.lsphi);
+        break;
+    }
     case EPI_MARG: {
         float g = raw;
         if (!(g >= floor_)) { g = floor_; ep.clamps++; }
@@ -216,13 +232,13 @@ __device__ __forceinline__ void epi_block_finish(const Task& T, const Globals& G
             atomicAdd(T.acc_node + 1, pl);
             atomicAdd(T.acc_node + 2, m);
         }
-        if (T.mode == EPI_PHI || T.mode == EPI_ROOT || T.mode == EPI_PHI_FREE) {
+        if (T.mode == EPI_PHI || T.mode == EPI_ROOT || T.mode == EPI_PHI_FREE || T.mode == EPI_CROOT) {
             T.phi_sc->ls = phi_logscale(T, tf, Lsrc);
             atomic_max_pos(&T.phi_sc->mx_bits, b);
             int it = *G.iter;
             IterAcc* nxt = G.acc + ((it + 1) % G.R);
             if (l != 0.0) atomicAdd(&nxt->logphi, l);
-            if (T.mode == EPI_ROOT) {
+            if (T.mode == EPI_ROOT || T.mode == EPI_CROOT) {
                 IterAcc* cur = G.acc + (it % G.R);
                 atomicAdd(&cur->mass, m);
                 atomicAdd(&cur->rootviol, v);

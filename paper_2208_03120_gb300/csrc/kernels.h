@@ -87,3 +87,15 @@ cudaError_t launch_init_phi(float* phi, VecScale* sc, const int* perm, const dou
 // Scatter a plain vector into sorted order and back.
 cudaError_t launch_permute_in(const float* src, const int* perm, int n, float* dst, cudaStream_t st);
 cudaError_t launch_permute_out(const float* src, const int* perm, int n, float* dst, cudaStream_t st);
+
+// ---- circle structure (circle.cu) --------------------------------------------------------
+#include <algorithm>
+// raw[i] += sum_c B[c][i] G[c][i] phi[c] over normalised factors (raw zeroed by the caller).
+cudaError_t launch_rowdot(const float* B, const VecScale* sB, const float* G, const VecScale* sG, const float* phi,
+                          const VecScale* sP, int ni, int nc, float* raw, cudaStream_t st);
+// raw[c] = sum_j A[c][j] B[c][j] phi[j] over normalised factors.
+cudaError_t launch_colsum(const float* A, const VecScale* sA, const float* B, const VecScale* sB, const float* phi,
+                          const VecScale* sP, int nj, int nc, float* raw, cudaStream_t st);
+// K[c][i] = exp(-||u_i - u_c||^2 / eta_u) (column-major, grid units); scale record ls = 0, mx = 1.
+cudaError_t launch_kernel_matrix(const float* ui, int ni, const float* uc, int nc, int d, float eta_u, float* K,
+                                 VecScale* sc, cudaStream_t st);

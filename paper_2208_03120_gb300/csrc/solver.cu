@@ -985,6 +985,546 @@ int tree_solve(const mot_problem* P, const mot_options& o, void* ws, size_t ws_b
     return status;
 }
 
+
+// =============================================================================================
+// circle plan (Algorithm 3)
+// =============================================================================================
+//
+// Nodes 0..K-1 with edges {k, k+1 mod K} (edge k).  beta_k (k = 1..K-1) and Gam_k = gamma_k^T
+// (k = 1..K-1) are n_k x n_0 matrices stored column by column (column c = point c of node 0).
+// beta_{K-1} = K^{(K-1,0)} and Gam_1 = K^{(1,0)} are fixed dense kernel matrices; the others are
+// batches of kernel matrix-vector products, one per column:
+//   Gam_k[c]  = K^{(k,k-1)} (phi^{k-1} (.) Gam_{k-1}[c]),  k = 2..K-1   (forward)
+//   beta_k[c] = K^{(k,k+1)} (phi^{k+1} (.) beta_{k+1}[c]), k = K-2..1   (backward)
+// phi^0_c = mu^0_c / sum_j Gam_1[c][j] phi^1_j beta_1[c][j]  (column sums)
+// phi^k_i = mu^k_i / sum_c beta_k[c][i] phi^0_c Gam_k[c][i]   (row dots), k = 1..K-1.
+struct CBatch {
+    int s = 0, t = 0, edge = 0;
+    std::vector<Task> tasks;
+    Task* d_tasks = nullptr;
+    VecScale* out_sc = nullptr;
+    int grid_src = 1, grid_tgt = 1, ntb = 1, nsplit = 1;
+};
+
+struct CirclePlan {
+    int K = 0, d = 0, path = MOT_PATH_NFFT, n0 = 0, CB = 1;
+    double eta = 0.0;
+    std::vector<double> w;          // edge weights, edge k = {k, k+1 mod K}
+    std::vector<int> n;
+    GridChoice g;
+    mot_options o;
+    std::vector<SetBufs> sets;
+    std::vector<float*> phi, beta, gam, raw, D;
+    std::vector<float*> grid, hgrid, rawm;   // per column slot of a chunk
+    std::vector<float2*> spec;
+    VecScale* sc = nullptr;         // [4K]: phi, beta, gam, raw
+    IterAcc* acc = nullptr;
+    int* iter = nullptr;
+    double* acc_node = nullptr;
+    int* err = nullptr;
+    Factor* d_fac = nullptr;
+    size_t fac_cap = 0;
+    VecScale** d_resets = nullptr;
+    Task* d_tasks = nullptr;
+    size_t task_cap = 0;
+    PrepSet* d_sets = nullptr;
+    float* box_scratch = nullptr;
+    float* box_out = nullptr;
+    double* dscr_a = nullptr;
+    double* dscr_b = nullptr;
+    char* stats_begin = nullptr;
+    size_t stats_bytes = 0;
+    std::vector<Factor> fac;
+    std::vector<VecScale*> resets;
+    size_t it_r0 = 0, it_rn = 0, bw_r0 = 0, bw_rn = 0, ck_r0 = 0, ck_rn = 0;
+    std::vector<CBatch> fwd, bwd;   // fwd[k] produces Gam_k (k >= 2); bwd[k] produces beta_k (k <= K-2)
+    std::vector<Task> node_tasks;   // [0] root update, [1..K-1] phi^k updates, [K..2K-1] check marginals
+    Task* d_node = nullptr;
+    Globals G;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_iters = 0;
+    long long launches_per_iter = 0;
+
+    VecScale* phi_sc(int k) const { return sc + k; }
+    VecScale* beta_sc(int k) const { return sc + K + k; }
+    VecScale* gam_sc(int k) const { return sc + 2 * K + k; }
+    VecScale* raw_sc(int k) const { return sc + 3 * K + k; }
+};
+
+void layout_circle(Arena& A, CirclePlan& C) {
+    const int K = C.K, d = C.d, ng = C.g.n, M = C.g.M;
+    const bool nfft = C.path == MOT_PATH_NFFT;
+    size_t gsz = 1;
+    for (int t = 0; t < d; ++t) gsz *= ng;
+    int nmax = 0;
+    for (int k = 0; k < K; ++k) nmax = std::max(nmax, C.n[k]);
+    C.sets.assign(K, SetBufs());
+    for (int k = 0; k < K; ++k) layout_set(A, C.sets[k], C.n[k], d, ng, true);
+    C.phi.assign(K, nullptr);
+    C.raw.assign(K, nullptr);
+    C.beta.assign(K, nullptr);
+    C.gam.assign(K, nullptr);
+    C.D.assign(K, nullptr);
+    for (int k = 0; k < K; ++k) {
+        C.phi[k] = A.take<float>(C.n[k]);
+        C.raw[k] = A.take<float>(C.n[k]);
+    }
+    for (int k = 1; k < K; ++k) {
+        C.beta[k] = A.take<float>((size_t)C.n[k] * C.n0);
+        C.gam[k] = A.take<float>((size_t)C.n[k] * C.n0);
+    }
+    C.grid.assign(C.CB, nullptr);
+    C.hgrid.assign(C.CB, nullptr);
+    C.spec.assign(C.CB, nullptr);
+    C.rawm.assign(C.CB, nullptr);
+    for (int c = 0; c < C.CB; ++c) {
+        if (nfft) {
+            C.grid[c] = A.take<float>(gsz);
+            C.hgrid[c] = A.take<float>(gsz);
+            if (d == 3) C.spec[c] = A.take<float2>((size_t)ng * (2 * M + 1) * (M + 1));
+        } else {
+            C.rawm[c] = A.take<float>(nmax);
+        }
+    }
+    if (nfft)
+        for (int k = 0; k < K; ++k) C.D[k] = A.take<float>(D_floats(d, M));
+    size_t stats = sizeof(IterAcc) * kRing + sizeof(double) * 3 * K + sizeof(VecScale) * 4 * K + 16;
+    C.stats_begin = A.take<char>(stats);
+    C.stats_bytes = stats;
+    if (!A.measure) {
+        C.acc = reinterpret_cast<IterAcc*>(C.stats_begin);
+        C.acc_node = reinterpret_cast<double*>(C.stats_begin + sizeof(IterAcc) * kRing);
+        C.sc = reinterpret_cast<VecScale*>(C.stats_begin + sizeof(IterAcc) * kRing + sizeof(double) * 3 * K);
+        C.err = reinterpret_cast<int*>(C.stats_begin + stats - 16);
+        C.iter = C.err + 1;
+    }
+    C.d_sets = A.take<PrepSet>(K);
+    C.box_scratch = A.take<float>(8);
+    C.box_out = A.take<float>(8);
+    if (nfft) {
+        size_t sd = make_D_scratch_doubles(d, M);
+        C.dscr_a = A.take<double>(sd);
+        C.dscr_b = A.take<double>(sd);
+    }
+    C.fac_cap = (size_t)4 * K * C.n0 + 16 * (size_t)K + 64;
+    C.d_fac = A.take<Factor>(C.fac_cap);
+    C.d_resets = A.take<VecScale*>(8 * (size_t)K + 8);
+    C.task_cap = (size_t)2 * K * C.n0 + 4 * (size_t)K + 8;
+    C.d_tasks = A.take<Task>(C.task_cap);
+}
+
+int c_add_factor(CirclePlan& C, const float* mant, const VecScale* sc) {
+    Factor f;
+    f.mant = mant;
+    f.sc = sc;
+    f.inv = 0;
+    f.use_prev = 0;
+    C.fac.push_back(f);
+    return (int)C.fac.size() - 1;
+}
+
+// Batch of column products: Y = K^{(t,s)} (phi^s (.) X), X = mats[s] (n_s x n0), Y = mats[t].
+void c_build_batch(CirclePlan& C, CBatch& B, int s, int t, int edge, float* X, VecScale* sX, float* Y, VecScale* sY) {
+    B.s = s;
+    B.t = t;
+    B.edge = edge;
+    B.out_sc = sY;
+    B.tasks.clear();
+    const double eta_n = (C.eta / C.w[edge]) / (C.g.s * C.g.s);
+    for (int c = 0; c < C.n0; ++c) {
+        Task tk = blank_task();
+        tk.src = pointset_of(C.sets[s]);
+        tk.sf0 = (int)C.fac.size();
+        c_add_factor(C, C.phi[s], C.phi_sc(s));
+        c_add_factor(C, X + (size_t)c * C.n[s], sX);
+        tk.snf = 2;
+        const int slot = c % C.CB;
+        tk.grid = C.grid[slot];
+        tk.hgrid = C.hgrid[slot];
+        tk.spec = C.spec[slot];
+        tk.D = C.D[edge];
+        tk.raw = C.rawm[slot];
+        tk.eta_u = (float)(eta_n * (double)C.g.n * (double)C.g.n);
+        tk.tgt = pointset_of(C.sets[t]);
+        tk.mode = EPI_MSG;
+        tk.out = Y + (size_t)c * C.n[t];
+        tk.out_sc = sY;
+        B.tasks.push_back(tk);
+    }
+    int ms = 1, mt = 1;
+    ms = std::max(ms, C.sets[s].maxsub);
+    mt = std::max(mt, C.sets[t].maxsub);
+    B.grid_src = std::min(ms, 1024);
+    B.grid_tgt = C.path == MOT_PATH_NFFT ? std::min(mt, 1024) : std::min((C.n[t] + 255) / 256, 1024);
+    B.ntb = (C.n[t] + 511) / 512;
+    B.nsplit = std::max(1, std::min(64, 4 * 152 / std::max(1, B.ntb * std::min(C.CB, C.n0))));
+}
+
+void c_build(CirclePlan& C) {
+    const int K = C.K;
+    C.fac.clear();
+    C.resets.clear();
+    C.fwd.assign(K, CBatch());
+    C.bwd.assign(K, CBatch());
+    for (int k = 2; k < K; ++k)
+        c_build_batch(C, C.fwd[k], k - 1, k, k - 1, C.gam[k - 1], C.gam_sc(k - 1), C.gam[k], C.gam_sc(k));
+    for (int k = K - 2; k >= 1; --k)
+        c_build_batch(C, C.bwd[k], k + 1, k, k, C.beta[k + 1], C.beta_sc(k + 1), C.beta[k], C.beta_sc(k));
+    // node tasks (k_epi): raw = row dots / column sums
+    C.node_tasks.assign(2 * K, blank_task());
+    for (int k = 0; k < K; ++k) {
+        for (int pass = 0; pass < 2; ++pass) {
+            Task t = blank_task();
+            t.tgt = pointset_of(C.sets[k]);
+            t.raw = C.raw[k];
+            t.sf0 = (int)C.fac.size();
+            if (k == 0) {
+                c_add_factor(C, C.gam[1], C.gam_sc(1));
+                c_add_factor(C, C.phi[1], C.phi_sc(1));
+                c_add_factor(C, C.beta[1], C.beta_sc(1));
+            } else {
+                c_add_factor(C, C.beta[k], C.beta_sc(k));
+                c_add_factor(C, C.phi[0], C.phi_sc(0));
+                c_add_factor(C, C.gam[k], C.gam_sc(k));
+            }
+            t.snf = 3;
+            t.phi = C.phi[k];
+            t.phi_sc = C.phi_sc(k);
+            t.mu_f = C.sets[k].mu_f;
+            t.mu_d = C.sets[k].mu_d;
+            if (pass == 0) {
+                t.mode = k == 0 ? EPI_CROOT : EPI_PHI;
+                t.tf0 = (int)C.fac.size();
+                t.tnf = 0;
+            } else {
+                t.mode = EPI_MARG;
+                t.tf0 = (int)C.fac.size();
+                c_add_factor(C, C.phi[k], C.phi_sc(k));
+                t.tnf = 1;
+                t.acc_node = C.acc_node + 3 * k;
+            }
+            C.node_tasks[pass * K + k] = t;
+        }
+    }
+    C.it_r0 = C.resets.size();
+    for (int k = 0; k < K; ++k) C.resets.push_back(C.phi_sc(k));
+    for (int k = 2; k < K; ++k) C.resets.push_back(C.gam_sc(k));
+    C.it_rn = C.resets.size() - C.it_r0;
+    C.bw_r0 = C.resets.size();
+    for (int k = 1; k <= K - 2; ++k) C.resets.push_back(C.beta_sc(k));
+    C.bw_rn = C.resets.size() - C.bw_r0;
+    C.ck_r0 = C.resets.size();
+    for (int k = 2; k < K; ++k) C.resets.push_back(C.gam_sc(k));
+    C.ck_rn = C.resets.size() - C.ck_r0;
+}
+
+int c_upload(CirclePlan& C, cudaStream_t st) {
+    if (C.fac.size() > C.fac_cap) return MOT_EUNSUPPORTED;
+    CK(cudaMemcpyAsync(C.d_fac, C.fac.data(), sizeof(Factor) * C.fac.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(C.d_resets, C.resets.data(), sizeof(VecScale*) * C.resets.size(), cudaMemcpyHostToDevice, st));
+    size_t off = 0;
+    std::vector<Task> all;
+    for (auto* v : {&C.fwd, &C.bwd})
+        for (auto& B : *v) {
+            B.d_tasks = C.d_tasks + off;
+            off += B.tasks.size();
+            all.insert(all.end(), B.tasks.begin(), B.tasks.end());
+        }
+    C.d_node = C.d_tasks + off;
+    all.insert(all.end(), C.node_tasks.begin(), C.node_tasks.end());
+    if (all.size() > C.task_cap) return MOT_EUNSUPPORTED;
+    CK(cudaMemcpyAsync(C.d_tasks, all.data(), sizeof(Task) * all.size(), cudaMemcpyHostToDevice, st));
+    C.G.iter = C.iter;
+    C.G.acc = C.acc;
+    C.G.R = kRing;
+    C.G.floor_ = 1e-30f;
+    C.G.n_grid = C.g.n;
+    C.G.M = C.g.M;
+    C.G.fac = C.d_fac;
+    return MOT_OK;
+}
+
+int c_run_batch(CirclePlan& C, CBatch& B, cudaStream_t st, Timer& tm, long long& nl) {
+    cudaEvent_t e = nullptr;
+    for (int c0 = 0; c0 < C.n0; c0 += C.CB) {
+        const int cnt = std::min(C.CB, C.n0 - c0);
+        const Task* tk = B.d_tasks + c0;
+        if (C.path == MOT_PATH_NFFT) {
+            RET(tm.begin(MOT_K_SPREAD, &e));
+            CK(launch_spread(C.d, tk, cnt, B.grid_src, C.G, st));
+            RET(tm.end(e));
+            int nf = 0;
+            RET(tm.begin(MOT_K_FFTCONV, &e));
+            CK(launch_fftconv(C.d, tk, cnt, C.G, st, &nf));
+            RET(tm.end(e));
+            RET(tm.begin(MOT_K_GATHER, &e));
+            CK(launch_gather(C.d, tk, cnt, B.grid_tgt, C.G, st));
+            RET(tm.end(e));
+            nl += 2 + nf;
+        } else {
+            RET(tm.begin(MOT_K_DENSE, &e));
+            CK(launch_dense(C.d, tk, cnt, B.ntb, B.nsplit, C.G, st));
+            RET(tm.end(e));
+            RET(tm.begin(MOT_K_NODE, &e));
+            CK(launch_epi(C.d, tk, cnt, B.grid_tgt, C.G, st));
+            RET(tm.end(e));
+            nl += 2;
+        }
+    }
+    return MOT_OK;
+}
+
+int c_node(CirclePlan& C, int k, int pass, cudaStream_t st, Timer& tm, long long& nl) {
+    cudaEvent_t e = nullptr;
+    RET(tm.begin(MOT_K_CIRCLE, &e));
+    if (k == 0)
+        CK(launch_colsum(C.gam[1], C.gam_sc(1), C.beta[1], C.beta_sc(1), C.phi[1], C.phi_sc(1), C.n[1], C.n0, C.raw[0],
+                         st));
+    else
+        CK(launch_rowdot(C.beta[k], C.beta_sc(k), C.gam[k], C.gam_sc(k), C.phi[0], C.phi_sc(0), C.n[k], C.n0,
+                         C.raw[k], st));
+    RET(tm.end(e));
+    RET(tm.begin(MOT_K_NODE, &e));
+    CK(launch_epi(C.d, C.d_node + pass * C.K + k, 1, std::min((C.n[k] + 255) / 256, 1024), C.G, st));
+    RET(tm.end(e));
+    nl += 2;
+    return MOT_OK;
+}
+
+int c_backward(CirclePlan& C, cudaStream_t st, Timer& tm, long long& nl) {
+    for (int k = C.K - 2; k >= 1; --k) RET(c_run_batch(C, C.bwd[k], st, tm, nl));
+    return MOT_OK;
+}
+
+int c_iteration(CirclePlan& C, cudaStream_t st, Timer& tm, long long& nl) {
+    cudaEvent_t e = nullptr;
+    RET(tm.begin(MOT_K_NODE, &e));
+    CK(launch_prologue(C.d_resets + C.it_r0, (int)C.it_rn, 1, 1, nullptr, 0, C.G, st));
+    RET(tm.end(e));
+    nl += 1;
+    RET(c_node(C, 0, 0, st, tm, nl));
+    for (int k = 1; k < C.K; ++k) {
+        if (k >= 2) RET(c_run_batch(C, C.fwd[k], st, tm, nl));
+        RET(c_node(C, k, 0, st, tm, nl));
+    }
+    RET(tm.begin(MOT_K_NODE, &e));
+    CK(launch_prologue(C.d_resets + C.bw_r0, (int)C.bw_rn, 0, 0, nullptr, 0, C.G, st));
+    RET(tm.end(e));
+    nl += 1;
+    return c_backward(C, st, tm, nl);
+}
+
+int c_check(CirclePlan& C, cudaStream_t st, Timer& tm, long long& nl) {
+    cudaEvent_t e = nullptr;
+    RET(tm.begin(MOT_K_NODE, &e));
+    CK(launch_prologue(C.d_resets + C.ck_r0, (int)C.ck_rn, 0, 0, C.acc_node, 3 * C.K, C.G, st));
+    RET(tm.end(e));
+    nl += 1;
+    RET(c_node(C, 0, 1, st, tm, nl));
+    for (int k = 1; k < C.K; ++k) {
+        if (k >= 2) RET(c_run_batch(C, C.fwd[k], st, tm, nl));
+        RET(c_node(C, k, 1, st, tm, nl));
+    }
+    return MOT_OK;
+}
+
+int c_run_iterations(CirclePlan& C, int count, cudaStream_t st, Timer& tm, long long& nl, bool graphs) {
+    if (count <= 0) return MOT_OK;
+    if (graphs && !tm.on && st != nullptr) {
+        if (C.gexec == nullptr || C.graph_iters != count) {
+            if (C.gexec) {
+                cudaGraphExecDestroy(C.gexec);
+                C.gexec = nullptr;
+            }
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            long long dummy = 0;
+            int rc = MOT_OK;
+            for (int i = 0; i < count && rc == MOT_OK; ++i) rc = c_iteration(C, st, tm, dummy);
+            cudaError_t ce = cudaStreamEndCapture(st, &graph);
+            if (rc != MOT_OK) return rc;
+            CK(ce);
+            CK(cudaGraphInstantiate(&C.gexec, graph, 0));
+            cudaGraphDestroy(graph);
+            C.graph_iters = count;
+            C.launches_per_iter = dummy / count;
+        }
+        CK(cudaGraphLaunch(C.gexec, st));
+        nl += C.launches_per_iter * count;
+        return MOT_OK;
+    }
+    for (int i = 0; i < count; ++i) RET(c_iteration(C, st, tm, nl));
+    return MOT_OK;
+}
+
+int circle_setup(const mot_problem* P, const mot_options& o, CirclePlan& C, void* ws, size_t ws_bytes, bool measure,
+                 size_t* need, cudaStream_t st) {
+    const int K = P->K;
+    if (K < 3) return MOT_EUNSUPPORTED;
+    if (P->free_nodes)
+        for (int k = 0; k < K; ++k)
+            if (P->free_nodes[k]) return MOT_EUNSUPPORTED;
+    C.K = K;
+    C.d = P->d;
+    C.eta = P->eta;
+    C.path = o.path;
+    C.o = o;
+    if (C.path != MOT_PATH_NFFT && C.path != MOT_PATH_DENSE) return MOT_EUNSUPPORTED;
+    C.n.resize(K);
+    for (int k = 0; k < K; ++k) C.n[k] = (int)P->n[k];
+    C.n0 = C.n[0];
+    C.w.assign(K, 1.0);
+    if (P->edge_w)
+        for (int k = 0; k < K; ++k) C.w[k] = P->edge_w[k];
+    C.CB = C.d == 1 ? C.n0 : (C.d == 2 ? std::min(C.n0, 256) : std::min(C.n0, 16));
+    GridChoice gmax;
+    gmax.n = o.n_grid > 0 ? o.n_grid : max_grid(C.d);
+    gmax.M = gmax.n / 4;
+    C.g = gmax;
+    Arena A;
+    A.measure = measure;
+    A.base = reinterpret_cast<char*>(ws);
+    A.cap = ws_bytes;
+    layout_circle(A, C);
+    if (measure) {
+        *need = A.off + 256;
+        return MOT_OK;
+    }
+    if (A.off > ws_bytes) return MOT_ENOMEM;
+    double emin = 1e300, emax = 0.0;
+    for (int k = 0; k < K; ++k) {
+        emin = std::min(emin, C.eta / C.w[k]);
+        emax = std::max(emax, C.eta / C.w[k]);
+    }
+    std::vector<PrepSet> sets;
+    for (int k = 0; k < K; ++k) sets.push_back(prepset_of(C.sets[k], P->x[k], P->mu[k]));
+    GridChoice g;
+    RET(measure_and_choose(sets, C.d_sets, C.box_scratch, C.box_out, C.d, emin, emax, o, g, st));
+    if (g.n > gmax.n) g.n = gmax.n;
+    g.M = g.n / 4;
+    C.g = g;
+    CK(cudaMemsetAsync(C.stats_begin, 0, C.stats_bytes, st));
+    std::vector<PrepSet> s2;
+    for (int k = 0; k < K; ++k) {
+        C.sets[k].maxsub = (C.n[k] + mot_sub_points(C.d) - 1) / mot_sub_points(C.d) + mot_ntiles(C.d, g.n);
+        s2.push_back(prepset_of(C.sets[k], P->x[k], P->mu[k]));
+    }
+    CK(cudaMemcpyAsync(C.d_sets, s2.data(), sizeof(PrepSet) * s2.size(), cudaMemcpyHostToDevice, st));
+    CK(launch_prep(C.d_sets, s2.data(), K, C.d, g.n, g.c, g.s, C.err, st));
+    for (int k = 0; k < K; ++k) CK(cudaMemsetAsync(C.raw[k], 0, sizeof(float) * C.n[k], st));
+    if (C.path == MOT_PATH_NFFT) {
+        CK(prepare_window());
+        CK(prepare_fftconv(C.d, g.n));
+        size_t gsz = 1;
+        for (int t = 0; t < C.d; ++t) gsz *= g.n;
+        for (int k = 0; k < K; ++k) RET(make_D_for((C.eta / C.w[k]) / (g.s * g.s), g, C.d, o, C.dscr_a, C.dscr_b, C.D[k], st));
+        for (int c = 0; c < C.CB; ++c) CK(cudaMemsetAsync(C.grid[c], 0, gsz * sizeof(float), st));
+    } else {
+        int nmax = 0;
+        for (int k = 0; k < K; ++k) nmax = std::max(nmax, C.n[k]);
+        for (int c = 0; c < C.CB; ++c) CK(cudaMemsetAsync(C.rawm[c], 0, sizeof(float) * nmax, st));
+    }
+    // fixed dense kernel matrices: beta_{K-1} = K^{(K-1,0)}, Gam_1 = K^{(1,0)}
+    auto eta_u = [&](int edge) { return (float)((C.eta / C.w[edge]) / (g.s * g.s) * (double)g.n * (double)g.n); };
+    CK(launch_kernel_matrix(C.sets[K - 1].u, C.n[K - 1], C.sets[0].u, C.n0, C.d, eta_u(K - 1), C.beta[K - 1],
+                            C.beta_sc(K - 1), st));
+    CK(launch_kernel_matrix(C.sets[1].u, C.n[1], C.sets[0].u, C.n0, C.d, eta_u(0), C.gam[1], C.gam_sc(1), st));
+    c_build(C);
+    RET(c_upload(C, st));
+    return MOT_OK;
+}
+
+int circle_solve(const mot_problem* P, const mot_options& o, void* ws, size_t ws_bytes, const double* const* u_warm,
+                 mot_result* res, cudaStream_t st) {
+    CirclePlan C;
+    RET(circle_setup(P, o, C, ws, ws_bytes, false, nullptr, st));
+    Timer tm;
+    tm.on = o.timing != 0;
+    tm.st = st;
+    long long nl = 0;
+    const int K = C.K;
+    int minus1 = -1;
+    CK(cudaMemcpyAsync(C.iter, &minus1, sizeof(int), cudaMemcpyHostToDevice, st));
+    for (int k = 0; k < K; ++k) {
+        const double* uw = u_warm ? u_warm[k] : nullptr;
+        CK(launch_init_phi(C.phi[k], C.phi_sc(k), C.sets[k].perm, C.sets[k].mu_d, C.n[k], uw, C.eta,
+                           &C.acc[0].logphi, C.box_scratch, st));
+        nl += uw ? 2 : 1;
+    }
+    {   // initial beta sweep (Algorithm 3, steps 3-5)
+        cudaEvent_t e = nullptr;
+        RET(tm.begin(MOT_K_NODE, &e));
+        CK(launch_prologue(C.d_resets + C.bw_r0, (int)C.bw_rn, 0, 0, nullptr, 0, C.G, st));
+        RET(tm.end(e));
+        RET(c_backward(C, st, tm, nl));
+    }
+    const bool graphs = o.use_graphs > 0;
+    const bool want_viol = o.tol_viol >= 0.0;
+    int iters = 0, status = MOT_OK;
+    std::vector<char> buf(C.stats_bytes);
+    auto accp = [&]() { return reinterpret_cast<const IterAcc*>(buf.data()); };
+    auto nodep = [&]() { return reinterpret_cast<const double*>(buf.data() + sizeof(IterAcc) * kRing); };
+    double viol = INFINITY, S_last = NAN, S_prev = NAN;
+    bool met = false;
+    while (true) {
+        int chunk = std::min(o.check_every, o.max_iter - iters);
+        if (chunk <= 0) break;
+        RET(c_run_iterations(C, chunk, st, tm, nl, graphs));
+        iters += chunk;
+        RET(c_check(C, st, tm, nl));
+        CK(cudaMemcpyAsync(buf.data(), C.stats_begin, C.stats_bytes, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        RET(tm.collect(res));
+        if (*reinterpret_cast<const int*>(buf.data() + buf.size() - 16)) return MOT_ENUMERIC;
+        viol = 0.0;
+        for (int k = 0; k < K; ++k) viol = std::max(viol, nodep()[3 * k]);
+        auto Sval = [&](int r) { const IterAcc& a = accp()[r % kRing]; return C.eta * (a.logphi - a.mass); };
+        if (iters >= 1) S_last = Sval(iters - 1);
+        if (iters >= 2) S_prev = Sval(iters - 2);
+        if (!std::isfinite(viol)) return MOT_ENUMERIC;
+        if (iters >= o.min_iter) {
+            if (want_viol && viol <= o.tol_viol) { met = true; break; }
+            if (o.delta_S > 0.0 && iters >= 2 && std::fabs(S_last - S_prev) < o.delta_S) { met = true; break; }
+        }
+        if (iters >= o.max_iter) break;
+    }
+    if (!met && (want_viol || o.delta_S > 0.0)) status = MOT_ENOCONV;
+    if (res) {
+        const double* node = nodep();
+        double mass = node[2];
+        double plogphi = 0.0;
+        for (int k = 0; k < K; ++k) plogphi += node[3 * k + 1];
+        const IterAcc& cur = accp()[iters % kRing];
+        res->violation = viol;
+        res->mass = mass;
+        res->cost_dual = C.eta * (cur.logphi - mass);
+        res->cost_primal = C.eta * (plogphi - mass);
+        res->S_last = S_last;
+        res->S_prev = S_prev;
+        res->iters = iters;
+        long long cl = 0;
+        const VecScale* scs = reinterpret_cast<const VecScale*>(buf.data() + sizeof(IterAcc) * kRing + sizeof(double) * 3 * K);
+        for (int i = 0; i < 4 * K; ++i) cl += scs[i].clamped;
+        res->clamped = cl;
+        res->scale = C.g.s;
+        res->eta_norm = C.eta / (C.g.s * C.g.s);
+        res->n_grid = C.path == MOT_PATH_NFFT ? C.g.n : 0;
+        res->M = C.path == MOT_PATH_NFFT ? C.g.M : 0;
+        if (res->u) {
+            for (int k = 0; k < K; ++k) {
+                if (!res->u[k]) continue;
+                CK(launch_output(C.phi[k], C.phi_sc(k), C.sets[k].perm, C.n[k], C.eta, res->u[k], st));
+                nl += 1;
+            }
+        }
+        res->launches = nl;
+        res->status = status;
+    }
+    CK(cudaStreamSynchronize(st));
+    if (C.gexec) cudaGraphExecDestroy(C.gexec);
+    return status;
+}
+
 }  // namespace
 
 // =============================================================================================
@@ -1178,7 +1718,10 @@ int mot_workspace_bytes(const mot_problem* prob, const mot_options* opt, size_t*
     fill_defaults(o, opt);
     if (o.n_grid && (o.n_grid < 16 || o.n_grid > max_grid(prob->d) || (o.n_grid & (o.n_grid - 1)))) return MOT_EINVAL;
     if (o.m != 4) return MOT_EUNSUPPORTED;
-    if (prob->topology != MOT_TREE) return MOT_EUNSUPPORTED;
+    if (prob->topology == MOT_CIRCLE) {
+        CirclePlan C;
+        return circle_setup(prob, o, C, nullptr, 0, true, bytes, nullptr);
+    }
     TreePlan T;
     return tree_plan_setup(prob, o, T, nullptr, 0, true, bytes, nullptr);
 }
@@ -1199,7 +1742,6 @@ int mot_solve(const mot_problem* prob, const mot_options* opt, void* ws, size_t 
         *const_cast<double* const**>(&res->u) = u;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (prob->topology != MOT_TREE) return MOT_EUNSUPPORTED;
     // The legacy default stream cannot be captured into a graph: run on a private stream
     // ordered after / before the caller's work by events.
     cudaStream_t own = nullptr;
@@ -1211,7 +1753,8 @@ int mot_solve(const mot_problem* prob, const mot_options* opt, void* ws, size_t 
         CK(cudaEventRecord(ev_in, nullptr));
         CK(cudaStreamWaitEvent(own, ev_in, 0));
     }
-    int rc = tree_solve(prob, o, ws, ws_bytes, u_warm, res, own ? own : st);
+    int rc = prob->topology == MOT_TREE ? tree_solve(prob, o, ws, ws_bytes, u_warm, res, own ? own : st)
+                                         : circle_solve(prob, o, ws, ws_bytes, u_warm, res, own ? own : st);
     if (own) {
         cudaEventRecord(ev_out, own);
         cudaStreamWaitEvent(nullptr, ev_out, 0);

@@ -124,3 +124,11 @@ def test_solve_rejects_without_touching_gpu(M):
     lib = M.lib()
     assert lib.mot_solve(C.byref(p), None, None, 0, None, C.byref(res), None) == M.MOT_EINVAL
     assert lib.mot_solve(C.byref(p), None, C.c_void_p(0x1001), 1 << 20, None, C.byref(res), None) == M.MOT_EINVAL
+
+
+def test_circle_workspace_query(M):
+    p, keep = _fake_problem(M, 5, 1, [200, 210, 220, 230, 240], None, topology=1)
+    st, nb = _ws(M, p)
+    assert st == M.MOT_OK and nb > 4 * 200 * 210 * 2        # beta and gamma matrices
+    p2, k2 = _fake_problem(M, 2, 1, [20, 20], None, topology=1)
+    assert _ws(M, p2)[0] == M.MOT_EUNSUPPORTED              # a circle needs K >= 3
