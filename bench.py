@@ -129,15 +129,20 @@ def algorithmic_bytes(prob, n_grid):
     bwd_spread = 4 * d * N + 8 * N + G
     bwd_gather = G + 4 * d * N + 4 * N
     launches = K   # one forward launch + (K-1) backward launches per class
-    return {
+    out = {
         "spread": (fwd_spread + (K - 1) * bwd_spread) / launches,
         "gather": (fwd_gather + (K - 1) * bwd_gather) / launches,
         "fftconv": ((K - 1) * 2 * G + (K - 1) * 2 * G) / launches,
     }
+    # the fused 2-D kernel does all three with the grid in shared memory: its algorithmic
+    # bytes are the point data and the vectors only (no grid round trips)
+    out["fused"] = out["spread"] + out["gather"] - 2 * G * (2 * (K - 1)) / launches
+    return out
 
 
 def kernel_source_hash(cls):
     files = {"spread": ["nfft.cu", "common.cuh", "epilogue.cuh"], "gather": ["nfft.cu", "common.cuh", "epilogue.cuh"],
+             "fused": ["nfft.cu", "common.cuh", "epilogue.cuh", "window.cuh"],
              "fftconv": ["nfft.cu", "fft_smem.cuh"], "dense": ["dense.cu", "common.cuh", "epilogue.cuh"]}.get(cls, [])
     h = hashlib.sha256()
     for f in files:
@@ -334,6 +339,35 @@ def main():
                          "BF16-split path needs several right-hand sides)",
                  "value": di / dt, "unit": "iters/s", "iters_per_solve": o3.iters, "violation": o3.violation}
 
+    # ---- the other workloads (same metric, reported beside the headline) -------------------
+    others = {}
+    if not args.no_dense and args.workload == WORKLOAD:
+        for wname, topo in (("star9_d3", M.MOT_TREE), ("circle5_d1", M.MOT_CIRCLE)):
+            wp = W.WORKLOADS[wname]()
+            wx = [torch.from_numpy(a).to(dev) for a in wp.x]
+            wm = [torch.from_numpy(m).to(dev) for m in wp.mu]
+            entry = {}
+            for pname, path, reps in (("nfft", M.MOT_PATH_NFFT, 3), ("dense", M.MOT_PATH_DENSE, 2)):
+                wo = M.options(path=path, tol_viol=TOL, max_iter=3000)
+                wws = torch.empty(M.mot_workspace_bytes(wx, wm, wp.eta, topo, edges=wp.edges, opt=wo),
+                                  dtype=torch.uint8, device=dev)
+                tt, ti = 0.0, 0
+                for r in range(reps + 1):
+                    with torch.cuda.stream(stream):
+                        flush.random_(0, 255)
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        ow = M.mot_solve(wx, wm, wp.eta, topo, edges=wp.edges, opt=wo, workspace=wws, stream=stream)
+                        e1.record(stream)
+                    e1.synchronize()
+                    if r > 0:
+                        tt += e0.elapsed_time(e1) / 1e3
+                        ti += ow.iters
+                entry[pname] = {"value": ti / tt, "unit": "iters/s", "iters_per_solve": ow.iters,
+                                "violation": ow.violation, "status": ow.status}
+                del wws
+            others[wname] = entry
+
     # ---- end to end through the C ABI with host buffers ---------------------------------
     xh = [torch.from_numpy(a).pin_memory() for a in prob.x]
     muh = [torch.from_numpy(m).pin_memory() for m in prob.mu]
@@ -382,6 +416,7 @@ def main():
                    "l2": "flushed between steps (256 MB write)"},
         "latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "dense": dense,
+        "other_workloads": others,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -58,7 +58,8 @@ extern "C" {
 #define MOT_K_DENSE    3    /* dense direct matrix-vector product                              */
 #define MOT_K_NODE     4    /* element-wise sweep updates and FP64 reductions                  */
 #define MOT_K_SETUP    5    /* normalisation, binning, kernel Fourier coefficients             */
-#define MOT_K_CIRCLE   6    /* circle-structure batched kernels                                */
+#define MOT_K_CIRCLE   6    /* circle row-dot / column-sum scaling updates                     */
+#define MOT_K_FUSED    7    /* fused 2-D fast summation (spread, DFTs, gather in one cluster)  */
 #define MOT_NKCLASS    8
 
 /* ---- problem --------------------------------------------------------------------- */

@@ -706,7 +706,7 @@ struct Timer {
 int run_level(TreePlan& T, Level& L, cudaStream_t st, Timer& tm, long long& nl) {
     cudaEvent_t e = nullptr;
     if (T.path == MOT_PATH_NFFT && T.fused) {
-        RET(tm.begin(MOT_K_GATHER, &e));
+        RET(tm.begin(MOT_K_FUSED, &e));
         CK(launch_fused2d(L.d_tgt, (int)L.tgt.size(), T.G, st));
         RET(tm.end(e));
         nl += 1;

@@ -18,7 +18,7 @@ MOT_OK, MOT_EINVAL, MOT_ENOTTREE, MOT_ENOMEM, MOT_ENUMERIC, MOT_ENOCONV, MOT_ETI
 MOT_TREE, MOT_CIRCLE = 0, 1
 MOT_PATH_NFFT, MOT_PATH_DENSE, MOT_PATH_DENSE_BF16X3 = 0, 1, 2
 MOT_NKCLASS = 8
-KERNEL_CLASSES = ["spread", "fftconv", "gather", "dense", "node", "setup", "circle", "spare"]
+KERNEL_CLASSES = ["spread", "fftconv", "gather", "dense", "node", "setup", "circle", "fused"]
 
 
 class MotError(RuntimeError):
