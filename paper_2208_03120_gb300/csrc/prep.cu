@@ -206,6 +206,9 @@ __global__ void k_khat_samples(double* S, KernelArgs K) {
 __global__ void k_cos_pass(const double* __restrict__ in, double* __restrict__ out, long long pre, long long post,
                            int M) {
     const int L = 2 * M;
+    extern __shared__ double ctab[];                       // cos(pi a / M), a = 0..2M-1
+    for (int a = threadIdx.x; a < L; a += blockDim.x) ctab[a] = cospi((double)a / (double)M);
+    __syncthreads();
     const long long total = pre * (M + 1) * post;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -215,10 +218,11 @@ __global__ void k_cos_pass(const double* __restrict__ in, double* __restrict__ o
         long long p = rest / (M + 1);
         const double* src = in + (p * L) * post + q;
         double acc = 0.0;
+        int a = (int)(((long long)m * (L - M)) % L);        // m (j - M) mod 2M at j = 0
         for (int j = 0; j < L; ++j) {
-            long long a = ((long long)m * (j - M)) % L;
-            if (a < 0) a += L;
-            acc += src[(long long)j * post] * cospi((double)a / (double)M);
+            acc += src[(long long)j * post] * ctab[a];
+            a += m;
+            if (a >= L) a -= L;
         }
         out[idx] = acc / (double)L;
     }
@@ -247,6 +251,12 @@ __device__ double window_ft(int k, int n) {
 }
 
 __global__ void k_make_D(const double* __restrict__ khat, float* D, int d, int M, int n) {
+    extern __shared__ double inv_psi2[];                   // 1 / Psi(k)^2, k = 0..M
+    for (int k = threadIdx.x; k <= M; k += blockDim.x) {
+        const double p = window_ft(k, n);
+        inv_psi2[k] = 1.0 / (p * p);
+    }
+    __syncthreads();
     const int nk = 2 * M + 1, nh = M + 1;
     long long total = nh;
     for (int t = 1; t < d; ++t) total *= nk;
@@ -262,16 +272,14 @@ __global__ void k_make_D(const double* __restrict__ khat, float* D, int d, int M
         }
         double w = (k[0] == 0) ? 1.0 : 2.0;   // mirrored negative half in the first coordinate
         long long kidx = 0, mult = 1;
-        double psi = 1.0;
         for (int t = 0; t < d; ++t) {
             int a = abs(k[t]);
             if (a == M) w *= 0.5;              // symmetric weight on the faces |k_t| = M
             kidx += a * mult;
             mult *= nh;
-            double p = window_ft(a, n);
-            psi *= p * p;
+            w *= inv_psi2[a];
         }
-        D[idx] = (float)(w * khat[kidx] / psi);
+        D[idx] = (float)(w * khat[kidx]);
     }
 }
 
@@ -413,13 +421,13 @@ cudaError_t launch_make_D(int d, int M, int n, double eta_n, double tau, double 
         long long pre = 1;
         for (int s = t + 1; s < d; ++s) pre *= L;
         long long outn = pre * (M + 1) * post;
-        k_cos_pass<<<blocks_for(outn), 256, 0, st>>>(in, out, pre, post, M);
+        k_cos_pass<<<blocks_for(outn), 256, sizeof(double) * L, st>>>(in, out, pre, post, M);
         post *= (M + 1);
         double* tmp = in;
         in = out;
         out = tmp;
     }
-    k_make_D<<<blocks_for((long long)D_floats(d, M)), 256, 0, st>>>(in, D, d, M, n);
+    k_make_D<<<blocks_for((long long)D_floats(d, M)), 256, sizeof(double) * (M + 1), st>>>(in, D, d, M, n);
     return cudaGetLastError();
 }
 

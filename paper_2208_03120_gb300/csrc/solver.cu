@@ -878,8 +878,16 @@ int tree_plan_setup(const mot_problem* P, const mot_options& o, TreePlan& T, voi
         size_t gsz = 1;
         for (int t = 0; t < T.d; ++t) gsz *= g.n;
         for (int k = 1; k < T.K; ++k) {
-            double eta_n = (T.eta / T.w[k]) / (g.s * g.s);
-            RET(make_D_for(eta_n, g, T.d, o, T.dscr_a, T.dscr_b, T.D[k], st));
+            // edges with the same weight share one multiplier
+            int same = -1;
+            for (int q = 1; q < k && same < 0; ++q)
+                if (T.w[q] == T.w[k]) same = q;
+            if (same > 0) {
+                T.D[k] = T.D[same];
+            } else {
+                double eta_n = (T.eta / T.w[k]) / (g.s * g.s);
+                RET(make_D_for(eta_n, g, T.d, o, T.dscr_a, T.dscr_b, T.D[k], st));
+            }
             CK(cudaMemsetAsync(T.grid[k], 0, gsz * sizeof(float), st));
         }
     } else {
@@ -1417,7 +1425,15 @@ int circle_setup(const mot_problem* P, const mot_options& o, CirclePlan& C, void
         CK(prepare_fftconv(C.d, g.n));
         size_t gsz = 1;
         for (int t = 0; t < C.d; ++t) gsz *= g.n;
-        for (int k = 0; k < K; ++k) RET(make_D_for((C.eta / C.w[k]) / (g.s * g.s), g, C.d, o, C.dscr_a, C.dscr_b, C.D[k], st));
+        for (int k = 0; k < K; ++k) {
+            int same = -1;
+            for (int q = 0; q < k && same < 0; ++q)
+                if (C.w[q] == C.w[k]) same = q;
+            if (same >= 0)
+                C.D[k] = C.D[same];
+            else
+                RET(make_D_for((C.eta / C.w[k]) / (g.s * g.s), g, C.d, o, C.dscr_a, C.dscr_b, C.D[k], st));
+        }
         for (int c = 0; c < C.CB; ++c) CK(cudaMemsetAsync(C.grid[c], 0, gsz * sizeof(float), st));
     } else {
         int nmax = 0;
