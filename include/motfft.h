@@ -169,6 +169,40 @@ int mot_fastsum(int d, double eta, const float* x_src, int64_t n_src, const floa
                 const mot_options* opt, void* ws, size_t ws_bytes, double* scale_out,
                 void* stream);
 
+/* ---- serving: continuous batching of solves ---------------------------------------- */
+/*
+ * A server runs many mot_solve-equivalent requests at once.  Each admitted request gets its
+ * own CUDA stream, its own captured iteration graph and a region of the caller's device pool
+ * sized by mot_workspace_bytes (admission in arrival order while a slot and pool memory are
+ * free); requests that arrive while others run are admitted as slots and memory free up, and
+ * their kernels overlap on the GPU.  Results equal mot_solve's for the same request (up to
+ * floating-point summation order).  The API is driven by the caller and not thread-safe.
+ */
+typedef struct mot_server_s* mot_server;
+typedef struct {
+    long long tag;          /* the submit tag                                                 */
+    int status;             /* MOT_OK, MOT_ENOCONV, or the error of the request               */
+    int iters;
+    double violation, cost_dual, cost_primal;
+    double submit_ms, admit_ms, done_ms;  /* host clock since mot_server_create              */
+} mot_server_result;
+/* pool: device memory owned by the caller (256-byte aligned) shared by the requests'
+   workspaces; max_active: concurrent requests (1..256).  Creates max_active streams and
+   pinned host stat buffers (32 KiB each). */
+int mot_server_create(void* pool, size_t pool_bytes, int max_active, mot_server* out);
+/* Queue a request.  The problem's arrays are copied; the device buffers it points to (x, mu)
+   and u (host [K] of device pointers, may be NULL) must stay valid until its result is polled.
+   A request larger than the whole pool completes with MOT_ENOMEM. */
+int mot_server_submit(mot_server s, const mot_problem* prob, const mot_options* opt, double* const* u,
+                      long long tag);
+/* Non-blocking step: advance running requests whose last chunk finished (stop test, next chunk
+   or outputs), complete finished ones and admit pending ones (admission performs the request's
+   set-up, which reads back the point-cloud radius). */
+int mot_server_progress(mot_server s, int* n_active, int* n_pending);
+/* Move up to max completed results into out. */
+int mot_server_poll(mot_server s, mot_server_result* out, int max, int* n_out);
+int mot_server_destroy(mot_server s);
+
 /*
  * Allocation-free variant of mot_fastsum (the paper has no counterpart: this serves callers
  * that cannot allocate GPU memory or pass a workspace, e.g. code that must not allocate while

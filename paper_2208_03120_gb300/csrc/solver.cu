@@ -8,6 +8,7 @@
 // as FP32 mantissas with an FP64 log-scale (VecScale); the dual value, marginal violation and
 // cost are FP64 reductions.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -902,96 +903,6 @@ int tree_plan_setup(const mot_problem* P, const mot_options& o, TreePlan& T, voi
     return MOT_OK;
 }
 
-int tree_solve(const mot_problem* P, const mot_options& o, void* ws, size_t ws_bytes, const double* const* u_warm,
-               mot_result* res, cudaStream_t st) {
-    TreePlan T;
-    RET(tree_plan_setup(P, o, T, ws, ws_bytes, false, nullptr, st));
-    Timer tm;
-    tm.on = o.timing != 0;
-    tm.st = st;
-    long long nl = 0;
-    const int K = T.K;
-    // initial scalings, iteration counter, accumulators
-    {
-        int minus1 = -1;
-        CK(cudaMemcpyAsync(T.iter, &minus1, sizeof(int), cudaMemcpyHostToDevice, st));
-        for (int k = 0; k < K; ++k) {
-            const double* uw = (u_warm && !T.free_[k]) ? u_warm[T.order[k]] : nullptr;
-            CK(launch_init_phi(T.phi[k], T.phi_sc(k), T.sets[k].perm, T.sets[k].mu_d, T.n[k], uw, T.eta,
-                               &T.acc[0].logphi, T.box_scratch, st));
-            nl += uw ? 2 : 1;
-        }
-    }
-    // initial beta sweep (Algorithm 2, steps 3-5)
-    for (auto& L : T.bwd) RET(run_level(T, L, st, tm, nl));
-
-    const bool graphs = o.use_graphs > 0;
-    const bool want_viol = o.tol_viol >= 0.0;
-    int iters = 0, status = MOT_OK;
-    Stats S;
-    double viol = INFINITY, S_last = NAN, S_prev = NAN;
-    bool met = false;
-    while (true) {
-        int chunk = std::min(o.check_every, o.max_iter - iters);
-        if (chunk <= 0) break;
-        RET(run_iterations(T, chunk, st, tm, nl, graphs));
-        iters += chunk;
-        RET(run_check(T, st, tm, nl));
-        RET(read_stats(T, S, st));
-        RET(tm.collect(res));
-        if (S.err() & 1) return MOT_ENUMERIC;
-        if (S.err() & 2) return MOT_ENUMERIC;
-        viol = 0.0;
-        for (int k = 0; k < K; ++k)
-            if (!T.free_[k]) viol = std::max(viol, S.node(K)[3 * k]);
-        // S^(r) = eta (logphi^(r) - mass^(r)), r = iters-1 and iters-2 complete
-        auto Sval = [&](int r) { const IterAcc& a = S.acc()[r % kRing]; return T.eta * (a.logphi - a.mass); };
-        if (iters >= 1) S_last = Sval(iters - 1);
-        if (iters >= 2) S_prev = Sval(iters - 2);
-        if (!std::isfinite(viol)) return MOT_ENUMERIC;
-        if (iters >= o.min_iter) {
-            if (want_viol && viol <= o.tol_viol) { met = true; break; }
-            if (o.delta_S > 0.0 && iters >= 2 && std::fabs(S_last - S_prev) < o.delta_S) { met = true; break; }
-        }
-        if (iters >= o.max_iter) break;
-    }
-    if (!met && (want_viol || o.delta_S > 0.0)) status = MOT_ENOCONV;
-    // outputs
-    if (res) {
-        const double* node = S.node(K);
-        double mass = node[2];
-        double plogphi = 0.0;
-        for (int k = 0; k < K; ++k) plogphi += node[3 * k + 1];
-        const IterAcc& cur = S.acc()[iters % kRing];
-        res->violation = viol;
-        res->mass = mass;
-        res->cost_dual = T.eta * (cur.logphi - mass);
-        res->cost_primal = T.eta * (plogphi - mass);
-        res->S_last = S_last;
-        res->S_prev = S_prev;
-        res->iters = iters;
-        long long cl = 0;
-        const VecScale* scs = S.sc(K);
-        for (int i = 0; i < 4 * K; ++i) cl += scs[i].clamped;
-        res->clamped = cl;
-        res->scale = T.g.s;
-        res->eta_norm = T.eta / (T.g.s * T.g.s);
-        res->n_grid = T.path == MOT_PATH_NFFT ? T.g.n : 0;
-        res->M = T.path == MOT_PATH_NFFT ? T.g.M : 0;
-        if (res->u) {
-            for (int k = 0; k < K; ++k) {
-                if (!res->u[T.order[k]]) continue;
-                CK(launch_output(T.phi[k], T.phi_sc(k), T.sets[k].perm, T.n[k], T.eta, res->u[T.order[k]], st));
-                nl += 1;
-            }
-        }
-        res->launches = nl;
-        res->status = status;
-    }
-    CK(cudaStreamSynchronize(st));
-    if (T.gexec) cudaGraphExecDestroy(T.gexec);
-    return status;
-}
 
 
 // =============================================================================================
@@ -1450,95 +1361,359 @@ int circle_setup(const mot_problem* P, const mot_options& o, CirclePlan& C, void
     return MOT_OK;
 }
 
-int circle_solve(const mot_problem* P, const mot_options& o, void* ws, size_t ws_bytes, const double* const* u_warm,
-                 mot_result* res, cudaStream_t st) {
-    CirclePlan C;
-    RET(circle_setup(P, o, C, ws, ws_bytes, false, nullptr, st));
-    Timer tm;
-    tm.on = o.timing != 0;
-    tm.st = st;
-    long long nl = 0;
-    const int K = C.K;
-    int minus1 = -1;
-    CK(cudaMemcpyAsync(C.iter, &minus1, sizeof(int), cudaMemcpyHostToDevice, st));
-    for (int k = 0; k < K; ++k) {
-        const double* uw = u_warm ? u_warm[k] : nullptr;
-        CK(launch_init_phi(C.phi[k], C.phi_sc(k), C.sets[k].perm, C.sets[k].mu_d, C.n[k], uw, C.eta,
-                           &C.acc[0].logphi, C.box_scratch, st));
-        nl += uw ? 2 : 1;
+
+// =============================================================================================
+// resumable solve: a plan plus the stop-test loop, shared by mot_solve and the server
+// =============================================================================================
+struct PlanOps {
+    virtual ~PlanOps() {}
+    virtual int init(const double* const* u_warm, cudaStream_t st, Timer& tm, long long& nl) = 0;
+    virtual int iterations(int count, cudaStream_t st, Timer& tm, long long& nl, bool graphs) = 0;
+    virtual int check(cudaStream_t st, Timer& tm, long long& nl) = 0;
+    virtual char* stats_dev() = 0;
+    virtual size_t stats_bytes() const = 0;
+    virtual int K() const = 0;
+    virtual bool constrained(int k) const = 0;
+    virtual double eta() const = 0;
+    virtual int output(double* const* u, cudaStream_t st, long long& nl) = 0;
+    virtual void geometry(mot_result* r) const = 0;
+};
+
+struct TreeOps : PlanOps {
+    TreePlan T;
+    int init(const double* const* u_warm, cudaStream_t st, Timer& tm, long long& nl) override {
+        int minus1 = -1;
+        CK(cudaMemcpyAsync(T.iter, &minus1, sizeof(int), cudaMemcpyHostToDevice, st));
+        for (int k = 0; k < T.K; ++k) {
+            const double* uw = (u_warm && !T.free_[k]) ? u_warm[T.order[k]] : nullptr;
+            CK(launch_init_phi(T.phi[k], T.phi_sc(k), T.sets[k].perm, T.sets[k].mu_d, T.n[k], uw, T.eta,
+                               &T.acc[0].logphi, T.box_scratch, st));
+            nl += uw ? 2 : 1;
+        }
+        for (auto& L : T.bwd) RET(run_level(T, L, st, tm, nl));   // Algorithm 2, steps 3-5
+        return MOT_OK;
     }
-    {   // initial beta sweep (Algorithm 3, steps 3-5)
-        cudaEvent_t e = nullptr;
+    int iterations(int count, cudaStream_t st, Timer& tm, long long& nl, bool graphs) override {
+        return run_iterations(T, count, st, tm, nl, graphs);
+    }
+    int check(cudaStream_t st, Timer& tm, long long& nl) override { return run_check(T, st, tm, nl); }
+    char* stats_dev() override { return T.stats_begin; }
+    size_t stats_bytes() const override { return T.stats_bytes; }
+    int K() const override { return T.K; }
+    bool constrained(int k) const override { return !T.free_[k]; }
+    double eta() const override { return T.eta; }
+    int output(double* const* u, cudaStream_t st, long long& nl) override {
+        for (int k = 0; k < T.K; ++k) {
+            if (!u[T.order[k]]) continue;
+            CK(launch_output(T.phi[k], T.phi_sc(k), T.sets[k].perm, T.n[k], T.eta, u[T.order[k]], st));
+            nl += 1;
+        }
+        return MOT_OK;
+    }
+    void geometry(mot_result* r) const override {
+        r->scale = T.g.s;
+        r->eta_norm = T.eta / (T.g.s * T.g.s);
+        r->n_grid = T.path == MOT_PATH_NFFT ? T.g.n : 0;
+        r->M = T.path == MOT_PATH_NFFT ? T.g.M : 0;
+    }
+    ~TreeOps() override {
+        if (T.gexec) cudaGraphExecDestroy(T.gexec);
+    }
+};
+
+struct CircleOps : PlanOps {
+    CirclePlan C;
+    int init(const double* const* u_warm, cudaStream_t st, Timer& tm, long long& nl) override {
+        int minus1 = -1;
+        CK(cudaMemcpyAsync(C.iter, &minus1, sizeof(int), cudaMemcpyHostToDevice, st));
+        for (int k = 0; k < C.K; ++k) {
+            const double* uw = u_warm ? u_warm[k] : nullptr;
+            CK(launch_init_phi(C.phi[k], C.phi_sc(k), C.sets[k].perm, C.sets[k].mu_d, C.n[k], uw, C.eta,
+                               &C.acc[0].logphi, C.box_scratch, st));
+            nl += uw ? 2 : 1;
+        }
+        cudaEvent_t e = nullptr;                                   // Algorithm 3, steps 3-5
         RET(tm.begin(MOT_K_NODE, &e));
         CK(launch_prologue(C.d_resets + C.bw_r0, (int)C.bw_rn, 0, 0, nullptr, 0, C.G, st));
         RET(tm.end(e));
-        RET(c_backward(C, st, tm, nl));
+        return c_backward(C, st, tm, nl);
     }
-    const bool graphs = o.use_graphs > 0;
-    const bool want_viol = o.tol_viol >= 0.0;
+    int iterations(int count, cudaStream_t st, Timer& tm, long long& nl, bool graphs) override {
+        return c_run_iterations(C, count, st, tm, nl, graphs);
+    }
+    int check(cudaStream_t st, Timer& tm, long long& nl) override { return c_check(C, st, tm, nl); }
+    char* stats_dev() override { return C.stats_begin; }
+    size_t stats_bytes() const override { return C.stats_bytes; }
+    int K() const override { return C.K; }
+    bool constrained(int) const override { return true; }
+    double eta() const override { return C.eta; }
+    int output(double* const* u, cudaStream_t st, long long& nl) override {
+        for (int k = 0; k < C.K; ++k) {
+            if (!u[k]) continue;
+            CK(launch_output(C.phi[k], C.phi_sc(k), C.sets[k].perm, C.n[k], C.eta, u[k], st));
+            nl += 1;
+        }
+        return MOT_OK;
+    }
+    void geometry(mot_result* r) const override {
+        r->scale = C.g.s;
+        r->eta_norm = C.eta / (C.g.s * C.g.s);
+        r->n_grid = C.path == MOT_PATH_NFFT ? C.g.n : 0;
+        r->M = C.path == MOT_PATH_NFFT ? C.g.M : 0;
+    }
+    ~CircleOps() override {
+        if (C.gexec) cudaGraphExecDestroy(C.gexec);
+    }
+};
+
+// Build the plan of a problem inside `ws` (sizes: mot_workspace_bytes) and enqueue its set-up.
+int make_ops(const mot_problem* P, const mot_options& o, void* ws, size_t ws_bytes, cudaStream_t st, PlanOps** out) {
+    if (P->topology == MOT_TREE) {
+        TreeOps* t = new TreeOps();
+        int rc = tree_plan_setup(P, o, t->T, ws, ws_bytes, false, nullptr, st);
+        if (rc != MOT_OK) {
+            delete t;
+            return rc;
+        }
+        *out = t;
+    } else {
+        CircleOps* c = new CircleOps();
+        int rc = circle_setup(P, o, c->C, ws, ws_bytes, false, nullptr, st);
+        if (rc != MOT_OK) {
+            delete c;
+            return rc;
+        }
+        *out = c;
+    }
+    return MOT_OK;
+}
+
+struct Solve {
+    PlanOps* ops = nullptr;
+    mot_options o;
+    cudaStream_t st = nullptr;
+    Timer tm;
+    long long nl = 0;
     int iters = 0, status = MOT_OK;
-    std::vector<char> buf(C.stats_bytes);
-    auto accp = [&]() { return reinterpret_cast<const IterAcc*>(buf.data()); };
-    auto nodep = [&]() { return reinterpret_cast<const double*>(buf.data() + sizeof(IterAcc) * kRing); };
     double viol = INFINITY, S_last = NAN, S_prev = NAN;
-    bool met = false;
-    while (true) {
-        int chunk = std::min(o.check_every, o.max_iter - iters);
-        if (chunk <= 0) break;
-        RET(c_run_iterations(C, chunk, st, tm, nl, graphs));
+    bool met = false, done = false;
+    char* hstats = nullptr;           // host copy of the stats region (pinned for the server)
+    cudaEvent_t ev = nullptr;
+
+    int start(const double* const* u_warm) {
+        tm.on = o.timing != 0;
+        tm.st = st;
+        return ops->init(u_warm, st, tm, nl);
+    }
+    // enqueue the next chunk of iterations, the check pass and the stats copy; record ev
+    int launch() {
+        const int chunk = std::min(o.check_every, o.max_iter - iters);
+        RET(ops->iterations(chunk, st, tm, nl, o.use_graphs > 0));
         iters += chunk;
-        RET(c_check(C, st, tm, nl));
-        CK(cudaMemcpyAsync(buf.data(), C.stats_begin, C.stats_bytes, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        RET(ops->check(st, tm, nl));
+        CK(cudaMemcpyAsync(hstats, ops->stats_dev(), ops->stats_bytes(), cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(ev, st));
+        return MOT_OK;
+    }
+    // after ev completed: stop test (sets done)
+    int evaluate(mot_result* res) {
         RET(tm.collect(res));
-        if (*reinterpret_cast<const int*>(buf.data() + buf.size() - 16)) return MOT_ENUMERIC;
+        const size_t sb = ops->stats_bytes();
+        const int K = ops->K();
+        const IterAcc* acc = reinterpret_cast<const IterAcc*>(hstats);
+        const double* node = reinterpret_cast<const double*>(hstats + sizeof(IterAcc) * kRing);
+        if (*reinterpret_cast<const int*>(hstats + sb - 16)) return MOT_ENUMERIC;
         viol = 0.0;
-        for (int k = 0; k < K; ++k) viol = std::max(viol, nodep()[3 * k]);
-        auto Sval = [&](int r) { const IterAcc& a = accp()[r % kRing]; return C.eta * (a.logphi - a.mass); };
+        for (int k = 0; k < K; ++k)
+            if (ops->constrained(k)) viol = std::max(viol, node[3 * k]);
+        auto Sval = [&](int r) { const IterAcc& a = acc[r % kRing]; return ops->eta() * (a.logphi - a.mass); };
         if (iters >= 1) S_last = Sval(iters - 1);
         if (iters >= 2) S_prev = Sval(iters - 2);
         if (!std::isfinite(viol)) return MOT_ENUMERIC;
+        const bool want_viol = o.tol_viol >= 0.0;
         if (iters >= o.min_iter) {
-            if (want_viol && viol <= o.tol_viol) { met = true; break; }
-            if (o.delta_S > 0.0 && iters >= 2 && std::fabs(S_last - S_prev) < o.delta_S) { met = true; break; }
+            if (want_viol && viol <= o.tol_viol) met = true;
+            if (o.delta_S > 0.0 && iters >= 2 && std::fabs(S_last - S_prev) < o.delta_S) met = true;
         }
-        if (iters >= o.max_iter) break;
+        if (met || iters >= o.max_iter) {
+            done = true;
+            if (!met && (want_viol || o.delta_S > 0.0)) status = MOT_ENOCONV;
+        }
+        return MOT_OK;
     }
-    if (!met && (want_viol || o.delta_S > 0.0)) status = MOT_ENOCONV;
-    if (res) {
-        const double* node = nodep();
-        double mass = node[2];
-        double plogphi = 0.0;
-        for (int k = 0; k < K; ++k) plogphi += node[3 * k + 1];
-        const IterAcc& cur = accp()[iters % kRing];
-        res->violation = viol;
-        res->mass = mass;
-        res->cost_dual = C.eta * (cur.logphi - mass);
-        res->cost_primal = C.eta * (plogphi - mass);
-        res->S_last = S_last;
-        res->S_prev = S_prev;
-        res->iters = iters;
-        long long cl = 0;
-        const VecScale* scs = reinterpret_cast<const VecScale*>(buf.data() + sizeof(IterAcc) * kRing + sizeof(double) * 3 * K);
-        for (int i = 0; i < 4 * K; ++i) cl += scs[i].clamped;
-        res->clamped = cl;
-        res->scale = C.g.s;
-        res->eta_norm = C.eta / (C.g.s * C.g.s);
-        res->n_grid = C.path == MOT_PATH_NFFT ? C.g.n : 0;
-        res->M = C.path == MOT_PATH_NFFT ? C.g.M : 0;
-        if (res->u) {
-            for (int k = 0; k < K; ++k) {
-                if (!res->u[k]) continue;
-                CK(launch_output(C.phi[k], C.phi_sc(k), C.sets[k].perm, C.n[k], C.eta, res->u[k], st));
-                nl += 1;
+    // fill the scalar results and enqueue u^k
+    int finish(mot_result* res, double* const* u) {
+        const int K = ops->K();
+        const IterAcc* acc = reinterpret_cast<const IterAcc*>(hstats);
+        const double* node = reinterpret_cast<const double*>(hstats + sizeof(IterAcc) * kRing);
+        const VecScale* scs = reinterpret_cast<const VecScale*>(hstats + sizeof(IterAcc) * kRing + sizeof(double) * 3 * K);
+        if (u) RET(ops->output(u, st, nl));
+        if (res) {
+            double mass = node[2], plogphi = 0.0;
+            for (int k = 0; k < K; ++k) plogphi += node[3 * k + 1];
+            const IterAcc& cur = acc[iters % kRing];
+            res->violation = viol;
+            res->mass = mass;
+            res->cost_dual = ops->eta() * (cur.logphi - mass);
+            res->cost_primal = ops->eta() * (plogphi - mass);
+            res->S_last = S_last;
+            res->S_prev = S_prev;
+            res->iters = iters;
+            long long cl = 0;
+            for (int i = 0; i < 4 * K; ++i) cl += scs[i].clamped;
+            res->clamped = cl;
+            ops->geometry(res);
+            res->launches = nl;
+            res->status = status;
+        }
+        return MOT_OK;
+    }
+};
+
+// Blocking solve on `st` (the mot_solve entry point).
+int solve_blocking(const mot_problem* P, const mot_options& o, void* ws, size_t ws_bytes, const double* const* u_warm,
+                   mot_result* res, cudaStream_t st) {
+    Solve S;
+    S.o = o;
+    S.st = st;
+    RET(make_ops(P, o, ws, ws_bytes, st, &S.ops));
+    std::vector<char> h(S.ops->stats_bytes());
+    S.hstats = h.data();
+    int rc = cudaEventCreateWithFlags(&S.ev, cudaEventDisableTiming) == cudaSuccess ? MOT_OK : MOT_ECUDA;
+    if (rc == MOT_OK) rc = S.start(u_warm);
+    while (rc == MOT_OK && !S.done) {
+        rc = S.launch();
+        if (rc != MOT_OK) break;
+        cudaError_t e = cudaEventSynchronize(S.ev);
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "cudaEventSynchronize");
+            rc = MOT_ECUDA;
+            break;
+        }
+        rc = S.evaluate(res);
+    }
+    if (rc == MOT_OK) rc = S.finish(res, res ? res->u : nullptr);
+    if (rc == MOT_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = MOT_ECUDA;
+    if (S.ev) cudaEventDestroy(S.ev);
+    delete S.ops;
+    return rc == MOT_OK ? S.status : rc;
+}
+
+// =============================================================================================
+// server: continuous batching of solves (admission by workspace bytes, one stream per slot)
+// =============================================================================================
+struct Pool {   // first-fit allocator over [0, size) in 256-byte units of the caller's pool
+    std::vector<std::pair<size_t, size_t>> free_;     // (offset, bytes), sorted, coalesced
+    size_t size = 0;
+    void init(size_t n) {
+        size = n & ~(size_t)255;
+        free_.assign(1, {0, size});
+    }
+    bool alloc(size_t n, size_t* off) {
+        n = (n + 255) & ~(size_t)255;
+        for (size_t i = 0; i < free_.size(); ++i) {
+            if (free_[i].second >= n) {
+                *off = free_[i].first;
+                free_[i].first += n;
+                free_[i].second -= n;
+                if (free_[i].second == 0) free_.erase(free_.begin() + i);
+                return true;
             }
         }
-        res->launches = nl;
-        res->status = status;
+        return false;
     }
-    CK(cudaStreamSynchronize(st));
-    if (C.gexec) cudaGraphExecDestroy(C.gexec);
-    return status;
+    void release(size_t off, size_t n) {
+        n = (n + 255) & ~(size_t)255;
+        auto it = free_.begin();
+        while (it != free_.end() && it->first < off) ++it;
+        it = free_.insert(it, {off, n});
+        const size_t i = it - free_.begin();
+        if (i + 1 < free_.size() && free_[i].first + free_[i].second == free_[i + 1].first) {
+            free_[i].second += free_[i + 1].second;
+            free_.erase(free_.begin() + i + 1);
+        }
+        if (i > 0 && free_[i - 1].first + free_[i - 1].second == free_[i].first) {
+            free_[i - 1].second += free_[i].second;
+            free_.erase(free_.begin() + i);
+        }
+    }
+};
+
+struct Request {
+    long long tag = 0;
+    mot_problem prob;
+    mot_options o;
+    std::vector<int64_t> n;
+    std::vector<const float*> x;
+    std::vector<const double*> mu;
+    std::vector<int> edges;
+    std::vector<double> w;
+    std::vector<unsigned char> freen;
+    std::vector<double*> u;
+    size_t ws_bytes = 0;
+    double t_submit = 0.0;
+};
+
+struct Active {
+    Request req;
+    size_t off = 0;
+    int slot = 0;
+    Solve solve;
+    mot_result res;
+    bool finishing = false;
+    double t_admit = 0.0;
+};
+
+const size_t kSlotStats = 32768;   // pinned host bytes per slot (stats of K <= 64)
+
+}  // namespace
+
+struct mot_server_s {
+    char* base = nullptr;
+    Pool pool;
+    int max_active = 0;
+    std::deque<Request> pending;
+    std::vector<Active*> active;
+    std::vector<mot_server_result> done;
+    std::vector<cudaStream_t> streams;
+    std::vector<char*> pinned;
+    std::vector<bool> slot_busy;
+    std::chrono::steady_clock::time_point t0;
+    double now() const {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+void server_complete(mot_server_s* S, Active* a, int status) {
+    mot_server_result r;
+    std::memset(&r, 0, sizeof(r));
+    r.tag = a->req.tag;
+    r.status = status;
+    r.iters = a->res.iters;
+    r.violation = a->res.violation;
+    r.cost_dual = a->res.cost_dual;
+    r.cost_primal = a->res.cost_primal;
+    r.submit_ms = a->req.t_submit;
+    r.admit_ms = a->t_admit;
+    r.done_ms = S->now();
+    S->done.push_back(r);
+    if (a->solve.ev) cudaEventDestroy(a->solve.ev);
+    delete a->solve.ops;
+    S->pool.release(a->off, a->req.ws_bytes);
+    S->slot_busy[a->slot] = false;
+    delete a;
+}
+
+void server_reject(mot_server_s* S, const Request& q, int status) {
+    mot_server_result r;
+    std::memset(&r, 0, sizeof(r));
+    r.tag = q.tag;
+    r.status = status;
+    r.submit_ms = q.t_submit;
+    r.admit_ms = r.done_ms = S->now();
+    S->done.push_back(r);
 }
 
 }  // namespace
@@ -1769,8 +1944,7 @@ int mot_solve(const mot_problem* prob, const mot_options* opt, void* ws, size_t 
         CK(cudaEventRecord(ev_in, nullptr));
         CK(cudaStreamWaitEvent(own, ev_in, 0));
     }
-    int rc = prob->topology == MOT_TREE ? tree_solve(prob, o, ws, ws_bytes, u_warm, res, own ? own : st)
-                                         : circle_solve(prob, o, ws, ws_bytes, u_warm, res, own ? own : st);
+    int rc = solve_blocking(prob, o, ws, ws_bytes, u_warm, res, own ? own : st);
     if (own) {
         cudaEventRecord(ev_out, own);
         cudaStreamWaitEvent(nullptr, ev_out, 0);
@@ -1801,6 +1975,173 @@ int mot_fastsum(int d, double eta, const float* x_src, int64_t n_src, const floa
     if (reinterpret_cast<uintptr_t>(ws) & 255) return MOT_EINVAL;
     return fastsum_impl(d, eta, x_src, n_src, x_tgt, n_tgt, alpha, nrhs, beta, o, ws, ws_bytes, scale_out,
                         reinterpret_cast<cudaStream_t>(stream), false, nullptr);
+}
+
+
+int mot_server_create(void* pool, size_t pool_bytes, int max_active, mot_server* out) {
+    if (!out || !pool || pool_bytes < 4096 || max_active < 1 || max_active > 256) return MOT_EINVAL;
+    if (reinterpret_cast<uintptr_t>(pool) & 255) return MOT_EINVAL;
+    mot_server_s* S = new mot_server_s();
+    S->base = reinterpret_cast<char*>(pool);
+    S->pool.init(pool_bytes);
+    S->max_active = max_active;
+    S->t0 = std::chrono::steady_clock::now();
+    for (int i = 0; i < max_active; ++i) {
+        cudaStream_t st = nullptr;
+        char* h = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaHostAlloc(reinterpret_cast<void**>(&h), kSlotStats, cudaHostAllocDefault) != cudaSuccess) {
+            set_cuda_error(cudaGetLastError(), "mot_server_create");
+            mot_server_destroy(S);
+            return MOT_ECUDA;
+        }
+        S->streams.push_back(st);
+        S->pinned.push_back(h);
+        S->slot_busy.push_back(false);
+    }
+    *out = S;
+    return MOT_OK;
+}
+
+int mot_server_submit(mot_server S, const mot_problem* prob, const mot_options* opt, double* const* u, long long tag) {
+    if (!S) return MOT_EINVAL;
+    RET(validate_problem(prob));
+    Request q;
+    q.tag = tag;
+    fill_defaults(q.o, opt);
+    if (q.o.m != 4 || q.o.timing) return MOT_EUNSUPPORTED;
+    const int K = prob->K;
+    q.n.assign(prob->n, prob->n + K);
+    q.x.assign(prob->x, prob->x + K);
+    q.mu.assign(prob->mu, prob->mu + K);
+    if (prob->topology == MOT_TREE) q.edges.assign(prob->edges, prob->edges + 2 * (K - 1));
+    const int ne = prob->topology == MOT_TREE ? K - 1 : K;
+    if (prob->edge_w) q.w.assign(prob->edge_w, prob->edge_w + ne);
+    if (prob->free_nodes) q.freen.assign(prob->free_nodes, prob->free_nodes + K);
+    if (u) q.u.assign(u, u + K);
+    q.prob = *prob;
+    q.prob.n = q.n.data();
+    q.prob.x = q.x.data();
+    q.prob.mu = q.mu.data();
+    q.prob.edges = q.edges.empty() ? nullptr : q.edges.data();
+    q.prob.edge_w = q.w.empty() ? nullptr : q.w.data();
+    q.prob.free_nodes = q.freen.empty() ? nullptr : q.freen.data();
+    RET(mot_workspace_bytes(&q.prob, &q.o, &q.ws_bytes));
+    q.t_submit = S->now();
+    S->pending.push_back(std::move(q));
+    // the vectors moved with the request: re-point the problem at the stored copies
+    Request& b = S->pending.back();
+    b.prob.n = b.n.data();
+    b.prob.x = b.x.data();
+    b.prob.mu = b.mu.data();
+    b.prob.edges = b.edges.empty() ? nullptr : b.edges.data();
+    b.prob.edge_w = b.w.empty() ? nullptr : b.w.data();
+    b.prob.free_nodes = b.freen.empty() ? nullptr : b.freen.data();
+    return MOT_OK;
+}
+
+int mot_server_progress(mot_server S, int* n_active, int* n_pending) {
+    if (!S) return MOT_EINVAL;
+    // 1. advance active solves whose last chunk completed
+    for (size_t i = 0; i < S->active.size();) {
+        Active* a = S->active[i];
+        cudaError_t q = cudaEventQuery(a->solve.ev);
+        if (q == cudaErrorNotReady) {
+            ++i;
+            continue;
+        }
+        int rc = q == cudaSuccess ? MOT_OK : MOT_ECUDA;
+        if (rc != MOT_OK) set_cuda_error(q, "mot_server_progress");
+        bool complete = false;
+        if (rc == MOT_OK && a->finishing) {
+            complete = true;
+        } else if (rc == MOT_OK) {
+            rc = a->solve.evaluate(&a->res);
+            if (rc == MOT_OK && !a->solve.done) {
+                rc = a->solve.launch();
+            } else if (rc == MOT_OK) {
+                rc = a->solve.finish(&a->res, a->req.u.empty() ? nullptr : a->req.u.data());
+                if (rc == MOT_OK && cudaEventRecord(a->solve.ev, a->solve.st) != cudaSuccess) rc = MOT_ECUDA;
+                a->finishing = true;
+            }
+        }
+        if (rc != MOT_OK || complete) {
+            cudaStreamSynchronize(a->solve.st);
+            server_complete(S, a, rc != MOT_OK ? rc : a->solve.status);
+            S->active.erase(S->active.begin() + i);
+            continue;
+        }
+        ++i;
+    }
+    // 2. admit pending requests in arrival order while a slot and pool memory are free
+    while (!S->pending.empty() && (int)S->active.size() < S->max_active) {
+        Request& q = S->pending.front();
+        if (q.ws_bytes > S->pool.size) {
+            server_reject(S, q, MOT_ENOMEM);
+            S->pending.pop_front();
+            continue;
+        }
+        size_t off = 0;
+        if (!S->pool.alloc(q.ws_bytes, &off)) break;          // wait for memory to free up
+        int slot = 0;
+        while (S->slot_busy[slot]) ++slot;
+        Active* a = new Active();
+        a->req = std::move(q);
+        S->pending.pop_front();
+        Request& r = a->req;
+        r.prob.n = r.n.data();
+        r.prob.x = r.x.data();
+        r.prob.mu = r.mu.data();
+        r.prob.edges = r.edges.empty() ? nullptr : r.edges.data();
+        r.prob.edge_w = r.w.empty() ? nullptr : r.w.data();
+        r.prob.free_nodes = r.freen.empty() ? nullptr : r.freen.data();
+        a->off = off;
+        a->slot = slot;
+        S->slot_busy[slot] = true;
+        a->t_admit = S->now();
+        std::memset(&a->res, 0, sizeof(a->res));
+        Solve& sv = a->solve;
+        sv.o = r.o;
+        sv.st = S->streams[slot];
+        sv.hstats = S->pinned[slot];
+        int rc = cudaEventCreateWithFlags(&sv.ev, cudaEventDisableTiming) == cudaSuccess ? MOT_OK : MOT_ECUDA;
+        if (rc == MOT_OK) rc = make_ops(&r.prob, r.o, S->base + off, r.ws_bytes, sv.st, &sv.ops);
+        if (rc == MOT_OK && sv.ops->stats_bytes() > kSlotStats) rc = MOT_EUNSUPPORTED;
+        if (rc == MOT_OK) rc = sv.start(nullptr);
+        if (rc == MOT_OK) rc = sv.launch();
+        if (rc != MOT_OK) {
+            cudaStreamSynchronize(sv.st);
+            server_complete(S, a, rc);
+            continue;
+        }
+        S->active.push_back(a);
+    }
+    if (n_active) *n_active = (int)S->active.size();
+    if (n_pending) *n_pending = (int)S->pending.size();
+    return MOT_OK;
+}
+
+int mot_server_poll(mot_server S, mot_server_result* out, int max, int* n_out) {
+    if (!S || !n_out || (max > 0 && !out)) return MOT_EINVAL;
+    const int n = std::min<int>(max, (int)S->done.size());
+    for (int i = 0; i < n; ++i) out[i] = S->done[i];
+    S->done.erase(S->done.begin(), S->done.begin() + n);
+    *n_out = n;
+    return MOT_OK;
+}
+
+int mot_server_destroy(mot_server S) {
+    if (!S) return MOT_EINVAL;
+    for (Active* a : S->active) {
+        cudaStreamSynchronize(a->solve.st);
+        if (a->solve.ev) cudaEventDestroy(a->solve.ev);
+        delete a->solve.ops;
+        delete a;
+    }
+    for (auto st : S->streams) cudaStreamDestroy(st);
+    for (auto h : S->pinned) cudaFreeHost(h);
+    delete S;
+    return MOT_OK;
 }
 
 }  // extern "C"

@@ -42,6 +42,14 @@ class Problem(C.Structure):
     ]
 
 
+class ServerResult(C.Structure):
+    _fields_ = [
+        ("tag", C.c_longlong), ("status", C.c_int), ("iters", C.c_int),
+        ("violation", C.c_double), ("cost_dual", C.c_double), ("cost_primal", C.c_double),
+        ("submit_ms", C.c_double), ("admit_ms", C.c_double), ("done_ms", C.c_double),
+    ]
+
+
 class Options(C.Structure):
     _fields_ = [
         ("path", C.c_int), ("max_iter", C.c_int),
@@ -93,6 +101,12 @@ def lib() -> C.CDLL:
         h.mot_fastsum_static.argtypes = [C.c_int, C.c_double, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                          C.c_void_p, C.c_int, C.c_void_p, C.POINTER(Options),
                                          C.POINTER(C.c_double), C.c_void_p]
+        h.mot_server_create.argtypes = [C.c_void_p, C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]
+        h.mot_server_submit.argtypes = [C.c_void_p, C.POINTER(Problem), C.POINTER(Options), C.POINTER(C.c_void_p),
+                                        C.c_longlong]
+        h.mot_server_progress.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        h.mot_server_poll.argtypes = [C.c_void_p, C.POINTER(ServerResult), C.c_int, C.POINTER(C.c_int)]
+        h.mot_server_destroy.argtypes = [C.c_void_p]
         _lib_handle = h
     return _lib_handle
 
@@ -303,7 +317,61 @@ def mot_solve(x, mu, eta, topology=MOT_TREE, edges=None, edge_w=None, free_nodes
     return SolveOutput(u, res)
 
 
+# ----------------------------------------------------------------------------------------
+# serving
+# ----------------------------------------------------------------------------------------
+
+class Server:
+    """Continuous batching of solves (mot_server_*): requests get their own stream, graph and
+    a region of the device pool; ``progress()`` advances them without blocking."""
+
+    def __init__(self, pool_bytes: int, max_active: int = 8, device=None):
+        import torch
+        self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=device or "cuda")
+        h = C.c_void_p()
+        _check(lib().mot_server_create(self.pool.data_ptr(), self.pool.numel(), max_active, C.byref(h)),
+               "mot_server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, x, mu, eta, topology=MOT_TREE, edges=None, edge_w=None, free_nodes=None, root=0,
+               opt: Optional[Options] = None, u_out=None, tag: int = 0):
+        import torch
+        holder = _ProblemHolder(x, mu, eta, topology, edges, edge_w, free_nodes, root)
+        u = u_out if u_out is not None else [torch.empty(int(t.shape[0]), dtype=torch.float64, device=t.device)
+                                             for t in x]
+        u_arr = (C.c_void_p * len(u))(*[t.data_ptr() for t in u])
+        _check(lib().mot_server_submit(self.h, C.byref(holder.p), C.byref(opt or options()), u_arr, int(tag)),
+               "mot_server_submit")
+        self._keep[int(tag)] = (holder, u, u_arr)
+        return u
+
+    def progress(self):
+        a, p = C.c_int(0), C.c_int(0)
+        _check(lib().mot_server_progress(self.h, C.byref(a), C.byref(p)), "mot_server_progress")
+        return a.value, p.value
+
+    def poll(self, max_results: int = 256):
+        buf = (ServerResult * max_results)()
+        n = C.c_int(0)
+        _check(lib().mot_server_poll(self.h, buf, max_results, C.byref(n)), "mot_server_poll")
+        out = []
+        for i in range(n.value):
+            r = buf[i]
+            out.append({"tag": r.tag, "status": r.status, "iters": r.iters, "violation": r.violation,
+                        "cost_dual": r.cost_dual, "cost_primal": r.cost_primal, "submit_ms": r.submit_ms,
+                        "admit_ms": r.admit_ms, "done_ms": r.done_ms,
+                        "u": self._keep.pop(int(r.tag), (None, None, None))[1]})
+        return out
+
+    def close(self):
+        if self.h:
+            lib().mot_server_destroy(self.h)
+            self.h = None
+
+
 # C-ABI entry points declared in include/motfft.h (checked by the test-suite).
 EXPORTED = ["mot_options_default", "mot_strerror", "mot_last_cuda_error", "mot_abi_version",
             "mot_workspace_bytes", "mot_solve", "mot_fastsum_workspace_bytes", "mot_fastsum",
-            "mot_fastsum_static"]
+            "mot_fastsum_static", "mot_server_create", "mot_server_submit", "mot_server_progress",
+            "mot_server_poll", "mot_server_destroy"]

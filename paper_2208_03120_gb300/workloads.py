@@ -165,10 +165,11 @@ class Request:
 
 
 def serving_stream(n_requests: int = 2000, rate_hz: float = 100.0, seed: Optional[int] = None,
-                   n_range: Tuple[int, int] = (500, 20_000), k_range: Tuple[int, int] = (3, 20)
-                   ) -> List[Request]:
+                   n_range: Tuple[int, int] = (500, 20_000), k_range: Tuple[int, int] = (3, 20),
+                   circle_n_max: Optional[int] = None) -> List[Request]:
     """Poisson arrivals; topology uniform over {path, star, circle}; K ~ U{3..20};
-    d ~ U{1,2,3}; N log-uniform on [500, 20000]; eta in {0.01, 0.05, 0.1}."""
+    d ~ U{1,2,3}; N log-uniform on [500, 20000]; eta in {0.01, 0.05, 0.1}.
+    ``circle_n_max`` caps N of circle requests (their cost grows as K N^2)."""
     rng = _rng(4, seed)
     t = 0.0
     out = []
@@ -181,6 +182,8 @@ def serving_stream(n_requests: int = 2000, rate_hz: float = 100.0, seed: Optiona
         eta = float(rng.choice([0.01, 0.05, 0.1]))
         sub = np.random.Generator(np.random.PCG64(int(rng.integers(0, 2**63 - 1))))
         if kind == 2:
+            if circle_n_max is not None:
+                N = min(N, circle_n_max)
             prob = random_problem(sub, CIRCLE, K, d, N, eta)
         else:
             prob = random_problem(sub, TREE, K, d, N, eta, shape="path" if kind == 0 else "star")

@@ -132,3 +132,14 @@ def test_circle_workspace_query(M):
     assert st == M.MOT_OK and nb > 4 * 200 * 210 * 2        # beta and gamma matrices
     p2, k2 = _fake_problem(M, 2, 1, [20, 20], None, topology=1)
     assert _ws(M, p2)[0] == M.MOT_EUNSUPPORTED              # a circle needs K >= 3
+
+
+def test_server_argument_validation(M):
+    """Invalid server arguments are rejected before any CUDA call."""
+    lib = M.lib()
+    h = C.c_void_p()
+    assert lib.mot_server_create(None, 1 << 20, 4, C.byref(h)) == M.MOT_EINVAL
+    assert lib.mot_server_create(C.c_void_p(0x1001), 1 << 20, 4, C.byref(h)) == M.MOT_EINVAL
+    assert lib.mot_server_create(C.c_void_p(0x1000), 1 << 20, 0, C.byref(h)) == M.MOT_EINVAL
+    assert lib.mot_server_progress(None, None, None) == M.MOT_EINVAL
+    assert lib.mot_server_destroy(None) == M.MOT_EINVAL
