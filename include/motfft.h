@@ -30,7 +30,7 @@
 extern "C" {
 #endif
 
-#define MOT_ABI_VERSION 1
+#define MOT_ABI_VERSION 2
 
 /* ---- status codes ---------------------------------------------------------------- */
 #define MOT_OK           0
@@ -60,7 +60,9 @@ extern "C" {
 #define MOT_K_SETUP    5    /* normalisation, binning, kernel Fourier coefficients             */
 #define MOT_K_CIRCLE   6    /* circle row-dot / column-sum scaling updates                     */
 #define MOT_K_FUSED    7    /* fused 2-D fast summation (spread, DFTs, gather in one cluster)  */
-#define MOT_NKCLASS    8
+#define MOT_K_TCGEMM   8    /* split-BF16 kernel product on the tensor cores (tcgen05)         */
+#define MOT_K_SPLIT    9    /* scaled source matrix split into BF16 hi / lo                    */
+#define MOT_NKCLASS    10
 
 /* ---- problem --------------------------------------------------------------------- */
 /* Section 2 / Section 4: K marginals mu^k on points x^k in R^d, a tree or a circle, eta. */
@@ -156,11 +158,14 @@ int mot_solve(const mot_problem* prob, const mot_options* opt, void* ws, size_t 
 /*
  * The kernel matrix-vector product of Eq. (fastsum-sum) on its own:
  *   beta_r[i] = sum_j alpha_r[j] exp(-||x_tgt[i] - x_src[j]||^2 / eta),  r = 0..nrhs-1,
- * by the fast summation of Algorithm 4 (opt->path = MOT_PATH_NFFT) or directly
- * (MOT_PATH_DENSE).  x_src: device [n_src][d] FP32; x_tgt: device [n_tgt][d];
+ * by the fast summation of Algorithm 4 (opt->path = MOT_PATH_NFFT), directly on the SIMT
+ * pipes (MOT_PATH_DENSE), or directly on the tensor cores (MOT_PATH_DENSE_BF16X3: alpha and
+ * the kernel matrix split into BF16 hi + lo, three products accumulated in FP32; relative
+ * error ~2^-16 per term).  x_src: device [n_src][d] FP32; x_tgt: device [n_tgt][d];
  * alpha: device [nrhs][n_src] FP32; beta: device [nrhs][n_tgt] FP32 (written).
  * Both point sets are mapped onto the torus together.  *scale_out (may be NULL)
- * receives the normalisation scale.  Errors: MOT_EINVAL, MOT_ENOMEM, MOT_ECUDA.
+ * receives the normalisation scale.  Errors: MOT_EINVAL, MOT_ENOMEM, MOT_ECUDA,
+ * MOT_ETIMEOUT (a bounded wait of the tensor-core kernel expired).
  */
 int mot_fastsum_workspace_bytes(int d, int64_t n_src, int64_t n_tgt, int nrhs,
                                 const mot_options* opt, size_t* bytes);

@@ -99,3 +99,33 @@ cudaError_t launch_colsum(const float* A, const VecScale* sA, const float* B, co
 // K[c][i] = exp(-||u_i - u_c||^2 / eta_u) (column-major, grid units); scale record ls = 0, mx = 1.
 cudaError_t launch_kernel_matrix(const float* ui, int ni, const float* uc, int nc, int d, float eta_u, float* K,
                                  VecScale* sc, cudaStream_t st);
+
+// ---- dense products on the tensor cores, BF16 hi + lo split (tc_gemm.cu) ------------------
+// Y[c][i] = sum_j A[c][j] B[i][j] with A = Ahi + Alo (M x K), B = Bhi + Blo (N x K), BF16,
+// row strides lda / ldb (multiples of 8 elements); FP32 accumulation of Ahi Bhi + Ahi Blo + Alo Bhi.
+struct TcGemm {
+    alignas(64) unsigned char maps[4][128];   // TMA tensor maps of Ahi, Alo, Bhi, Blo
+    int M, N, K, bn;
+};
+struct TcEpi {
+    int M, N, K;              // filled from the TcGemm by the launcher
+    float* out;               // out[c * ldo + i]
+    long long ldo;
+    int mode;                 // 0: plain product; 1: message (floor, maximum, clamp count, log-scale)
+    float floor_;
+    VecScale* out_sc;         // mode 1: scale record of the output (mx reset by the caller)
+    const VecScale* s_a;      // mode 1: scale records whose log-scales sum to that of the output
+    const VecScale* s_b;
+    int* err;                 // bit 4 set when a bounded wait expired
+};
+int tc_ld(int k);             // padded row stride (elements) of a split operand with k columns
+cudaError_t prepare_tc_gemm();
+bool tc_prepare(TcGemm* g, const void* a_hi, const void* a_lo, int M, int lda, const void* b_hi, const void* b_lo,
+                int N, int ldb, int K);
+cudaError_t launch_tc_gemm(const TcGemm& g, TcEpi e, cudaStream_t st);
+// hi/lo[c][j] of (phi_j / max phi)(X[c][j] / max X), X column c contiguous over j (phi may be null).
+cudaError_t launch_split_src(const float* X, const VecScale* sX, const float* phi, const VecScale* sP, int ns,
+                             int nrow, int ld, void* hi, void* lo, cudaStream_t st);
+// hi/lo[i][j] of exp(-||ut_i - us_j||^2 / eta_u) (grid units).
+cudaError_t launch_kernel_split(const float* ut, int nt, const float* us, int ns, int d, float eta_u, int ld,
+                                void* hi, void* lo, cudaStream_t st);

@@ -923,6 +923,13 @@ struct CBatch {
     Task* d_tasks = nullptr;
     VecScale* out_sc = nullptr;
     int grid_src = 1, grid_tgt = 1, ntb = 1, nsplit = 1;
+    // tensor-core path: Y = X' K^T with X' = split(phi^s (.) X), K = kernel matrix (n_t x n_s)
+    float* X = nullptr;
+    VecScale* sX = nullptr;
+    float* Y = nullptr;
+    uint16_t* kt_hi = nullptr;
+    uint16_t* kt_lo = nullptr;
+    TcGemm tc;
 };
 
 struct CirclePlan {
@@ -957,6 +964,9 @@ struct CirclePlan {
     std::vector<VecScale*> resets;
     size_t it_r0 = 0, it_rn = 0, bw_r0 = 0, bw_rn = 0, ck_r0 = 0, ck_rn = 0;
     std::vector<CBatch> fwd, bwd;   // fwd[k] produces Gam_k (k >= 2); bwd[k] produces beta_k (k <= K-2)
+    uint16_t* a_hi = nullptr;       // tensor-core path: split source matrix, n0 x ld (BF16 pairs)
+    uint16_t* a_lo = nullptr;
+    std::vector<uint16_t*> ktf_hi, ktf_lo, ktb_hi, ktb_lo;   // split kernel matrices per batch
     std::vector<Task> node_tasks;   // [0] root update, [1..K-1] phi^k updates, [K..2K-1] check marginals
     Task* d_node = nullptr;
     Globals G;
@@ -973,10 +983,14 @@ struct CirclePlan {
 void layout_circle(Arena& A, CirclePlan& C) {
     const int K = C.K, d = C.d, ng = C.g.n, M = C.g.M;
     const bool nfft = C.path == MOT_PATH_NFFT;
+    const bool tc = C.path == MOT_PATH_DENSE_BF16X3;
     size_t gsz = 1;
     for (int t = 0; t < d; ++t) gsz *= ng;
-    int nmax = 0;
-    for (int k = 0; k < K; ++k) nmax = std::max(nmax, C.n[k]);
+    int nmax = 0, ldmax = 0;
+    for (int k = 0; k < K; ++k) {
+        nmax = std::max(nmax, C.n[k]);
+        ldmax = std::max(ldmax, tc_ld(C.n[k]));
+    }
     C.sets.assign(K, SetBufs());
     for (int k = 0; k < K; ++k) layout_set(A, C.sets[k], C.n[k], d, ng, true);
     C.phi.assign(K, nullptr);
@@ -1001,8 +1015,24 @@ void layout_circle(Arena& A, CirclePlan& C) {
             C.grid[c] = A.take<float>(gsz);
             C.hgrid[c] = A.take<float>(gsz);
             if (d == 3) C.spec[c] = A.take<float2>((size_t)ng * (2 * M + 1) * (M + 1));
-        } else {
+        } else if (!tc) {
             C.rawm[c] = A.take<float>(nmax);
+        }
+    }
+    C.ktf_hi.assign(K, nullptr);
+    C.ktf_lo.assign(K, nullptr);
+    C.ktb_hi.assign(K, nullptr);
+    C.ktb_lo.assign(K, nullptr);
+    if (tc) {
+        C.a_hi = A.take<uint16_t>((size_t)C.n0 * ldmax);
+        C.a_lo = A.take<uint16_t>((size_t)C.n0 * ldmax);
+        for (int k = 2; k < K; ++k) {       // Gam_k from Gam_{k-1}: n_k x n_{k-1}
+            C.ktf_hi[k] = A.take<uint16_t>((size_t)C.n[k] * tc_ld(C.n[k - 1]));
+            C.ktf_lo[k] = A.take<uint16_t>((size_t)C.n[k] * tc_ld(C.n[k - 1]));
+        }
+        for (int k = 1; k <= K - 2; ++k) {  // beta_k from beta_{k+1}: n_k x n_{k+1}
+            C.ktb_hi[k] = A.take<uint16_t>((size_t)C.n[k] * tc_ld(C.n[k + 1]));
+            C.ktb_lo[k] = A.take<uint16_t>((size_t)C.n[k] * tc_ld(C.n[k + 1]));
         }
     }
     if (nfft)
@@ -1048,6 +1078,9 @@ void c_build_batch(CirclePlan& C, CBatch& B, int s, int t, int edge, float* X, V
     B.t = t;
     B.edge = edge;
     B.out_sc = sY;
+    B.X = X;
+    B.sX = sX;
+    B.Y = Y;
     B.tasks.clear();
     const double eta_n = (C.eta / C.w[edge]) / (C.g.s * C.g.s);
     for (int c = 0; c < C.n0; ++c) {
@@ -1163,7 +1196,10 @@ int c_upload(CirclePlan& C, cudaStream_t st) {
     return MOT_OK;
 }
 
+int c_run_batch_tc(CirclePlan& C, CBatch& B, cudaStream_t st, Timer& tm, long long& nl);
+
 int c_run_batch(CirclePlan& C, CBatch& B, cudaStream_t st, Timer& tm, long long& nl) {
+    if (C.path == MOT_PATH_DENSE_BF16X3) return c_run_batch_tc(C, B, st, tm, nl);
     cudaEvent_t e = nullptr;
     for (int c0 = 0; c0 < C.n0; c0 += C.CB) {
         const int cnt = std::min(C.CB, C.n0 - c0);
@@ -1190,6 +1226,29 @@ int c_run_batch(CirclePlan& C, CBatch& B, cudaStream_t st, Timer& tm, long long&
             nl += 2;
         }
     }
+    return MOT_OK;
+}
+
+// Tensor-core batch: the whole n_t x n0 message matrix as one split-BF16 product.
+int c_run_batch_tc(CirclePlan& C, CBatch& B, cudaStream_t st, Timer& tm, long long& nl) {
+    cudaEvent_t e = nullptr;
+    RET(tm.begin(MOT_K_SPLIT, &e));
+    CK(launch_split_src(B.X, B.sX, C.phi[B.s], C.phi_sc(B.s), C.n[B.s], C.n0, tc_ld(C.n[B.s]), C.a_hi, C.a_lo, st));
+    RET(tm.end(e));
+    TcEpi ep;
+    std::memset(&ep, 0, sizeof(ep));
+    ep.out = B.Y;
+    ep.ldo = C.n[B.t];
+    ep.mode = 1;
+    ep.floor_ = C.G.floor_;
+    ep.out_sc = B.out_sc;
+    ep.s_a = C.phi_sc(B.s);
+    ep.s_b = B.sX;
+    ep.err = C.err;
+    RET(tm.begin(MOT_K_TCGEMM, &e));
+    CK(launch_tc_gemm(B.tc, ep, st));
+    RET(tm.end(e));
+    nl += 2;
     return MOT_OK;
 }
 
@@ -1288,7 +1347,8 @@ int circle_setup(const mot_problem* P, const mot_options& o, CirclePlan& C, void
     C.eta = P->eta;
     C.path = o.path;
     C.o = o;
-    if (C.path != MOT_PATH_NFFT && C.path != MOT_PATH_DENSE) return MOT_EUNSUPPORTED;
+    if (C.path != MOT_PATH_NFFT && C.path != MOT_PATH_DENSE && C.path != MOT_PATH_DENSE_BF16X3)
+        return MOT_EUNSUPPORTED;
     C.n.resize(K);
     for (int k = 0; k < K; ++k) C.n[k] = (int)P->n[k];
     C.n0 = C.n[0];
@@ -1346,17 +1406,39 @@ int circle_setup(const mot_problem* P, const mot_options& o, CirclePlan& C, void
                 RET(make_D_for((C.eta / C.w[k]) / (g.s * g.s), g, C.d, o, C.dscr_a, C.dscr_b, C.D[k], st));
         }
         for (int c = 0; c < C.CB; ++c) CK(cudaMemsetAsync(C.grid[c], 0, gsz * sizeof(float), st));
-    } else {
+    } else if (C.path == MOT_PATH_DENSE) {
         int nmax = 0;
         for (int k = 0; k < K; ++k) nmax = std::max(nmax, C.n[k]);
         for (int c = 0; c < C.CB; ++c) CK(cudaMemsetAsync(C.rawm[c], 0, sizeof(float) * nmax, st));
     }
     // fixed dense kernel matrices: beta_{K-1} = K^{(K-1,0)}, Gam_1 = K^{(1,0)}
     auto eta_u = [&](int edge) { return (float)((C.eta / C.w[edge]) / (g.s * g.s) * (double)g.n * (double)g.n); };
+    if (C.path == MOT_PATH_DENSE_BF16X3) {
+        // split kernel matrices of the batched products (fixed for the solve)
+        CK(prepare_tc_gemm());
+        for (int k = 2; k < K; ++k)
+            CK(launch_kernel_split(C.sets[k].u, C.n[k], C.sets[k - 1].u, C.n[k - 1], C.d, eta_u(k - 1),
+                                   tc_ld(C.n[k - 1]), C.ktf_hi[k], C.ktf_lo[k], st));
+        for (int k = 1; k <= K - 2; ++k)
+            CK(launch_kernel_split(C.sets[k].u, C.n[k], C.sets[k + 1].u, C.n[k + 1], C.d, eta_u(k),
+                                   tc_ld(C.n[k + 1]), C.ktb_hi[k], C.ktb_lo[k], st));
+    }
     CK(launch_kernel_matrix(C.sets[K - 1].u, C.n[K - 1], C.sets[0].u, C.n0, C.d, eta_u(K - 1), C.beta[K - 1],
                             C.beta_sc(K - 1), st));
     CK(launch_kernel_matrix(C.sets[1].u, C.n[1], C.sets[0].u, C.n0, C.d, eta_u(0), C.gam[1], C.gam_sc(1), st));
     c_build(C);
+    if (C.path == MOT_PATH_DENSE_BF16X3) {
+        for (int k = 2; k < K; ++k) {
+            const int ld = tc_ld(C.n[k - 1]);
+            if (!tc_prepare(&C.fwd[k].tc, C.a_hi, C.a_lo, C.n0, ld, C.ktf_hi[k], C.ktf_lo[k], C.n[k], ld, C.n[k - 1]))
+                return MOT_ECUDA;
+        }
+        for (int k = 1; k <= K - 2; ++k) {
+            const int ld = tc_ld(C.n[k + 1]);
+            if (!tc_prepare(&C.bwd[k].tc, C.a_hi, C.a_lo, C.n0, ld, C.ktb_hi[k], C.ktb_lo[k], C.n[k], ld, C.n[k + 1]))
+                return MOT_ECUDA;
+        }
+    }
     RET(c_upload(C, st));
     return MOT_OK;
 }
@@ -1522,7 +1604,7 @@ struct Solve {
         const int K = ops->K();
         const IterAcc* acc = reinterpret_cast<const IterAcc*>(hstats);
         const double* node = reinterpret_cast<const double*>(hstats + sizeof(IterAcc) * kRing);
-        if (*reinterpret_cast<const int*>(hstats + sb - 16)) return MOT_ENUMERIC;
+        if (const int e = *reinterpret_cast<const int*>(hstats + sb - 16)) return (e & 4) ? MOT_ETIMEOUT : MOT_ENUMERIC;
         viol = 0.0;
         for (int k = 0; k < K; ++k)
             if (ops->constrained(k)) viol = std::max(viol, node[3 * k]);
@@ -1729,6 +1811,10 @@ struct FsPlan {
     std::vector<float2*> spec;
     float* D = nullptr;
     float* a_sorted = nullptr;   // [nrhs][n_src]
+    uint16_t* a_hi = nullptr;    // tensor-core path: split alpha [nrhs][ld] and kernel [n_tgt][ld]
+    uint16_t* a_lo = nullptr;
+    uint16_t* kt_hi = nullptr;
+    uint16_t* kt_lo = nullptr;
     float* b_sorted = nullptr;   // [nrhs][n_tgt]
     PrepSet* d_sets = nullptr;
     float* box_scratch = nullptr;
@@ -1756,9 +1842,16 @@ void layout_fs(Arena& A, FsPlan& F, int d, int64_t ns, int64_t nt, int nrhs, int
             F.grid[r] = A.take<float>(gsz);
             F.hgrid[r] = A.take<float>(gsz);
             if (d == 3) F.spec[r] = A.take<float2>((size_t)ng * (2 * M + 1) * (M + 1));
-        } else {
+        } else if (path == MOT_PATH_DENSE) {
             F.raw[r] = A.take<float>(nt);
         }
+    }
+    if (path == MOT_PATH_DENSE_BF16X3) {
+        const size_t ld = (size_t)tc_ld((int)ns);
+        F.a_hi = A.take<uint16_t>((size_t)nrhs * ld);
+        F.a_lo = A.take<uint16_t>((size_t)nrhs * ld);
+        F.kt_hi = A.take<uint16_t>((size_t)nt * ld);
+        F.kt_lo = A.take<uint16_t>((size_t)nt * ld);
     }
     if (path == MOT_PATH_NFFT) {
         F.D = A.take<float>(D_floats(d, M));
@@ -1783,7 +1876,8 @@ int fastsum_impl(int d, double eta, const float* x_src, int64_t n_src, const flo
     if (d < 1 || d > 3 || n_src < 1 || n_tgt < 1 || nrhs < 1 || nrhs > 65535) return MOT_EINVAL;
     if (n_src > (1 << 26) || n_tgt > (1 << 26)) return MOT_EINVAL;
     if (!(eta > 0.0) || !std::isfinite(eta)) return MOT_EINVAL;
-    if (o.path != MOT_PATH_NFFT && o.path != MOT_PATH_DENSE) return MOT_EUNSUPPORTED;
+    if (o.path != MOT_PATH_NFFT && o.path != MOT_PATH_DENSE && o.path != MOT_PATH_DENSE_BF16X3)
+        return MOT_EUNSUPPORTED;
     const int ngmax = o.n_grid > 0 ? o.n_grid : max_grid(d);
     if (ngmax < 16 || ngmax > max_grid(d) || (ngmax & (ngmax - 1))) return MOT_EINVAL;
     FsPlan F;
@@ -1820,7 +1914,7 @@ int fastsum_impl(int d, double eta, const float* x_src, int64_t n_src, const flo
         CK(prepare_fftconv(d, g.n));
         RET(make_D_for(eta_n, g, d, o, F.dscr_a, F.dscr_b, F.D, st));
         for (int r = 0; r < nrhs; ++r) CK(cudaMemsetAsync(F.grid[r], 0, gsz * sizeof(float), st));
-    } else {
+    } else if (o.path == MOT_PATH_DENSE) {
         for (int r = 0; r < nrhs; ++r) CK(cudaMemsetAsync(F.raw[r], 0, sizeof(float) * n_tgt, st));
     }
     for (int r = 0; r < nrhs; ++r)
@@ -1855,6 +1949,21 @@ int fastsum_impl(int d, double eta, const float* x_src, int64_t n_src, const flo
         CK(launch_spread(d, F.d_tasks, nrhs, gx, G, st));
         CK(launch_fftconv(d, F.d_tasks, nrhs, G, st, nullptr));
         CK(launch_gather(d, F.d_tasks, nrhs, gt, G, st));
+    } else if (o.path == MOT_PATH_DENSE_BF16X3) {
+        const int ld = tc_ld((int)n_src);
+        CK(prepare_tc_gemm());
+        CK(launch_kernel_split(F.tgt.u, (int)n_tgt, F.src.u, (int)n_src, d, (float)(eta_n * (double)g.n * (double)g.n),
+                               ld, F.kt_hi, F.kt_lo, st));
+        CK(launch_split_src(F.a_sorted, nullptr, nullptr, nullptr, (int)n_src, nrhs, ld, F.a_hi, F.a_lo, st));
+        TcGemm tg;
+        if (!tc_prepare(&tg, F.a_hi, F.a_lo, nrhs, ld, F.kt_hi, F.kt_lo, (int)n_tgt, ld, (int)n_src)) return MOT_ECUDA;
+        TcEpi ep;
+        std::memset(&ep, 0, sizeof(ep));
+        ep.out = F.b_sorted;
+        ep.ldo = n_tgt;
+        ep.mode = 0;
+        ep.err = F.err;
+        CK(launch_tc_gemm(tg, ep, st));
     } else {
         int ntb = (int)((n_tgt + 511) / 512);
         int split = std::max(1, std::min(64, 4 * 152 / std::max(1, ntb * nrhs)));
@@ -1866,7 +1975,7 @@ int fastsum_impl(int d, double eta, const float* x_src, int64_t n_src, const flo
     int err = 0;
     CK(cudaMemcpyAsync(&err, F.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (err) return MOT_ENUMERIC;
+    if (err) return (err & 4) ? MOT_ETIMEOUT : MOT_ENUMERIC;
     return MOT_OK;
 }
 

@@ -63,7 +63,7 @@ def assert_parity(prob, u_gpu, u_or, out):
         assert np.max(np.abs(va - vb)) <= 1e-3 * scale
 
 
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("path", [0, 1, 2])
 @pytest.mark.parametrize("K,d,n,eta", [(3, 1, 300, 0.05), (4, 2, 250, 0.03), (5, 1, 500, 0.05), (3, 3, 200, 0.1)])
 def test_small_circles_to_tolerance(M, path, K, d, n, eta):
     rng = np.random.default_rng(zlib.crc32(f"circle-{K}-{d}-{n}".encode()))
@@ -87,13 +87,15 @@ def test_circle_fixed_iterations_match_oracle(M):
 
 
 def test_circle5_workload_full_size(M):
-    """The 5-marginal d=1 circle workload at full size (N = 2000, eta = 0.05), NFFT and dense
-    paths to violation 1e-6; the oracle evaluates both results with exact kernels."""
+    """The 5-marginal d=1 circle workload at full size (N = 2000, eta = 0.05): NFFT, dense SIMT
+    and dense tensor-core paths to violation 1e-6; the oracle evaluates every result with
+    exact kernels."""
     prob = W.circle5_d1()
-    o1, u1 = gpu_solve(M, prob, tol_viol=1e-6, max_iter=3000)
-    o2, u2 = gpu_solve(M, prob, path=1, tol_viol=1e-6, max_iter=3000)
-    assert o1.status == 0 and o2.status == 0, (o1.iters, o1.violation, o2.iters, o2.violation)
-    r1, r2 = exact_report(prob, u1), exact_report(prob, u2)
-    assert r1["viol"] <= REL and r2["viol"] <= REL
-    assert abs(r1["dual"] - r2["dual"]) <= REL * abs(r2["dual"])
-    assert abs(o1.cost_dual - r1["dual"]) <= REL * abs(r1["dual"])
+    outs = [gpu_solve(M, prob, path=p, tol_viol=1e-6, max_iter=3000) for p in (0, 1, 2)]
+    for o, _ in outs:
+        assert o.status == 0, (o.iters, o.violation)
+    reps = [exact_report(prob, u) for _, u in outs]
+    for (o, _), r in zip(outs, reps):
+        assert r["viol"] <= REL
+        assert abs(r["dual"] - reps[1]["dual"]) <= REL * abs(reps[1]["dual"])
+        assert abs(o.cost_dual - r["dual"]) <= REL * abs(r["dual"])
