@@ -31,6 +31,7 @@ if ROOT not in sys.path:
 METRIC = "Sinkhorn iters/s, NFFT vs dense BF16-split at marginal err≤1e-6; p50/p99 latency"
 WORKLOAD = "path10_d2"
 TOL = 1e-6
+ROOT_CENTRE = -1             # Algorithm 2 rooted at a centre of the tree (fewest backward levels)
 FLUSH_BYTES = 256 << 20      # > 129 MB L2
 
 
@@ -46,6 +47,8 @@ def parse():
                     help="profiling runs only: the reported line is defined on path10_d2")
     ap.add_argument("--n", type=int, default=0, help="profiling runs only: points per marginal")
     ap.add_argument("--max-iter", type=int, default=5000, help="profiling runs only: iteration cap")
+    ap.add_argument("--serving-requests", type=int, default=32,
+                    help="requests of the Poisson-arrival serving replay (0: skip)")
     return ap.parse_args()
 
 
@@ -111,33 +114,28 @@ class ClockSampler:
 # algorithmic bytes of the fast-summation kernels (per launch, for the roofline)
 # ----------------------------------------------------------------------------------------
 def algorithmic_bytes(prob, n_grid):
-    """Bytes the method must move per launch of each kernel class, averaged over one
-    iteration's launches (FP32 values, FP64 weights; window tables excluded).
+    """Bytes the method must move per kernel product, by kernel class (FP32 values, FP64
+    weights; window tables excluded), averaged over the forward (gamma, scaling update) and
+    backward (beta) products of a sweep:
 
-    spread : source coordinates (4 d N) + source factors (4 N each) + grid write (4 n^d)
+    spread : source coordinates (4 d N) + source factors (4 N each, 2 on average) + grid write (4 n^d)
     fftconv: grid read + grid write (8 n^d)
-    gather : grid read (4 n^d) + target coordinates (4 d N) + target factors (4 N each)
-             + message / scaling write (4 N) [+ mu (12 N) on scaling updates]
+    gather : grid read (4 n^d) + target coordinates (4 d N) + target factors / message (8 N on
+             average) + on forward products the scaling write and mu (16 N)
+    fused  : spread + gather without the grid round trips (the grid stays in shared memory)
     """
-    K, d = prob.K, prob.d
-    N = prob.n[0]
+    d, N = prob.d, prob.n[0]
     G = 4 * n_grid ** d
-    # path tree: forward level = K-1 tasks (2 source factors; targets: <=1 child factor, mu,
-    # phi write), backward = K-1 levels of 1 task (phi + <=1 child factor; message write)
-    fwd_spread = (K - 1) * (4 * d * N + 8 * N + G)
-    fwd_gather = (K - 1) * (G + 4 * d * N + 4 * N + 12 * N + 4 * N + 4 * N) + (4 * N + 12 * N + 4 * N)
-    bwd_spread = 4 * d * N + 8 * N + G
-    bwd_gather = G + 4 * d * N + 4 * N
-    launches = K   # one forward launch + (K-1) backward launches per class
-    out = {
-        "spread": (fwd_spread + (K - 1) * bwd_spread) / launches,
-        "gather": (fwd_gather + (K - 1) * bwd_gather) / launches,
-        "fftconv": ((K - 1) * 2 * G + (K - 1) * 2 * G) / launches,
-    }
-    # the fused 2-D kernel does all three with the grid in shared memory: its algorithmic
-    # bytes are the point data and the vectors only (no grid round trips)
-    out["fused"] = out["spread"] + out["gather"] - 2 * G * (2 * (K - 1)) / launches
-    return out
+    spread = 4 * d * N + 8 * N + G
+    gather = G + 4 * d * N + 8 * N + 8 * N          # forward products add 16 N, backward none
+    return {"spread": spread, "gather": gather, "fftconv": 2 * G, "fused": spread + gather - 2 * G}
+
+
+def products_per_solve(prob, iters, check_every):
+    """Kernel products executed by one solve: the initial backward pass, 2(K-1) per sweep and
+    the K-1 forward products of each check pass."""
+    checks = -(-iters // check_every)
+    return (1 + 2 * iters + checks) * (prob.K - 1)
 
 
 def kernel_source_hash(cls):
@@ -214,6 +212,151 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def tc_roofline(M, wp, wx, wm, topo, wo, wws, stream, flush):
+    """Tensor-core roofline of the split-BF16 circle path: per GEMM launch the three BF16
+    products of the batched column product, 3 x 2 n0 n_t n_s flops, over the launch's
+    CUDA-event duration, against the measured dense BF16 peak (burst: each launch is short)."""
+    import torch
+    topt = M.options(path=M.MOT_PATH_DENSE_BF16X3, tol_viol=TOL, max_iter=3000, timing=1)
+    with torch.cuda.stream(stream):
+        flush.random_(0, 255)
+    o = M.mot_solve(wx, wm, wp.eta, topo, edges=wp.edges, opt=topt, workspace=wws, stream=stream)
+    torch.cuda.synchronize()
+    n = wp.n
+    # batches: Gam_k (k = 2..K-1) from Gam_{k-1}, beta_k (k = 1..K-2) from beta_{k+1}
+    flops = [6.0 * n[0] * n[k] * n[k - 1] for k in range(2, wp.K)] + \
+            [6.0 * n[0] * n[k] * n[k + 1] for k in range(1, wp.K - 1)]
+    per_launch = sum(flops) / len(flops)
+    launches = o.kernel_launches["tcgemm"]
+    avg_s = o.kernel_ms["tcgemm"] / 1e3 / max(1, launches)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("bf16_tflops", 1900.0)
+    achieved = per_launch / avg_s / 1e12
+    total = sum(o.kernel_ms.values())
+    return {"bound": "tensor", "kernel": "tcgemm", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": "measured burst" if "bf16_tflops" in peaks else "fallback",
+            "avg_launch_us": avg_s * 1e6, "alg_flops_per_launch": per_launch,
+            "share": {k: round(v / total, 4) for k, v in o.kernel_ms.items() if v > 0}}
+
+
+def scaleup_tree(M, W, dev, stream, flush, n=1_000_000):
+    """The 10-node d=2 path workload scaled to N = 10^6 points per marginal (same
+    distributions): there the products are large enough for the HBM roofline to mean
+    something.  NFFT path to violation 1e-6; roofline of its dominant kernel class."""
+    import torch
+    prob = W.path10_d2(n=n)
+    prob.root = ROOT_CENTRE
+    x = [torch.from_numpy(a).to(dev) for a in prob.x]
+    mu = [torch.from_numpy(m).to(dev) for m in prob.mu]
+    opt = M.options(path=M.MOT_PATH_NFFT, tol_viol=TOL, max_iter=3000)
+    ws = torch.empty(M.mot_workspace_bytes(x, mu, prob.eta, M.MOT_TREE, edges=prob.edges, root=prob.root, opt=opt),
+                     dtype=torch.uint8, device=dev)
+
+    def solve(o):
+        with torch.cuda.stream(stream):
+            flush.random_(0, 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = M.mot_solve(x, mu, prob.eta, M.MOT_TREE, edges=prob.edges, root=prob.root, opt=o, workspace=ws,
+                              stream=stream)
+            e1.record(stream)
+        e1.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    solve(opt)
+    tt, ti = 0.0, 0
+    for _ in range(2):
+        out, t = solve(opt)
+        tt += t
+        ti += out.iters
+    ot, _ = solve(M.options(path=M.MOT_PATH_NFFT, tol_viol=TOL, max_iter=3000, timing=1))
+    share = {k: v / sum(ot.kernel_ms.values()) for k, v in ot.kernel_ms.items() if v > 0}
+    dom = max(share, key=share.get)
+    alg = algorithmic_bytes(prob, ot.n_grid)
+    prods = products_per_solve(prob, ot.iters, 10)
+    avg_s = ot.kernel_ms[dom] / 1e3 / ot.kernel_launches[dom]
+    per_launch = alg.get(dom, 0.0) * prods / ot.kernel_launches[dom]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = per_launch / avg_s / 1e9
+    return {"value": ti / tt, "unit": "iters/s", "N": n, "iters_per_solve": out.iters, "violation": out.violation,
+            "status": out.status, "n_grid": ot.n_grid,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "avg_launch_us": avg_s * 1e6, "alg_bytes_per_launch": per_launch,
+                         "share": {k: round(v, 4) for k, v in share.items()}}}
+
+
+def serving_replay(M, W, dev, n_requests, flush):
+    """Poisson-arrival replay through the continuous-batching server (mot_server_*).
+
+    Requests: topology uniform over {path, star, circle}, K ~ U{3..20}, d ~ U{1,2,3},
+    N log-uniform on [500, 20000] (circles capped at N = 2000: their messages are K N^2),
+    eta in {0.01, 0.05, 0.1}; each solved to violation 1e-6 with at most 500 sweeps.
+    Inputs are uploaded before the replay.  The arrival rate is 75% of the capacity measured
+    by solving the first requests one after another; latency = completion - arrival.
+    Path per request: NFFT for trees and d = 1 circles; circles in d >= 2 take the tensor-core
+    dense path (their N right-hand sides make the batched NFFT launch-bound)."""
+    import torch
+    reqs = W.serving_stream(n_requests=n_requests, rate_hz=1.0, seed=None, circle_n_max=2000)
+    opt_nfft = M.options(path=M.MOT_PATH_NFFT, tol_viol=TOL, max_iter=500)
+    opt_tc = M.options(path=M.MOT_PATH_DENSE_BF16X3, tol_viol=TOL, max_iter=500)
+
+    def opt_of(p):
+        return opt_tc if (p.topology == W.CIRCLE and p.d >= 2) else opt_nfft
+    dev_in = []
+    for r in reqs:
+        p = r.problem
+        dev_in.append(([torch.from_numpy(a).to(dev) for a in p.x], [torch.from_numpy(m).to(dev) for m in p.mu]))
+    torch.cuda.synchronize()
+    # single-stream capacity from the first requests, solved one after another
+    n_cal = min(8, n_requests)
+    t0 = time.perf_counter()
+    for i in range(n_cal):
+        p = reqs[i].problem
+        M.mot_solve(*dev_in[i], p.eta, p.topology, edges=p.edges, opt=opt_of(p))
+    torch.cuda.synchronize()
+    service = (time.perf_counter() - t0) / n_cal
+    rate = 0.75 / service
+    gaps = [reqs[0].arrival_s] + [reqs[i].arrival_s - reqs[i - 1].arrival_s for i in range(1, n_requests)]
+    arrivals, t = [], 0.0
+    for g in gaps:                      # the stream's exponential gaps rescaled to the chosen rate
+        t += g / rate
+        arrivals.append(t)
+    srv = M.Server(pool_bytes=16 << 30, max_active=8, device=dev)
+    done, nxt = {}, 0
+    start = time.perf_counter()
+    while len(done) < n_requests:
+        now = time.perf_counter() - start
+        while nxt < n_requests and arrivals[nxt] <= now:
+            p = reqs[nxt].problem
+            srv.submit(*dev_in[nxt], p.eta, p.topology, edges=p.edges, opt=opt_of(p), tag=nxt)
+            nxt += 1
+        active, pending = srv.progress()
+        for res in srv.poll():
+            done[res["tag"]] = (time.perf_counter() - start, res)
+        if nxt < n_requests and active == 0 and pending == 0:
+            time.sleep(max(0.0, min(0.002, arrivals[nxt] - (time.perf_counter() - start))))
+    wall = time.perf_counter() - start
+    srv.close()
+    lat = sorted(done[i][0] - arrivals[i] for i in range(n_requests))
+    iters = sum(done[i][1]["iters"] for i in range(n_requests))
+    status = {}
+    for i in range(n_requests):
+        s_ = M.strerror(done[i][1]["status"])
+        status[s_] = status.get(s_, 0) + 1
+    pct = lambda q: 1e3 * lat[min(len(lat) - 1, int(q * len(lat)))]   # noqa: E731
+    return {"requests": n_requests, "arrival_rate_hz": rate, "single_stream_service_ms": 1e3 * service,
+            "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "max": 1e3 * lat[-1]},
+            "throughput_req_s": n_requests / wall, "iters_per_s": iters / wall, "status": status,
+            "max_active": 8, "pool_gb": 16, "max_iter": 500,
+            "mix": "path/star/circle, K 3-20, d 1-3, N 500-20000 (circle <= 2000)",
+            "path_policy": "NFFT for trees and d=1 circles, tensor-core dense for d>=2 circles",
+            "n_tensor_core": sum(1 for r in reqs if r.problem.topology == W.CIRCLE and r.problem.d >= 2)}
+
+
 # ----------------------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------------------
@@ -234,12 +377,13 @@ def main():
     dev = torch.device("cuda", local)
     build.build()
     prob = W.WORKLOADS[args.workload](n=args.n) if args.n else W.WORKLOADS[args.workload]()
+    prob.root = ROOT_CENTRE
     x = [torch.from_numpy(a).to(dev) for a in prob.x]
     mu = [torch.from_numpy(m).to(dev) for m in prob.mu]
     stream = torch.cuda.Stream(device=dev)
     tol = TOL if args.max_iter >= 5000 else -1.0
     opt = M.options(path=M.MOT_PATH_NFFT, tol_viol=tol, max_iter=args.max_iter)
-    ws = torch.empty(M.mot_workspace_bytes(x, mu, prob.eta, M.MOT_TREE, edges=prob.edges, opt=opt),
+    ws = torch.empty(M.mot_workspace_bytes(x, mu, prob.eta, M.MOT_TREE, edges=prob.edges, root=prob.root, opt=opt),
                      dtype=torch.uint8, device=dev)
     u = [torch.empty(n, dtype=torch.float64, device=dev) for n in prob.n]
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -250,8 +394,8 @@ def main():
 
     def solve(o=opt):
         with torch.cuda.stream(stream):
-            return M.mot_solve(x, mu, prob.eta, M.MOT_TREE, edges=prob.edges, opt=o, workspace=ws, stream=stream,
-                               u_out=u)
+            return M.mot_solve(x, mu, prob.eta, M.MOT_TREE, edges=prob.edges, root=prob.root, opt=o, workspace=ws,
+                               stream=stream, u_out=u)
 
     for _ in range(args.warmup):
         out = solve()
@@ -305,15 +449,19 @@ def main():
     share = {k: kms[k] / sum(kms.values()) for k in kms if kms[k] > 0}
     dom = max(share, key=share.get)
     alg = algorithmic_bytes(prob, last.n_grid)
+    nsolve = max(1, min(args.steps, 3))
+    prods = nsolve * products_per_solve(prob, o2.iters, 10)
     avg_s = kms[dom] / 1e3 / kls[dom]
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = alg.get(dom, 0.0) / avg_s / 1e9
+    per_launch = alg.get(dom, 0.0) * prods / kls[dom]
+    achieved = per_launch / avg_s / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": load_traffic(dom),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "avg_launch_us": avg_s * 1e6, "alg_bytes_per_launch": alg.get(dom),
+                "avg_launch_us": avg_s * 1e6, "alg_bytes_per_launch": per_launch,
+                "alg_bytes_per_product": alg.get(dom), "products_per_launch": prods / kls[dom],
                 "share": {k: round(v, 4) for k, v in share.items()}}
 
     # ---- dense comparison on the same workload -------------------------------------------
@@ -328,8 +476,8 @@ def main():
                 flush.random_(0, 255)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                o3 = M.mot_solve(x, mu, prob.eta, M.MOT_TREE, edges=prob.edges, opt=dopt, workspace=dws,
-                                 stream=stream)
+                o3 = M.mot_solve(x, mu, prob.eta, M.MOT_TREE, edges=prob.edges, root=prob.root, opt=dopt,
+                                 workspace=dws, stream=stream)
                 e1.record(stream)
             e1.synchronize()
             if r > 0:
@@ -347,7 +495,10 @@ def main():
             wx = [torch.from_numpy(a).to(dev) for a in wp.x]
             wm = [torch.from_numpy(m).to(dev) for m in wp.mu]
             entry = {}
-            for pname, path, reps in (("nfft", M.MOT_PATH_NFFT, 3), ("dense", M.MOT_PATH_DENSE, 2)):
+            paths = [("nfft", M.MOT_PATH_NFFT, 3), ("dense", M.MOT_PATH_DENSE, 2)]
+            if topo == M.MOT_CIRCLE:
+                paths.append(("dense_bf16x3", M.MOT_PATH_DENSE_BF16X3, 3))
+            for pname, path, reps in paths:
                 wo = M.options(path=path, tol_viol=TOL, max_iter=3000)
                 wws = torch.empty(M.mot_workspace_bytes(wx, wm, wp.eta, topo, edges=wp.edges, opt=wo),
                                   dtype=torch.uint8, device=dev)
@@ -365,8 +516,19 @@ def main():
                         ti += ow.iters
                 entry[pname] = {"value": ti / tt, "unit": "iters/s", "iters_per_solve": ow.iters,
                                 "violation": ow.violation, "status": ow.status}
+                if path == M.MOT_PATH_DENSE_BF16X3:
+                    entry[pname]["roofline"] = tc_roofline(M, wp, wx, wm, topo, wo, wws, stream, flush)
                 del wws
             others[wname] = entry
+
+    # ---- scale-up of the headline workload (N = 10^6) ---------------------------------------
+    if not args.no_dense and args.workload == WORKLOAD:
+        others["path10_d2_N1e6"] = scaleup_tree(M, W, dev, stream, flush)
+
+    # ---- serving: Poisson arrivals through the continuous-batching server -------------------
+    serving = None
+    if rank == 0 and args.serving_requests > 0 and args.workload == WORKLOAD:
+        serving = serving_replay(M, W, dev, args.serving_requests, flush)
 
     # ---- end to end through the C ABI with host buffers ---------------------------------
     xh = [torch.from_numpy(a).pin_memory() for a in prob.x]
@@ -386,8 +548,8 @@ def main():
                 a.copy_(b, non_blocking=True)
             for a, b in zip(mud, muh):
                 a.copy_(b, non_blocking=True)
-            o4 = M.mot_solve(xd, mud, prob.eta, M.MOT_TREE, edges=prob.edges, opt=opt, workspace=ws, stream=stream,
-                             u_out=u)
+            o4 = M.mot_solve(xd, mud, prob.eta, M.MOT_TREE, edges=prob.edges, root=prob.root, opt=opt, workspace=ws,
+                             stream=stream, u_out=u)
             for a, b in zip(uh, u):
                 a.copy_(b, non_blocking=True)
             e1.record(stream)
@@ -413,10 +575,12 @@ def main():
         "config": {"workload": WORKLOAD, "topology": "path", "K": prob.K, "d": prob.d, "N": prob.n[0],
                    "eta": prob.eta, "tol_viol": TOL, "n_grid": last.n_grid, "M": last.M,
                    "iters_per_solve": last.iters, "parallelism": f"replicas{world}",
+                   "root": "centre of the path (library choice, MOT_ROOT_CENTRE)",
                    "l2": "flushed between steps (256 MB write)"},
         "latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "dense": dense,
         "other_workloads": others,
+        "serving": serving,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -47,6 +47,8 @@ extern "C" {
 #define MOT_TREE   0        /* Section 4.1: cost decouples along the edges of a tree           */
 #define MOT_CIRCLE 1        /* Section 4.2: edges {k, k+1 mod K}                               */
 
+#define MOT_ROOT_CENTRE      (-1)  /* mot_problem.root: choose a centre of the tree               */
+
 #define MOT_PATH_NFFT         0  /* fast summation, Algorithm 4 (window spread, FFT, D, iFFT, gather), FP32 */
 #define MOT_PATH_DENSE        1  /* direct summation, Eq. (fastsum-sum), FP32 SIMT                          */
 #define MOT_PATH_DENSE_BF16X3 2  /* direct summation on tensor cores, split hi+lo BF16, FP32 accumulate     */
@@ -78,9 +80,14 @@ typedef struct {
                                        (Section 6.2): [K-1] in edge order (tree) or [K] for
                                        edges {k, k+1 mod K} (circle); NULL = all 1            */
     const unsigned char* free_nodes;/* host [K] or NULL: 1 = node without marginal constraint,
-                                       its scaling is held at 1 (Section 6.2, tree only)      */
+                                       its scaling is held at 1 (Section 6.2, tree only).
+                                       The root must be constrained (MOT_EUNSUPPORTED
+                                       otherwise); MOT_ROOT_CENTRE picks a constrained node */
     double eta;                     /* entropic regularisation eta > 0 (Eq. MOTe)             */
-    int root;                       /* tree root label (the paper's node 1)                   */
+    int root;                       /* tree root label (the paper's node 1), or
+                                       MOT_ROOT_CENTRE: a centre of the tree (least
+                                       eccentricity, smallest label on ties), which gives
+                                       the backward pass the fewest sequential levels         */
 } mot_problem;
 
 /* ---- options (zero-initialised fields take the defaults in brackets) ------------- */

@@ -258,6 +258,7 @@ struct TreePlan {
     int K = 0, d = 0, path = MOT_PATH_NFFT;
     double eta = 0.0;
     std::vector<int> order, new_of, parent, depth;
+    int root_label = 0;
     std::vector<std::vector<int>> children;
     std::vector<int> n;            // BFS labels
     std::vector<double> w;         // weight of edge {p(k), k}
@@ -317,7 +318,7 @@ int validate_problem(const mot_problem* P) {
     if (P->topology != MOT_TREE && P->topology != MOT_CIRCLE) return MOT_EINVAL;
     if (P->topology == MOT_TREE) {
         if (!P->edges) return MOT_EINVAL;
-        if (P->root < 0 || P->root >= P->K) return MOT_EINVAL;
+        if (P->root < MOT_ROOT_CENTRE || P->root >= P->K) return MOT_EINVAL;
     }
     int ne = P->topology == MOT_TREE ? P->K - 1 : P->K;
     if (P->edge_w)
@@ -325,6 +326,9 @@ int validate_problem(const mot_problem* P) {
             if (!(P->edge_w[e] > 0.0) || !std::isfinite(P->edge_w[e])) return MOT_EINVAL;
     return MOT_OK;
 }
+
+// Largest point set for which a tree uses the fused 2-D cluster kernel.
+constexpr int kFusedMaxPoints = 32768;
 
 // BFS relabelling so that p(k) < k (Section 4.1).
 int tree_structure(const mot_problem* P, TreePlan& T) {
@@ -338,14 +342,44 @@ int tree_structure(const mot_problem* P, TreePlan& T) {
         adj[b].push_back({a, w});
     }
     for (auto& v : adj) std::sort(v.begin(), v.end());
+    int root = P->root;
+    if (root == MOT_ROOT_CENTRE) {
+        // a centre: the node of least eccentricity (smallest label on ties), so that the
+        // backward pass of Algorithm 2 has the fewest sequential depth levels
+        int best = K + 1;
+        for (int r = 0; r < K; ++r) {
+            std::vector<int> dist(K, -1);
+            std::deque<int> bq{r};
+            dist[r] = 0;
+            int ecc = 0, seen = 1;
+            while (!bq.empty()) {
+                int u = bq.front();
+                bq.pop_front();
+                for (auto& vw : adj[u])
+                    if (dist[vw.first] < 0) {
+                        dist[vw.first] = dist[u] + 1;
+                        ecc = std::max(ecc, dist[vw.first]);
+                        ++seen;
+                        bq.push_back(vw.first);
+                    }
+            }
+            if (seen != K) return MOT_ENOTTREE;
+            if (P->free_nodes && P->free_nodes[r]) continue;   // the root must be constrained
+            if (ecc < best) {
+                best = ecc;
+                root = r;
+            }
+        }
+    }
     T.K = K;
-    T.order.assign(1, P->root);
+    T.root_label = root;
+    T.order.assign(1, root);
     T.new_of.assign(K, -1);
-    T.new_of[P->root] = 0;
+    T.new_of[root] = 0;
     T.parent.assign(1, -1);
     T.depth.assign(1, 0);
     T.w.assign(1, 1.0);
-    std::deque<int> q{P->root};
+    std::deque<int> q{root};
     while (!q.empty()) {
         int u = q.front();
         q.pop_front();
@@ -361,6 +395,9 @@ int tree_structure(const mot_problem* P, TreePlan& T) {
         }
     }
     if ((int)T.order.size() != K) return MOT_ENOTTREE;
+    // With a free root the sibling updates of Algorithm 2 act as a Jacobi step on the scaling
+    // gauge (period-2 oscillation for two children, divergence for more): not supported.
+    if (P->free_nodes && P->free_nodes[root]) return MOT_EUNSUPPORTED;
     T.children.assign(K, {});
     for (int k = 1; k < K; ++k) T.children[T.parent[k]].push_back(k);
     for (int k = 0; k < K; ++k)
@@ -875,7 +912,11 @@ int tree_plan_setup(const mot_problem* P, const mot_options& o, TreePlan& T, voi
         CK(prepare_window());
         CK(prepare_fftconv(T.d, g.n));
         CK(prepare_fused2d());
-        T.fused = fused2d_supported(T.d, g.n);
+        // one 16-CTA cluster per product: worth it while a product is small enough that the
+        // kernel's fixed phases dominate; larger sets use the whole GPU through the 3-kernel path
+        int nmax = 0;
+        for (int k = 0; k < T.K; ++k) nmax = std::max(nmax, T.n[k]);
+        T.fused = fused2d_supported(T.d, g.n) && nmax <= kFusedMaxPoints;
         size_t gsz = 1;
         for (int t = 0; t < T.d; ++t) gsz *= g.n;
         for (int k = 1; k < T.K; ++k) {

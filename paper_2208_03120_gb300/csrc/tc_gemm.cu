@@ -309,19 +309,43 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 // A[c][j] = (phi_j / max phi) (X[c][j] / max X), split into BF16 hi / lo; row stride ld.
+// Four consecutive j per thread: one 8-byte store each for hi and lo (ld is a multiple of 8).
+__device__ __forceinline__ void split4(const float (&a)[4], __nv_bfloat16* hi, __nv_bfloat16* lo) {
+    __nv_bfloat162 h01 = __floats2bfloat162_rn(a[0], a[1]), h23 = __floats2bfloat162_rn(a[2], a[3]);
+    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+    __nv_bfloat162 l01 = __floats2bfloat162_rn(a[0] - f01.x, a[1] - f01.y);
+    __nv_bfloat162 l23 = __floats2bfloat162_rn(a[2] - f23.x, a[3] - f23.y);
+    uint2 hv, lv;
+    hv.x = *reinterpret_cast<uint32_t*>(&h01);
+    hv.y = *reinterpret_cast<uint32_t*>(&h23);
+    lv.x = *reinterpret_cast<uint32_t*>(&l01);
+    lv.y = *reinterpret_cast<uint32_t*>(&l23);
+    *reinterpret_cast<uint2*>(hi) = hv;
+    *reinterpret_cast<uint2*>(lo) = lv;
+}
+
 __global__ void __launch_bounds__(256) k_split_src(const float* __restrict__ X, const VecScale* sX,
                                                    const float* __restrict__ phi, const VecScale* sP, int ns, int nrow,
                                                    int ld, __nv_bfloat16* __restrict__ hi,
                                                    __nv_bfloat16* __restrict__ lo) {
     const float sx = 1.f / mx_of(sX, 0), sp = phi ? 1.f / mx_of(sP, 0) : 1.f;
+    const int nq = (ns + 3) >> 2;
     for (int c = blockIdx.y; c < nrow; c += gridDim.y) {
         const float* x = X + (size_t)c * ns;
-        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ns; j += gridDim.x * blockDim.x) {
-            float a = x[j] * sx;
-            if (phi) a *= __ldg(phi + j) * sp;
-            const __nv_bfloat16 h = __float2bfloat16_rn(a);
-            hi[(size_t)c * ld + j] = h;
-            lo[(size_t)c * ld + j] = __float2bfloat16_rn(a - __bfloat162float(h));
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+            const int j0 = q << 2;
+            float a[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int j = j0 + t;
+                a[t] = 0.f;
+                if (j < ns) {
+                    a[t] = x[j] * sx;
+                    if (phi) a[t] *= __ldg(phi + j) * sp;
+                }
+            }
+            // the padding columns [ns, ld) receive zeros (never read: the tensor map stops at ns)
+            split4(a, hi + (size_t)c * ld + j0, lo + (size_t)c * ld + j0);
         }
     }
 }
@@ -436,7 +460,7 @@ cudaError_t launch_tc_gemm(const TcGemm& g, TcEpi e, cudaStream_t st) {
 cudaError_t launch_split_src(const float* X, const VecScale* sX, const float* phi, const VecScale* sP, int ns,
                              int nrow, int ld, void* hi, void* lo, cudaStream_t st) {
     if (nrow <= 0 || ns <= 0) return cudaSuccess;
-    const int bx = std::min((ns + 255) / 256, 8);
+    const int bx = std::min((ns + 1023) / 1024, 8);
     k_split_src<<<dim3(bx, std::min(nrow, 65535)), 256, 0, st>>>(X, sX, phi, sP, ns, nrow, ld, static_cast<__nv_bfloat16*>(hi),
                                                 static_cast<__nv_bfloat16*>(lo));
     return cudaGetLastError();

@@ -143,3 +143,19 @@ def test_server_argument_validation(M):
     assert lib.mot_server_create(C.c_void_p(0x1000), 1 << 20, 0, C.byref(h)) == M.MOT_EINVAL
     assert lib.mot_server_progress(None, None, None) == M.MOT_EINVAL
     assert lib.mot_server_destroy(None) == M.MOT_EINVAL
+
+
+def test_root_validation(M):
+    """root = -1 (MOT_ROOT_CENTRE) is accepted; other negative labels are not; a free root is
+    unsupported (its sibling updates do not converge)."""
+    p, keep = _fake_problem(M, 4, 2, [100, 200, 300, 150], [(0, 1), (1, 2), (1, 3)])
+    p.root = -1
+    assert _ws(M, p)[0] == M.MOT_OK
+    p.root = -2
+    assert _ws(M, p)[0] == M.MOT_EINVAL
+    p.root = 0
+    f = (C.c_ubyte * 4)(1, 0, 0, 0)
+    p.free_nodes = f
+    assert _ws(M, p)[0] == M.MOT_EUNSUPPORTED
+    p.root = -1                     # the centre among constrained nodes: node 1
+    assert _ws(M, p)[0] == M.MOT_OK

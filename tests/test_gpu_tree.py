@@ -109,12 +109,16 @@ def test_star_workload_reduced(M):
     assert_parity(prob, u, u_or, rep_g, rep_o, out)
 
 
-def test_path10_workload_full_size(M):
+@pytest.mark.parametrize("root", [0, -1])
+def test_path10_workload_full_size(M, root):
     """The 10-node d=2 path workload at full size (N = 10^4, eta = 0.01), solved to the
-    1e-6 violation of the metric in the launch configuration of the bench; the oracle
-    evaluates the returned scalings with exact kernels (18 dense products of 10^4 x 10^4)."""
+    1e-6 violation of the metric in the launch configuration of the bench (root at an end,
+    and at the centre chosen by the library); the oracle evaluates the returned scalings
+    with exact kernels (18 dense products of 10^4 x 10^4)."""
     prob = W.path10_d2()
+    prob.root = root
     out, u = gpu_solve(M, prob, tol_viol=1e-6, max_iter=5000)
+    prob.root = 0                    # the exact marginals do not depend on the root
     assert out.status == 0 and out.violation <= 1e-6
     rep = exact_report(prob, u)
     assert rep["viol"] <= REL
@@ -153,3 +157,78 @@ def test_warm_start_resumes(M):
     a, b = OS.gauge_fix(u, prob.mu), OS.gauge_fix(u2, prob.mu)
     for va, vb in zip(a, b):
         assert np.max(np.abs(va - vb)) <= 1e-4 * prob.eta * 100
+
+
+def _centre(K, edges):
+    """Least-eccentricity node, smallest label on ties (brute force over BFS distances)."""
+    adj = {k: [] for k in range(K)}
+    for a, b in edges:
+        adj[int(a)].append(int(b))
+        adj[int(b)].append(int(a))
+    best, arg = None, None
+    for r in range(K):
+        dist, frontier = {r: 0}, [r]
+        while frontier:
+            nxt = []
+            for u in frontier:
+                for v in adj[u]:
+                    if v not in dist:
+                        dist[v] = dist[u] + 1
+                        nxt.append(v)
+            frontier = nxt
+        ecc = max(dist.values())
+        if best is None or ecc < best:
+            best, arg = ecc, r
+    return arg
+
+
+@pytest.mark.parametrize("path", [0, 1])
+def test_centre_root_fixed_sweeps(M, path):
+    """MOT_ROOT_CENTRE: 40 sweeps of Algorithm 2 rooted at the tree's centre equal the
+    oracle's 40 sweeps with that root passed explicitly."""
+    rng = np.random.default_rng(4242)
+    prob = W.random_problem(rng, W.TREE, 9, 2, 500, 0.05, shape="tree-random")
+    centre = _centre(9, prob.edges)
+    prob.root = -1
+    out, u = gpu_solve(M, prob, path=path, max_iter=40, tol_viol=-1.0, check_every=10)
+    assert out.iters == 40
+    prob.root = centre
+    u_or, res = oracle_solve(prob, 40)
+    rep_g, rep_o = exact_report(prob, u), exact_report(prob, u_or)
+    assert_parity(prob, u, u_or, rep_g, rep_o)
+    assert abs(out.S_last - res.S[-1]) <= REL * abs(res.S[-1])
+
+
+@pytest.mark.parametrize("path", [0, 1])
+def test_barycenter_free_centre(M, path):
+    """Fixed-support barycenter (Section 6.2): star with a free centre (phi = 1) and four
+    constrained leaves, leaf-edge weights w_k summing to 1, rooted at a leaf.  At tolerance
+    the leaves' violation, the dual value and the barycenter (the centre's marginal) equal
+    the oracle's."""
+    import torch
+    rng = np.random.default_rng(99)
+    prob = W.random_problem(rng, W.TREE, 5, 2, [700, 500, 600, 550, 650], 0.03, shape="star")
+    w = np.array([0.1, 0.2, 0.3, 0.4])
+    free = [1, 0, 0, 0, 0]
+    x, mu = problem_tensors(prob)
+    out = M.mot_solve(x, mu, prob.eta, M.MOT_TREE, edges=prob.edges, edge_w=w, free_nodes=free, root=1,
+                      opt=M.options(path=path, tol_viol=1e-6, max_iter=4000))
+    torch.cuda.synchronize()
+    assert out.status == 0, (out.iters, out.violation)
+    u = [t.cpu().numpy() for t in out.u]
+    assert np.allclose(u[0], 0.0)
+    ts = OS.TreeSinkhorn(prob.x64(), prob.mu, prob.edges, prob.eta, root=1, edge_w=w)
+    res = ts.run(4000, free_nodes=[0])
+
+    def report(phi):
+        P = OS.tree_marginals(prob.x64(), phi, prob.edges, prob.eta, root=1, edge_w=w)
+        mass = OS.total_mass(P)
+        viol = max(np.sum(np.abs(P[k] - prob.mu[k])) for k in range(1, 5))
+        return P, viol, OS.dual_value(prob.mu, phi, mass, prob.eta)
+
+    Pg, vg, dg = report([np.exp(a / prob.eta) for a in u])
+    Po, vo, do = report(res.phi)
+    assert abs(vg - vo) <= REL
+    assert abs(dg - do) <= REL * abs(do)
+    assert abs(out.cost_dual - do) <= REL * abs(do)
+    assert np.sum(np.abs(Pg[0] - Po[0])) <= REL

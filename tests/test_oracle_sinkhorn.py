@@ -228,3 +228,59 @@ def test_path3_workload_against_bruteforce():
                 np.testing.assert_allclose(a, b, rtol=1e-9)
     P = OS.tensor_marginals(OS.plan_tensor(Kt, phi))
     assert OS.violation(P, prob.mu) < 1e-6
+
+
+@pytest.mark.parametrize("root", [1, 2])
+def test_free_centre_star_is_two_marginal_sinkhorn_on_composite_kernel(root):
+    """Barycenter modification (Section 6.2): a star whose centre carries no marginal
+    constraint (phi = 1) couples its two leaves through the composite kernel
+    G = K^{(a,c)} K^{(c,b)}, so at convergence the leaves' coupling diag(phi_a) G diag(phi_b)
+    equals the one of a textbook two-marginal Sinkhorn on G (written out here), with edge
+    weights w_e on the squared distances."""
+    rng = np.random.default_rng(2024)
+    n = [30, 25, 35]                      # centre 0, leaves 1 and 2
+    x = [rng.uniform(-0.3, 0.3, size=(m, 1)) for m in n]
+    mu = [np.full(n[0], 1.0 / n[0])] + [rng.uniform(0.2, 1.0, m) for m in n[1:]]
+    mu = [m / m.sum() for m in mu]
+    eta, w = 0.05, [0.7, 1.6]
+    edges = np.array([[0, 1], [0, 2]])
+    ts = OS.TreeSinkhorn(x, mu, edges, eta, root=root, edge_w=w)
+    res = ts.run(3000, free_nodes=[0])
+    assert np.allclose(res.phi[0], 1.0)
+
+    def kern(a, b, we):
+        return np.exp(-we * (a[:, 0][:, None] - b[:, 0][None, :]) ** 2 / eta)
+
+    G = kern(x[1], x[0], w[0]) @ kern(x[0], x[2], w[1])
+    pa, pb = np.ones(n[1]), np.ones(n[2])
+    for _ in range(3000):
+        pa = mu[1] / (G @ pb)
+        pb = mu[2] / (G.T @ pa)
+    P_ref = pa[:, None] * G * pb[None, :]
+    P_tree = res.phi[1][:, None] * G * res.phi[2][None, :]
+    assert np.max(np.abs(P_tree - P_ref)) <= 1e-10 * np.max(P_ref)
+    # the free centre's marginal is the pushforward of that coupling through the kernels
+    P = OS.tree_marginals(x, res.phi, edges, eta, root=root, edge_w=w)
+    Kac, Kcb = kern(x[1], x[0], w[0]), kern(x[0], x[2], w[1])
+    centre = np.einsum("a,ac,cb,b->c", pa, Kac, Kcb, pb)
+    assert np.allclose(P[0], centre, rtol=1e-8, atol=1e-14)
+
+
+def test_free_root_sibling_updates_do_not_converge():
+    """With a free root (phi = 1 at the root, Section 6.2 modification) the leaves of a star
+    are updated from each other's previous messages (Algorithm 2's sibling order), a Jacobi
+    step in the scaling gauge: scaling every leaf by c maps to c^{-(L-1)}.  For two leaves the
+    total mass alternates between two values instead of converging; this is why the CUDA path
+    requires a constrained root whenever free nodes are present."""
+    rng = np.random.default_rng(5)
+    n = [20, 15, 18]
+    x = [rng.uniform(-0.3, 0.3, size=(m, 1)) for m in n]
+    mu = [np.full(m, 1.0 / m) for m in n]
+    ts = OS.TreeSinkhorn(x, mu, np.array([[0, 1], [0, 2]]), 0.05, root=0)
+    masses = []
+    ts.run(400, free_nodes=[0], callback=lambda r, phi: masses.append(
+        float(OS.total_mass(OS.tree_marginals(x, phi, np.array([[0, 1], [0, 2]]), 0.05)))))
+    tail = np.array(masses[-6:])
+    assert np.max(np.abs(np.log(tail))) > 1e-3          # mass stays away from 1
+    assert np.allclose(tail[::2], tail[0], rtol=1e-9) and np.allclose(tail[1::2], tail[1], rtol=1e-9)
+    assert abs(np.log(tail[0]) + np.log(tail[1])) < 1e-6  # period 2: c and 1/c
