@@ -112,6 +112,110 @@ struct RunSpread {
     }
 };
 
+// ------------------------------------------------------------------------------------------
+// 2-D spread, batched: a warp takes SP2_B cell-sorted points at a time.  Lane (p, t) =
+// (lane & 15, lane >> 4) evaluates the 10 window taps of point p along dimension t (Horner
+// with the coefficients in constant memory) and stages them in shared memory, the x taps
+// scaled by the point's value v_p.  Lanes (a, blk) = (lane % 10, lane / 10) then form the
+// grid contributions g[a][4 blk + i] = sum_p (v wx)_p[a] wy_p[4 blk + i] of consecutive points
+// of one cell in registers and add them to the shared grid only when the cell changes.
+// ------------------------------------------------------------------------------------------
+constexpr int SP2_B = 16;         // points per warp batch
+constexpr int SP2_ROW = 24;       // staged floats per point: v wx [0,10), wy [12,22), cell key [23]
+constexpr int SP2_WARP = SP2_B * SP2_ROW;
+
+struct Spread2Acc {
+    float acc[4];
+    int a, b0, nb;
+    bool on;
+    __device__ __forceinline__ void init(int lane) {
+        on = lane < 30;
+        a = on ? lane % MOT_W : 0;
+        b0 = on ? 4 * (lane / MOT_W) : 8;         // lanes 30, 31 read a valid slot and never add
+        nb = lane < 20 ? 4 : 2;
+        zero();
+    }
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] = 0.f;
+    }
+    __device__ __forceinline__ void step(const float* row) {
+        const float xa = row[a];
+        const float4 y = *reinterpret_cast<const float4*>(row + 12 + b0);
+        acc[0] = fmaf(xa, y.x, acc[0]);
+        acc[1] = fmaf(xa, y.y, acc[1]);
+        acc[2] = fmaf(xa, y.z, acc[2]);
+        acc[3] = fmaf(xa, y.w, acc[3]);
+    }
+};
+
+// Stage one batch: lane (p, t) handles point jb + p along dimension t.  `value(j)` gives v_j,
+// `cell(lx, ly)` the key of the cell whose window starts at (lx, ly) (= floor(u) - MOT_WHALF).
+// Returns the cell key of point `lane` on lanes < cnt.
+template <class Value, class Cell>
+__device__ __forceinline__ int spread2_stage(float* stg, int lane, int jb, int cnt, const float* __restrict__ ux,
+                                             const float* __restrict__ uy, Value value, Cell cell) {
+    const int p = lane & 15, t = lane >> 4;
+    const bool ok = p < cnt;
+    const int j = jb + p;
+    int l = 0;
+    float w[MOT_W];
+    if (ok) {
+        const float u = t == 0 ? ux[j] : uy[j];
+        const float fl = floorf(u);
+        window_taps(u - fl, w);
+        l = (int)fl - MOT_WHALF;
+    }
+    const int lx = __shfl_sync(0xffffffffu, l, p), ly = __shfl_sync(0xffffffffu, l, p + 16);
+    const int key = cell(lx, ly);
+    if (ok) {
+        float* row = stg + p * SP2_ROW;
+        if (t == 0) {
+            const float v = value(j);
+#pragma unroll
+            for (int q = 0; q < MOT_W; ++q) w[q] *= v;
+            *reinterpret_cast<float4*>(row) = make_float4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<float4*>(row + 4) = make_float4(w[4], w[5], w[6], w[7]);
+            *reinterpret_cast<float2*>(row + 8) = make_float2(w[8], w[9]);
+        } else {
+            *reinterpret_cast<float4*>(row + 12) = make_float4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<float4*>(row + 16) = make_float4(w[4], w[5], w[6], w[7]);
+            *reinterpret_cast<float2*>(row + 20) = make_float2(w[8], w[9]);
+        }
+    }
+    __syncwarp();
+    return key;
+}
+
+// Accumulate a staged batch; `flush(key, acc)` adds a finished cell to the shared grid.  The
+// starts of new cells are found up front (one ballot over the keys held by lanes < cnt), so
+// the loop over the batch is unrolled and its shared-memory reads are issued back to back.
+template <class Flush>
+__device__ __forceinline__ void spread2_accumulate(const float* stg, int cnt, int key, int lane, Spread2Acc& A,
+                                                   int& cur, Flush flush) {
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const unsigned starts = __ballot_sync(0xffffffffu, lane < cnt && key != (lane == 0 ? cur : prev));
+    if (starts == 0u) {
+        if (cnt == SP2_B) {
+#pragma unroll
+            for (int q = 0; q < SP2_B; ++q) A.step(stg + q * SP2_ROW);
+        } else {
+            for (int q = 0; q < cnt; ++q) A.step(stg + q * SP2_ROW);
+        }
+    } else {
+#pragma unroll 4
+        for (int q = 0; q < cnt; ++q) {
+            if ((starts >> q) & 1u) {
+                if (cur >= 0) flush(cur, A);
+                A.zero();
+                cur = __shfl_sync(0xffffffffu, key, q);
+            }
+            A.step(stg + q * SP2_ROW);
+        }
+    }
+    __syncwarp();
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, Globals G) {
     __shared__ Task T;
@@ -132,15 +236,53 @@ __global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, 
     const int N = T.src.n;
     const int nsub = *T.src.nsub;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    float* stg = tile + ((npad + 3) & ~3) + warp * SP2_WARP;     // 2-D staging (per warp)
 
-    for (int s = blockIdx.x; s < nsub; s += gridDim.x) {
-        const Sub sb = T.src.subs[s];
-        int o[3];
-        tile_origin<D>(sb.tile, ntd, TS, o);
-        for (int i = threadIdx.x; i < npad; i += blockDim.x) tile[i] = 0.f;
+    // A contiguous range of subproblems per CTA: consecutive subproblems mostly share a tile,
+    // which then stays in shared memory and is added to the grid once.
+    const int per = (nsub + gridDim.x - 1) / gridDim.x;
+    const int sbeg = min(nsub, (int)blockIdx.x * per), send = min(nsub, sbeg + per);
+    int cur_tile = -1;
+    int o[3] = {0, 0, 0};
+    auto flush_tile = [&]() {
         __syncthreads();
+        for (int i = threadIdx.x; i < npad; i += blockDim.x) {
+            const float val = tile[i];
+            if (val != 0.f) atomicAdd(&T.grid[tile_to_global<D>(i, P, o, n)], val);
+        }
+    };
+    for (int s = sbeg; s < send; ++s) {
+        const Sub sb = T.src.subs[s];
+        if (sb.tile != cur_tile) {
+            if (cur_tile >= 0) flush_tile();
+            __syncthreads();
+            for (int i = threadIdx.x; i < npad; i += blockDim.x) tile[i] = 0.f;
+            tile_origin<D>(sb.tile, ntd, TS, o);
+            cur_tile = sb.tile;
+            __syncthreads();
+        }
         const int chunk = (sb.len + nwarps - 1) / nwarps;
         const int j0 = sb.start + min(sb.len, warp * chunk), j1 = sb.start + min(sb.len, (warp + 1) * chunk);
+        if (D == 2) {
+            Spread2Acc A;
+            A.init(lane);
+            int cur = -1;
+            auto value = [&](int j) { return T.alpha ? T.alpha[j] : eval_prod(fc, j); };
+            auto cell = [&](int lx, int ly) { return (ly - o[1]) * P + (lx - o[0]); };
+            auto flush = [&](int key, const Spread2Acc& S) {
+                if (S.on)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (i < S.nb) atomicAdd(&tile[key + (S.b0 + i) * P + S.a], S.acc[i]);
+            };
+            for (int jb = j0; jb < j1; jb += SP2_B) {
+                const int cnt = min(SP2_B, j1 - jb);
+                const int key = spread2_stage(stg, lane, jb, cnt, T.src.u, T.src.u + N, value, cell);
+                spread2_accumulate(stg, cnt, key, lane, A, cur, flush);
+            }
+            if (cur >= 0) flush(cur, A);
+            continue;
+        }
         RunSpread<D> rs;
         rs.init(lane);
         int cur = -1;
@@ -189,13 +331,8 @@ __global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, 
                 for (int c = 0; c < RunSpread<D>::NC; ++c)
                     if (rs.ok[i]) atomicAdd(&tile[cur + (c * P + rs.b[i]) * (D >= 2 ? P : 0) + rs.a[i]], rs.acc[i][c]);
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < npad; i += blockDim.x) {
-            const float val = tile[i];
-            if (val != 0.f) atomicAdd(&T.grid[tile_to_global<D>(i, P, o, n)], val);
-        }
-        __syncthreads();
     }
+    if (cur_tile >= 0) flush_tile();
 }
 
 // ------------------------------------------------------------------------------------------
@@ -236,12 +373,19 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
         if (D >= 3) npad *= P;
         const int N = T.tgt.n;
         const int nsub = *T.tgt.nsub;
-        for (int s = blockIdx.x; s < nsub; s += gridDim.x) {
+        const int per = (nsub + gridDim.x - 1) / gridDim.x;
+        const int sbeg = min(nsub, (int)blockIdx.x * per), send = min(nsub, sbeg + per);
+        int cur_tile = -1;
+        int o[3] = {0, 0, 0};
+        for (int s = sbeg; s < send; ++s) {
             const Sub sb = T.tgt.subs[s];
-            int o[3];
-            tile_origin<D>(sb.tile, ntd, TS, o);
-            for (int i = threadIdx.x; i < npad; i += blockDim.x) tile[i] = __ldg(&T.hgrid[tile_to_global<D>(i, P, o, n)]);
-            __syncthreads();
+            if (sb.tile != cur_tile) {      // consecutive subproblems mostly share the tile
+                __syncthreads();
+                tile_origin<D>(sb.tile, ntd, TS, o);
+                for (int i = threadIdx.x; i < npad; i += blockDim.x) tile[i] = __ldg(&T.hgrid[tile_to_global<D>(i, P, o, n)]);
+                cur_tile = sb.tile;
+                __syncthreads();
+            }
             const int j1 = sb.start + sb.len;
             for (int j = sb.start + threadIdx.x; j < j1; j += blockDim.x) {
                 float w[D][MOT_W];
@@ -285,7 +429,6 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
                 }
                 epilogue_point(T, tf, C, G.floor_, j, acc, ep);
             }
-            __syncthreads();
         }
     }
     epi_block_finish(T, G, tf, Lsrc, ep);
@@ -310,6 +453,7 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
 #define F2_MAXR 8          // rows per CTA (n / CS) for CS >= 8
 #define F2_MAXC 3          // columns per CTA (ceil((M+1) / CS)) for CS >= 8
 #define F2_THREADS 512
+#define F2_DYN_SMEM (F2_THREADS / 32 * SP2_WARP * 4)   // spread staging
 
 // Sum of `v` over groups of G consecutive lanes (G a power of two <= 32).
 template <int G>
@@ -335,11 +479,11 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
     __shared__ float2 Arow[F2_MAXR * (F2_M + 1)];
     __shared__ float Hrow[F2_MAXR * F2_N];
     __shared__ float2 tw[F2_N];
-    __shared__ float cw[MOT_W][MOT_WDEG + 1];     // window coefficients (per-lane rows)
+    extern __shared__ float4 f2_dyn[];             // spread staging, SP2_WARP floats per warp
+    float* f2_stage = reinterpret_cast<float*>(f2_dyn);
 
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
-    for (int i = tid; i < MOT_W * (MOT_WDEG + 1); i += nt) (&cw[0][0])[i] = (&c_win[0][0])[i];
     const int CS = (int)cluster.num_blocks();
     const int r = (int)cluster.block_rank();
     load_task(T, tasks + blockIdx.y);
@@ -372,44 +516,25 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
         {
             const int chunk = (j1 - j0 + nwarps - 1) / nwarps;
             const int w0 = j0 + min(j1 - j0, warp * chunk), w1 = j0 + min(j1 - j0, (warp + 1) * chunk);
-            RunSpread<2> rs;
-            rs.init(lane);
-            int cur = -1, clx = 0, cly = 0;
-            for (int jb = w0; jb < w1; jb += 32) {
-              const int jl = jb + lane;
-              float pv = 0.f, px = 0.f, py = 0.f;
-              if (jl < w1) {
-                  pv = T.alpha ? T.alpha[jl] : eval_prod(fc, jl);
-                  px = T.src.u[jl];
-                  py = T.src.u[Ns + jl];
-              }
-              const int cnt = min(32, w1 - jb);
-              for (int k = 0; k < cnt; ++k) {
-                const float v = __shfl_sync(0xffffffffu, pv, k);
-                const float ux = __shfl_sync(0xffffffffu, px, k), uy = __shfl_sync(0xffffffffu, py, k);
-                const float fx = floorf(ux), fy = floorf(uy);
-                const int lx = (int)fx - MOT_WHALF, ly = (int)fy - MOT_WHALF;
-                const int key = ((ly & mask) << 8) | (lx & mask);
-                if (key != cur) {
-                    if (cur >= 0) {
+            float* stg = f2_stage + warp * SP2_WARP;
+            Spread2Acc A;
+            A.init(lane);
+            int cur = -1;
+            auto value = [&](int j) { return T.alpha ? T.alpha[j] : eval_prod(fc, j); };
+            auto cell = [&](int lx, int ly) { return ((ly & mask) << 8) | (lx & mask); };
+            auto flush = [&](int key, const Spread2Acc& S) {
+                const int clx = key & 255, cly = key >> 8;
+                if (S.on)
 #pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            if (rs.ok[i]) atomicAdd(&Gs[((cly + rs.b[i]) & mask) * n + ((clx + rs.a[i]) & mask)], rs.acc[i][0]);
-                        rs.zero();
-                    }
-                    cur = key;
-                    clx = lx;
-                    cly = ly;
-                }
-                const float f[2] = {ux - fx, uy - fy};
-                rs.add(v, rs.lane_weight(cw, f));
-              }
+                    for (int i = 0; i < 4; ++i)
+                        if (i < S.nb) atomicAdd(&Gs[((cly + S.b0 + i) & mask) * n + ((clx + S.a) & mask)], S.acc[i]);
+            };
+            for (int jb = w0; jb < w1; jb += SP2_B) {
+                const int cnt = min(SP2_B, w1 - jb);
+                const int key = spread2_stage(stg, lane, jb, cnt, T.src.u, T.src.u + Ns, value, cell);
+                spread2_accumulate(stg, cnt, key, lane, A, cur, flush);
             }
-            if (cur >= 0) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (rs.ok[i]) atomicAdd(&Gs[((cly + rs.b[i]) & mask) * n + ((clx + rs.a[i]) & mask)], rs.acc[i][0]);
-            }
+            if (cur >= 0) flush(cur, A);
         }
         cluster.sync();
         // ---- 2. reduce owned rows, DFT along x (4 lanes per output) ---------------------
@@ -812,11 +937,17 @@ int ilog2(int n) {
 
 }  // namespace
 
-int spread_smem_bytes(int d, int n) {
+int gather_smem_bytes(int d, int n) {
     int TS = mot_tile_size(d, n), P = TS + MOT_W - 1;
     int np = P;
     for (int i = 1; i < d; ++i) np *= P;
     return np * (int)sizeof(float);
+}
+
+// padded tile, plus the per-warp staging of the batched 2-D spread (8 warps)
+int spread_smem_bytes(int d, int n) {
+    const int tile = ((gather_smem_bytes(d, n) / 4 + 3) & ~3) * 4;
+    return tile + (d == 2 ? 8 * SP2_WARP * (int)sizeof(float) : 0);
 }
 
 cudaError_t launch_spread(int d, const Task* tasks, int ntask, int grid_x, const Globals& G, cudaStream_t st) {
@@ -834,7 +965,7 @@ cudaError_t launch_spread(int d, const Task* tasks, int ntask, int grid_x, const
 cudaError_t launch_gather(int d, const Task* tasks, int ntask, int grid_x, const Globals& G, cudaStream_t st) {
     if (ntask <= 0) return cudaSuccess;
     dim3 grid(grid_x, ntask);
-    int sm = spread_smem_bytes(d, G.n_grid);
+    int sm = gather_smem_bytes(d, G.n_grid);
     switch (d) {
     case 1: k_gather<1><<<grid, 256, sm, st>>>(tasks, G); break;
     case 2: k_gather<2><<<grid, 256, sm, st>>>(tasks, G); break;
@@ -907,10 +1038,13 @@ cudaError_t prepare_fused2d() {
     if (g_cluster_size != 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_fastsum2d, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) cudaGetLastError();
+    e = cudaFuncSetAttribute(k_fastsum2d, cudaFuncAttributeMaxDynamicSharedMemorySize, F2_DYN_SMEM);
+    if (e != cudaSuccess) return e;
     for (int cs : {16, 8}) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cs, 1, 1);
         cfg.blockDim = dim3(F2_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = F2_DYN_SMEM;
         cudaLaunchAttribute attr;
         attr.id = cudaLaunchAttributeClusterDimension;
         attr.val.clusterDim.x = cs;
@@ -936,7 +1070,7 @@ cudaError_t launch_fused2d(const Task* tasks, int ntask, const Globals& G, cudaS
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, ntask, 1);
     cfg.blockDim = dim3(F2_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = F2_DYN_SMEM;
     cfg.stream = st;
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeClusterDimension;
