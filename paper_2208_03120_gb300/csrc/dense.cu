@@ -89,19 +89,13 @@ __global__ void __launch_bounds__(DENSE_TPB) k_dense(const Task* __restrict__ ta
 // Epilogue over raw sums (dense path) or with raw = 1 (node steps).  Zeroes raw after use.
 __global__ void __launch_bounds__(256) k_epi(const Task* __restrict__ tasks, Globals G) {
     __shared__ Task T;
-    __shared__ FacCache tf;
+    __shared__ FacCache fc, tf;
     __shared__ double sLsrc;
     __shared__ EpiConst sC;
+    __shared__ EpiPre sP;
     load_task(T, tasks + blockIdx.y);
     __syncthreads();
-    load_factors(tf, G.fac, T.tf0, T.tnf);
-    if (threadIdx.x < 32) {
-        const double L = T.alpha == nullptr ? factors_L_warp(G.fac, T.sf0, T.snf) : 0.0;
-        if (threadIdx.x == 0) {
-            sLsrc = L;
-            epi_prepare(T, tf, L, sC);
-        }
-    }
+    load_task_consts(T, G, fc, tf, sP, sC, sLsrc);
     __syncthreads();
     const double Lsrc = sLsrc;
     const EpiConst C = sC;
@@ -115,7 +109,7 @@ __global__ void __launch_bounds__(256) k_epi(const Task* __restrict__ tasks, Glo
         }
         epilogue_point(T, tf, C, G.floor_, i, raw, ep);
     }
-    epi_block_finish(T, G, tf, Lsrc, ep);
+    epi_block_finish(T, G, tf, Lsrc, ep, sP.iter);
 }
 
 }  // namespace

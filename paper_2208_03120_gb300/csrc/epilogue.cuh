@@ -116,8 +116,120 @@ __device__ __forceinline__ void epi_prepare(const Task& T, const FacCache& tf, d
     }
 }
 
-__device__ __forceinline__ void epilogue_point(const Task& T, const FacCache& tf, const EpiConst& C,
-                                               float floor_, int i, float raw, EpiPartial& ep) {
+// One warp fills a factor cache: lanes stride over the factors, reading each factor and its
+// scale record once, and the log-scale is summed over the warp.  No barrier.
+__device__ __forceinline__ void fill_factors_warp(FacCache& fc, const Factor* F, int f0, int nf, int lane) {
+    double L = 0.0;
+    for (int t = lane; t < nf; t += 32) {
+        const Factor f = F[f0 + t];
+        const float mx = mx_of(f.sc, f.use_prev);
+        fc.mant[t] = f.mant;
+        fc.scale[t] = 1.f / mx;
+        fc.inv[t] = f.inv;
+        const double Lt = ls_of(f.sc, f.use_prev) + (double)logf(mx);
+        L += f.inv ? -Lt : Lt;
+    }
+    L = warp_sum_d(L);
+    if (lane == 0) {
+        fc.nf = nf;
+        fc.L = L;
+    }
+}
+
+// Scale-record values of the epilogue that depend on the task alone, and the iteration counter
+// (constant while a sweep's kernels run: the prologue kernel advances it).
+struct EpiPre {
+    double ls_phi_k, Lold;
+    float inv_mx_old;
+    int iter;
+};
+
+// Factor caches and epilogue constants of a task with one barrier: warps 0 / 1 fill the source /
+// target caches, warp 2 reads the scale records; thread 0 then derives the constants, which the
+// other threads may read after the caller's next barrier.  Needs at least 3 warps.
+__device__ __forceinline__ void load_task_consts(const Task& T, const Globals& G, FacCache& fc, FacCache& tf,
+                                                 EpiPre& pre, EpiConst& C, double& sLsrc) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        if (T.alpha == nullptr) {
+            fill_factors_warp(fc, G.fac, T.sf0, T.snf, lane);
+        } else if (lane == 0) {
+            fc.nf = 0;
+            fc.L = 0.0;
+        }
+    } else if (warp == 1) {
+        fill_factors_warp(tf, G.fac, T.tf0, T.tnf, lane);
+    } else if (warp == 2 && lane == 0) {
+        pre.ls_phi_k = ls_of(T.phi_sc, 0);
+        pre.Lold = ls_of(T.phi_sc, 1) + (double)logf(mx_of(T.phi_sc, 1));
+        pre.inv_mx_old = 1.f / mx_of(T.phi_sc, 1);
+        pre.iter = G.iter ? *G.iter : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double Lsrc = T.alpha == nullptr ? fc.L : 0.0;
+        sLsrc = Lsrc;
+        C.lsphi = phi_logscale(T, tf, Lsrc);
+        C.E = 1.0;
+        C.ls_phi_k = 0.0;
+        C.inv_mx_old = 1.f;
+        if (T.mode == EPI_MARG) {
+            C.E = exp(Lsrc + tf.L);
+            C.ls_phi_k = pre.ls_phi_k;
+        } else if (T.mode == EPI_ROOT || T.mode == EPI_CROOT) {
+            C.E = exp(pre.Lold + (T.mode == EPI_ROOT ? tf.L : Lsrc));
+            C.inv_mx_old = pre.inv_mx_old;
+        }
+    }
+}
+
+// Target-side inputs of the epilogue of point i, loaded ahead of the kernel sum so that their
+// latency overlaps it.
+struct EpiIn {
+    float t;      // product of the target-side factors
+    float muf;    // mu_i (FP32)
+    float phi;    // current scaling mantissa
+    double mud;   // mu_i (FP64)
+};
+
+__device__ __forceinline__ EpiIn epi_load(const Task& T, const FacCache& tf, int i) {
+    EpiIn in;
+    in.t = 1.f;
+    in.muf = 0.f;
+    in.phi = 0.f;
+    in.mud = 0.0;
+    switch (T.mode) {
+    case EPI_PHI:
+        in.t = eval_prod(tf, i);
+        in.muf = T.mu_f[i];
+        in.mud = T.mu_d[i];
+        break;
+    case EPI_ROOT:
+        in.t = eval_prod(tf, i);
+        in.phi = T.phi[i];
+        if (!T.free_node) {
+            in.muf = T.mu_f[i];
+            in.mud = T.mu_d[i];
+        }
+        break;
+    case EPI_CROOT:
+        in.phi = T.phi[i];
+        in.muf = T.mu_f[i];
+        in.mud = T.mu_d[i];
+        break;
+    case EPI_MARG:
+        in.t = eval_prod(tf, i);                 // phi^k and the children's messages
+        in.phi = T.phi[i];
+        if (T.mu_d) in.mud = T.mu_d[i];
+        break;
+    default:
+        break;
+    }
+    return in;
+}
+
+__device__ __forceinline__ void epilogue_point_in(const Task& T, const EpiConst& C, float floor_, int i, float raw,
+                                                  const EpiIn& in, EpiPartial& ep) {
     switch (T.mode) {
     case EPI_RAW:
         T.out[i] = raw;
@@ -133,12 +245,10 @@ __device__ __forceinline__ void epilogue_point(const Task& T, const FacCache& tf
         float g = raw;
         if (!(g >= floor_)) { g = floor_; ep.clamps++; }
         if (T.out) T.out[i] = g;
-        const float t = eval_prod(tf, i);
-        const float ph = T.mu_f[i] / (g * t);
+        const float ph = in.muf / (g * in.t);
         T.phi[i] = ph;
         ep.mx_phi = fmaxf(ep.mx_phi, ph);
-        const double m = T.mu_d[i];
-        if (m > 0.0) ep.logphi += m * ((double)logf(ph) + C.lsphi);
+        if (in.mud > 0.0) ep.logphi += in.mud * ((double)logf(ph) + C.lsphi);
         break;
     }
     case EPI_PHI_FREE:
@@ -153,35 +263,32 @@ __device__ __forceinline__ void epilogue_point(const Task& T, const FacCache& tf
         break;
     case EPI_ROOT: {
         // mass and violation of the last iterate (scale record prev), then the update
-        const float t = eval_prod(tf, i);
-        const float old = T.phi[i] * C.inv_mx_old;
-        const double P = (double)(old * t) * C.E;
+        const float old = in.phi * C.inv_mx_old;
+        const double P = (double)(old * in.t) * C.E;
         ep.mass += P;
         if (T.free_node) {
             ep.mx_phi = 1.f;
         } else {
-            ep.viol += fabs(P - T.mu_d[i]);
-            const float ph = T.mu_f[i] / t;
+            ep.viol += fabs(P - in.mud);
+            const float ph = in.muf / in.t;
             T.phi[i] = ph;
             ep.mx_phi = fmaxf(ep.mx_phi, ph);
-            const double m = T.mu_d[i];
-            if (m > 0.0) ep.logphi += m * ((double)logf(ph) + C.lsphi);
+            if (in.mud > 0.0) ep.logphi += in.mud * ((double)logf(ph) + C.lsphi);
         }
         break;
     }
     case EPI_CROOT: {
         // raw = sum over the root's column of the circle product (normalised factors)
-        const float old = T.phi[i] * C.inv_mx_old;
+        const float old = in.phi * C.inv_mx_old;
         const double P = (double)(old * raw) * C.E;
         ep.mass += P;
-        ep.viol += fabs(P - T.mu_d[i]);
+        ep.viol += fabs(P - in.mud);
         float g = raw;
         if (!(g >= floor_)) { g = floor_; ep.clamps++; }
-        const float ph = T.mu_f[i] / g;
+        const float ph = in.muf / g;
         T.phi[i] = ph;
         ep.mx_phi = fmaxf(ep.mx_phi, ph);
-        const double m = T.mu_d[i];
-        if (m > 0.0) ep.logphi += m * ((double)logf(ph) + C.lsphi);
+        if (in.mud > 0.0) ep.logphi += in.mud * ((double)logf(ph) + C.lsphi);
         break;
     }
     case EPI_MARG: {
@@ -189,11 +296,10 @@ __device__ __forceinline__ void epilogue_point(const Task& T, const FacCache& tf
         if (!(g >= floor_)) { g = floor_; ep.clamps++; }
         if (T.out) T.out[i] = g;
         ep.mx_out = fmaxf(ep.mx_out, g);
-        const float t = eval_prod(tf, i);            // phi^k and the children's messages
-        const double P = (double)(g * t) * C.E;
+        const double P = (double)(g * in.t) * C.E;
         ep.mass += P;
-        if (T.mu_d) ep.viol += fabs(P - T.mu_d[i]);
-        if (P > 0.0) ep.plogphi += P * ((double)logf(T.phi[i]) + C.ls_phi_k);
+        if (T.mu_d) ep.viol += fabs(P - in.mud);
+        if (P > 0.0) ep.plogphi += P * ((double)logf(in.phi) + C.ls_phi_k);
         break;
     }
     default:
@@ -201,47 +307,70 @@ __device__ __forceinline__ void epilogue_point(const Task& T, const FacCache& tf
     }
 }
 
-// Reduce the partials of the block and publish them.  All threads call it.
+__device__ __forceinline__ void epilogue_point(const Task& T, const FacCache& tf, const EpiConst& C,
+                                               float floor_, int i, float raw, EpiPartial& ep) {
+    epilogue_point_in(T, C, floor_, i, raw, epi_load(T, tf, i), ep);
+}
+
+// Reduce the partials of the block and publish them.  All threads call it.  Only the
+// quantities the task's mode produces are reduced (the FP64 ones cost most); warp 0 combines
+// the warps' partials lane-parallel.  `iter` is the sweep counter read at the kernel's start.
 __device__ __forceinline__ void epi_block_finish(const Task& T, const Globals& G, const FacCache& tf,
-                                                 double Lsrc, EpiPartial ep) {
+                                                 double Lsrc, EpiPartial ep, int iter) {
     __shared__ float s_mx[2][32];
     __shared__ double s_d[4][32];
     __shared__ unsigned int s_c[32];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    float a = warp_max(ep.mx_out), b = warp_max(ep.mx_phi);
-    double l = warp_sum_d(ep.logphi), v = warp_sum_d(ep.viol), m = warp_sum_d(ep.mass), pl = warp_sum_d(ep.plogphi);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const int mode = T.mode;
+    const bool has_out = (mode == EPI_MSG || mode == EPI_MARG ||
+                          ((mode == EPI_PHI || mode == EPI_PHI_FREE) && T.out != nullptr)) && T.out_sc != nullptr;
+    const bool has_phi = mode == EPI_PHI || mode == EPI_ROOT || mode == EPI_PHI_FREE || mode == EPI_CROOT;
+    const bool d_log = mode == EPI_PHI || mode == EPI_ROOT || mode == EPI_CROOT;
+    const bool d_vm = mode == EPI_MARG || mode == EPI_ROOT || mode == EPI_CROOT;
+    const bool d_pl = mode == EPI_MARG;
+    float a = has_out ? warp_max(ep.mx_out) : 0.f;
+    float b = has_phi ? warp_max(ep.mx_phi) : 0.f;
+    double l = d_log ? warp_sum_d(ep.logphi) : 0.0;
+    double v = d_vm ? warp_sum_d(ep.viol) : 0.0;
+    double m = d_vm ? warp_sum_d(ep.mass) : 0.0;
+    double pl = d_pl ? warp_sum_d(ep.plogphi) : 0.0;
     unsigned int c = ep.clamps;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if (lane == 0) { s_mx[0][w] = a; s_mx[1][w] = b; s_d[0][w] = l; s_d[1][w] = v; s_d[2][w] = m; s_d[3][w] = pl; s_c[w] = c; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 1; k < nw; ++k) {
-            a = fmaxf(a, s_mx[0][k]); b = fmaxf(b, s_mx[1][k]);
-            l += s_d[0][k]; v += s_d[1][k]; m += s_d[2][k]; pl += s_d[3][k]; c += s_c[k];
-        }
-        const bool has_out = (T.mode == EPI_MSG || T.mode == EPI_MARG ||
-                              ((T.mode == EPI_PHI || T.mode == EPI_PHI_FREE) && T.out != nullptr));
-        if (has_out && T.out_sc) {
-            T.out_sc->ls = Lsrc;
-            atomic_max_pos(&T.out_sc->mx_bits, a);
-            if (c) atomicAdd(&T.out_sc->clamped, c);
-        }
-        if (T.mode == EPI_MARG && T.acc_node) {
-            atomicAdd(T.acc_node + 0, v);
-            atomicAdd(T.acc_node + 1, pl);
-            atomicAdd(T.acc_node + 2, m);
-        }
-        if (T.mode == EPI_PHI || T.mode == EPI_ROOT || T.mode == EPI_PHI_FREE || T.mode == EPI_CROOT) {
-            T.phi_sc->ls = phi_logscale(T, tf, Lsrc);
-            atomic_max_pos(&T.phi_sc->mx_bits, b);
-            int it = *G.iter;
-            IterAcc* nxt = G.acc + ((it + 1) % G.R);
-            if (l != 0.0) atomicAdd(&nxt->logphi, l);
-            if (T.mode == EPI_ROOT || T.mode == EPI_CROOT) {
-                IterAcc* cur = G.acc + (it % G.R);
-                atomicAdd(&cur->mass, m);
-                atomicAdd(&cur->rootviol, v);
+    if (w == 0) {
+        const bool in = lane < nw;
+        a = has_out ? warp_max(in ? s_mx[0][lane] : 0.f) : 0.f;
+        b = has_phi ? warp_max(in ? s_mx[1][lane] : 0.f) : 0.f;
+        l = d_log ? warp_sum_d(in ? s_d[0][lane] : 0.0) : 0.0;
+        v = d_vm ? warp_sum_d(in ? s_d[1][lane] : 0.0) : 0.0;
+        m = d_vm ? warp_sum_d(in ? s_d[2][lane] : 0.0) : 0.0;
+        pl = d_pl ? warp_sum_d(in ? s_d[3][lane] : 0.0) : 0.0;
+        c = in ? s_c[lane] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) {
+            if (has_out) {
+                T.out_sc->ls = Lsrc;
+                atomic_max_pos(&T.out_sc->mx_bits, a);
+                if (c) atomicAdd(&T.out_sc->clamped, c);
+            }
+            if (mode == EPI_MARG && T.acc_node) {
+                atomicAdd(T.acc_node + 0, v);
+                atomicAdd(T.acc_node + 1, pl);
+                atomicAdd(T.acc_node + 2, m);
+            }
+            if (has_phi) {
+                T.phi_sc->ls = phi_logscale(T, tf, Lsrc);
+                atomic_max_pos(&T.phi_sc->mx_bits, b);
+                IterAcc* nxt = G.acc + ((iter + 1) % G.R);
+                if (l != 0.0) atomicAdd(&nxt->logphi, l);
+                if (mode == EPI_ROOT || mode == EPI_CROOT) {
+                    IterAcc* cur = G.acc + (iter % G.R);
+                    atomicAdd(&cur->mass, m);
+                    atomicAdd(&cur->rootviol, v);
+                }
             }
         }
     }

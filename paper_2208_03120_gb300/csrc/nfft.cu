@@ -341,20 +341,14 @@ __global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, 
 template <int D>
 __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, Globals G) {
     __shared__ Task T;
-    __shared__ FacCache tf;
+    __shared__ FacCache fc, tf;
     __shared__ double sLsrc;
     __shared__ EpiConst sC;
+    __shared__ EpiPre sP;
     extern __shared__ float tile[];
     load_task(T, tasks + blockIdx.y);
     __syncthreads();
-    load_factors(tf, G.fac, T.tf0, T.tnf);
-    if (threadIdx.x < 32) {
-        const double L = T.alpha == nullptr ? factors_L_warp(G.fac, T.sf0, T.snf) : 0.0;
-        if (threadIdx.x == 0) {
-            sLsrc = L;
-            epi_prepare(T, tf, L, sC);
-        }
-    }
+    load_task_consts(T, G, fc, tf, sP, sC, sLsrc);
     __syncthreads();
     const double Lsrc = sLsrc;
     const EpiConst C = sC;
@@ -388,6 +382,7 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
             }
             const int j1 = sb.start + sb.len;
             for (int j = sb.start + threadIdx.x; j < j1; j += blockDim.x) {
+                const EpiIn in = epi_load(T, tf, j);
                 float w[D][MOT_W];
                 int base = 0, stride = 1;
 #pragma unroll
@@ -427,11 +422,11 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
                         for (int q = 0; q < MOT_W - 1; ++q) w[D - 1][q] = w[D - 1][q + 1];
                     }
                 }
-                epilogue_point(T, tf, C, G.floor_, j, acc, ep);
+                epilogue_point_in(T, C, G.floor_, j, acc, in, ep);
             }
         }
     }
-    epi_block_finish(T, G, tf, Lsrc, ep);
+    epi_block_finish(T, G, tf, Lsrc, ep, sP.iter);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -452,7 +447,7 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
 #define F2_M 16
 #define F2_MAXR 8          // rows per CTA (n / CS) for CS >= 8
 #define F2_MAXC 3          // columns per CTA (ceil((M+1) / CS)) for CS >= 8
-#define F2_THREADS 512
+#define F2_THREADS 640
 #define F2_DYN_SMEM (F2_THREADS / 32 * SP2_WARP * 4)   // spread staging
 
 // Sum of `v` over groups of G consecutive lanes (G a power of two <= 32).
@@ -470,6 +465,9 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
     __shared__ FacCache fc, tf;
     __shared__ double sLsrc;
     __shared__ EpiConst sC;
+    __shared__ EpiPre sP;
+    __shared__ int s_ylo, s_yhi;                   // window rows of this CTA's targets
+    __shared__ int s_next;                         // next spread batch of this CTA
     __shared__ float Gs[F2_N * F2_N];
     __shared__ float Grow[F2_MAXR * F2_N];
     __shared__ float2 Gx[F2_MAXR * (F2_M + 1)];
@@ -487,16 +485,12 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
     const int CS = (int)cluster.num_blocks();
     const int r = (int)cluster.block_rank();
     load_task(T, tasks + blockIdx.y);
-    __syncthreads();
-    if (r == 0 && tid == 0) task_resets(T, G, 0);
-    if (T.alpha == nullptr) load_factors(fc, G.fac, T.sf0, T.snf);
-    load_factors(tf, G.fac, T.tf0, T.tnf);
-    if (tid == 0) {
-        sLsrc = T.alpha == nullptr ? fc.L : 0.0;
-        epi_prepare(T, tf, sLsrc, sC);
-    }
     const int n = G.n_grid, M = G.M, mask = n - 1;
-    const bool fast = T.hgrid != nullptr;
+    if (tid == 0) {
+        s_ylo = 1 << 30;
+        s_yhi = -(1 << 30);
+        s_next = 0;
+    }
     for (int i = tid; i < n * n; i += nt) Gs[i] = 0.f;
     for (int k = tid; k < n; k += nt) {
         float sn, cs;
@@ -504,18 +498,20 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
         tw[k] = make_float2(cs, -sn);                  // e^{-2 pi i k / n}
     }
     __syncthreads();
+    if (r == 0 && tid == 0) task_resets(T, G, 0);
+    load_task_consts(T, G, fc, tf, sP, sC, sLsrc);   // constants visible after the next barrier
+    const bool fast = T.hgrid != nullptr;
     EpiPartial ep;
     epi_zero(ep);
-    const double Lsrc = sLsrc;
-    const EpiConst C = sC;
 
     if (fast) {
         // ---- 1. spread: warps walk contiguous runs of cell-sorted points ----------------------
+        // 16-point batches: rank r takes every CS-th batch of the sorted sources (so sparse
+        // regions, one flush per point, and dense ones, long runs, are shared evenly between the
+        // CTAs), and its warps claim them one at a time from a shared counter
         const int Ns = T.src.n;
-        const int j0 = (int)((long long)r * Ns / CS), j1 = (int)((long long)(r + 1) * Ns / CS);
         {
-            const int chunk = (j1 - j0 + nwarps - 1) / nwarps;
-            const int w0 = j0 + min(j1 - j0, warp * chunk), w1 = j0 + min(j1 - j0, (warp + 1) * chunk);
+            const int nbatch = (Ns + SP2_B - 1) / SP2_B;
             float* stg = f2_stage + warp * SP2_WARP;
             Spread2Acc A;
             A.init(lane);
@@ -529,12 +525,36 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
                     for (int i = 0; i < 4; ++i)
                         if (i < S.nb) atomicAdd(&Gs[((cly + S.b0 + i) & mask) * n + ((clx + S.a) & mask)], S.acc[i]);
             };
-            for (int jb = w0; jb < w1; jb += SP2_B) {
-                const int cnt = min(SP2_B, w1 - jb);
+            for (;;) {
+                int k = 0;
+                if (lane == 0) k = atomicAdd(&s_next, 1);
+                const int b = r + CS * __shfl_sync(0xffffffffu, k, 0);
+                if (b >= nbatch) break;
+                const int jb = b * SP2_B, cnt = min(SP2_B, Ns - jb);
+                cur = -1;
                 const int key = spread2_stage(stg, lane, jb, cnt, T.src.u, T.src.u + Ns, value, cell);
                 spread2_accumulate(stg, cnt, key, lane, A, cur, flush);
+                flush(cur, A);
             }
-            if (cur >= 0) flush(cur, A);
+        }
+        {   // rows of h this CTA's targets will read: [min ly, max ly + 9] (targets are cell-sorted)
+            const int Nt = T.tgt.n;
+            const int i0 = (int)((long long)r * Nt / CS), i1 = (int)((long long)(r + 1) * Nt / CS);
+            int lo = 1 << 30, hi = -(1 << 30);
+            for (int i = i0 + tid; i < i1; i += nt) {
+                const int ly = (int)floorf(T.tgt.u[Nt + i]) - MOT_WHALF;
+                lo = min(lo, ly);
+                hi = max(hi, ly);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            }
+            if (lane == 0 && lo <= hi) {
+                atomicMin(&s_ylo, lo);
+                atomicMax(&s_yhi, hi);
+            }
         }
         cluster.sync();
         // ---- 2. reduce owned rows, DFT along x (4 lanes per output) ---------------------
@@ -656,27 +676,41 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
             }
         }
         cluster.sync();
-        // ---- 5. copy h, interpolate (one thread per target) ------------------------------
-        for (int i0 = tid; i0 < n * n; i0 += 4 * nt) {
-            float vals[4];
-#pragma unroll
-            for (int u4 = 0; u4 < 4; ++u4) {
-                const int i = i0 + u4 * nt;
-                vals[u4] = 0.f;
-                if (i < n * n) {
-                    const int y = i / n;
-                    const int owner = y / R;
-                    vals[u4] = cluster.map_shared_rank(Hrow, owner)[(y - owner * R) * n + (i - y * n)];
-                }
+        // ---- 5. copy the rows of h this CTA reads, interpolate (one thread per target) -------
+        {
+            int ylo = s_ylo, nrows = s_yhi >= s_ylo ? s_yhi - s_ylo + MOT_W : 0;
+            if (nrows >= n) {
+                ylo = 0;
+                nrows = n;
             }
+            const int cnt = nrows * n;
+            for (int i0 = tid; i0 < cnt; i0 += 4 * nt) {
+                float vals[4];
+                int dst[4];
 #pragma unroll
-            for (int u4 = 0; u4 < 4; ++u4)
-                if (i0 + u4 * nt < n * n) Gs[i0 + u4 * nt] = vals[u4];
+                for (int u4 = 0; u4 < 4; ++u4) {
+                    const int i = i0 + u4 * nt;
+                    vals[u4] = 0.f;
+                    dst[u4] = -1;
+                    if (i < cnt) {
+                        const int q = i / n;
+                        const int y = (ylo + q) & mask, x = i - q * n;
+                        const int owner = y / R;
+                        vals[u4] = cluster.map_shared_rank(Hrow, owner)[(y - owner * R) * n + x];
+                        dst[u4] = y * n + x;
+                    }
+                }
+#pragma unroll
+                for (int u4 = 0; u4 < 4; ++u4)
+                    if (dst[u4] >= 0) Gs[dst[u4]] = vals[u4];
+            }
         }
         cluster.sync();      // peers may now leave; Hrow of this CTA is no longer read
+        const EpiConst C = sC;
         const int Nt = T.tgt.n;
         const int i0 = (int)((long long)r * Nt / CS), i1 = (int)((long long)(r + 1) * Nt / CS);
         for (int i = i0 + tid; i < i1; i += nt) {
+            const EpiIn in = epi_load(T, tf, i);
             const float ux = T.tgt.u[i], uy = T.tgt.u[Nt + i];
             const float fx = floorf(ux), fy = floorf(uy);
             float wx[MOT_W], wy[MOT_W];
@@ -692,16 +726,17 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
                 for (int a = 0; a < MOT_W; ++a) s2 = fmaf(row[(lx + a) & mask], wx[a], s2);
                 acc = fmaf(s2, wy[b], acc);
             }
-            epilogue_point(T, tf, C, G.floor_, i, acc, ep);
+            epilogue_point_in(T, C, G.floor_, i, acc, in, ep);
         }
     } else {
         // node step without a kernel product; the cluster barrier orders the reset above
         cluster.sync();
+        const EpiConst C = sC;
         const int Nt = T.tgt.n;
         const int i0 = (int)((long long)r * Nt / CS), i1 = (int)((long long)(r + 1) * Nt / CS);
         for (int i = i0 + tid; i < i1; i += nt) epilogue_point(T, tf, C, G.floor_, i, 1.f, ep);
     }
-    epi_block_finish(T, G, tf, Lsrc, ep);
+    epi_block_finish(T, G, tf, sLsrc, ep, sP.iter);
 }
 
 // ------------------------------------------------------------------------------------------
