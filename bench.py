@@ -43,8 +43,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense comparison (profiling runs)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=["path10_d2", "star9_d3", "path3_d1"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=["path10_d2", "star9_d3", "path3_d1", "circle5_d1"],
                     help="profiling runs only: the reported line is defined on path10_d2")
+    ap.add_argument("--path", default="nfft", choices=["nfft", "dense", "tc"],
+                    help="profiling runs only: kernel path of the timed solves")
     ap.add_argument("--n", type=int, default=0, help="profiling runs only: points per marginal")
     ap.add_argument("--max-iter", type=int, default=5000, help="profiling runs only: iteration cap")
     ap.add_argument("--serving-requests", type=int, default=32,
@@ -378,12 +380,14 @@ def main():
     build.build()
     prob = W.WORKLOADS[args.workload](n=args.n) if args.n else W.WORKLOADS[args.workload]()
     prob.root = ROOT_CENTRE
+    topo = M.MOT_CIRCLE if prob.topology == W.CIRCLE else M.MOT_TREE
+    path = {"nfft": M.MOT_PATH_NFFT, "dense": M.MOT_PATH_DENSE, "tc": M.MOT_PATH_DENSE_BF16X3}[args.path]
     x = [torch.from_numpy(a).to(dev) for a in prob.x]
     mu = [torch.from_numpy(m).to(dev) for m in prob.mu]
     stream = torch.cuda.Stream(device=dev)
     tol = TOL if args.max_iter >= 5000 else -1.0
-    opt = M.options(path=M.MOT_PATH_NFFT, tol_viol=tol, max_iter=args.max_iter)
-    ws = torch.empty(M.mot_workspace_bytes(x, mu, prob.eta, M.MOT_TREE, edges=prob.edges, root=prob.root, opt=opt),
+    opt = M.options(path=path, tol_viol=tol, max_iter=args.max_iter)
+    ws = torch.empty(M.mot_workspace_bytes(x, mu, prob.eta, topo, edges=prob.edges, root=prob.root, opt=opt),
                      dtype=torch.uint8, device=dev)
     u = [torch.empty(n, dtype=torch.float64, device=dev) for n in prob.n]
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -394,7 +398,7 @@ def main():
 
     def solve(o=opt):
         with torch.cuda.stream(stream):
-            return M.mot_solve(x, mu, prob.eta, M.MOT_TREE, edges=prob.edges, root=prob.root, opt=o, workspace=ws,
+            return M.mot_solve(x, mu, prob.eta, topo, edges=prob.edges, root=prob.root, opt=o, workspace=ws,
                                stream=stream, u_out=u)
 
     for _ in range(args.warmup):
@@ -436,7 +440,7 @@ def main():
     last = out
 
     # ---- per-kernel durations (events around each launch on the launching stream) -------
-    topt = M.options(path=M.MOT_PATH_NFFT, tol_viol=tol, max_iter=args.max_iter, timing=1)
+    topt = M.options(path=path, tol_viol=tol, max_iter=args.max_iter, timing=1)
     kms = {k: 0.0 for k in M.KERNEL_CLASSES}
     kls = {k: 0 for k in M.KERNEL_CLASSES}
     for _ in range(max(1, min(args.steps, 3))):
@@ -490,17 +494,17 @@ def main():
     # ---- the other workloads (same metric, reported beside the headline) -------------------
     others = {}
     if not args.no_dense and args.workload == WORKLOAD:
-        for wname, topo in (("star9_d3", M.MOT_TREE), ("circle5_d1", M.MOT_CIRCLE)):
+        for wname, wtopo in (("star9_d3", M.MOT_TREE), ("circle5_d1", M.MOT_CIRCLE)):
             wp = W.WORKLOADS[wname]()
             wx = [torch.from_numpy(a).to(dev) for a in wp.x]
             wm = [torch.from_numpy(m).to(dev) for m in wp.mu]
             entry = {}
             paths = [("nfft", M.MOT_PATH_NFFT, 3), ("dense", M.MOT_PATH_DENSE, 2)]
-            if topo == M.MOT_CIRCLE:
+            if wtopo == M.MOT_CIRCLE:
                 paths.append(("dense_bf16x3", M.MOT_PATH_DENSE_BF16X3, 3))
             for pname, path, reps in paths:
                 wo = M.options(path=path, tol_viol=TOL, max_iter=3000)
-                wws = torch.empty(M.mot_workspace_bytes(wx, wm, wp.eta, topo, edges=wp.edges, opt=wo),
+                wws = torch.empty(M.mot_workspace_bytes(wx, wm, wp.eta, wtopo, edges=wp.edges, opt=wo),
                                   dtype=torch.uint8, device=dev)
                 tt, ti = 0.0, 0
                 for r in range(reps + 1):
@@ -508,7 +512,7 @@ def main():
                         flush.random_(0, 255)
                         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                         e0.record(stream)
-                        ow = M.mot_solve(wx, wm, wp.eta, topo, edges=wp.edges, opt=wo, workspace=wws, stream=stream)
+                        ow = M.mot_solve(wx, wm, wp.eta, wtopo, edges=wp.edges, opt=wo, workspace=wws, stream=stream)
                         e1.record(stream)
                     e1.synchronize()
                     if r > 0:
@@ -517,7 +521,7 @@ def main():
                 entry[pname] = {"value": ti / tt, "unit": "iters/s", "iters_per_solve": ow.iters,
                                 "violation": ow.violation, "status": ow.status}
                 if path == M.MOT_PATH_DENSE_BF16X3:
-                    entry[pname]["roofline"] = tc_roofline(M, wp, wx, wm, topo, wo, wws, stream, flush)
+                    entry[pname]["roofline"] = tc_roofline(M, wp, wx, wm, wtopo, wo, wws, stream, flush)
                 del wws
             others[wname] = entry
 
@@ -548,7 +552,7 @@ def main():
                 a.copy_(b, non_blocking=True)
             for a, b in zip(mud, muh):
                 a.copy_(b, non_blocking=True)
-            o4 = M.mot_solve(xd, mud, prob.eta, M.MOT_TREE, edges=prob.edges, root=prob.root, opt=opt, workspace=ws,
+            o4 = M.mot_solve(xd, mud, prob.eta, topo, edges=prob.edges, root=prob.root, opt=opt, workspace=ws,
                              stream=stream, u_out=u)
             for a, b in zip(uh, u):
                 a.copy_(b, non_blocking=True)

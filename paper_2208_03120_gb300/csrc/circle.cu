@@ -25,8 +25,19 @@ __global__ void __launch_bounds__(256) k_rowdot(const float* __restrict__ B, con
     for (int cb = c0; cb < c1; cb += 16) {
         const int ce = min(c1, cb + 16);
         float p = 0.f;
-        for (int c = cb; c < ce; ++c)
-            p = fmaf(B[(size_t)c * ni + i] * Gm[(size_t)c * ni + i], __ldg(phi + c), p);
+        if (ce - cb == 16) {        // 32 independent loads in flight
+            float bv[16], gv[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                bv[u] = __ldg(B + (size_t)(cb + u) * ni + i);
+                gv[u] = __ldg(Gm + (size_t)(cb + u) * ni + i);
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) p = fmaf(bv[u] * gv[u], __ldg(phi + cb + u), p);
+        } else {
+            for (int c = cb; c < ce; ++c)
+                p = fmaf(B[(size_t)c * ni + i] * Gm[(size_t)c * ni + i], __ldg(phi + c), p);
+        }
         const float y = p - cmp, t = acc + y;
         cmp = (t - acc) - y;
         acc = t;

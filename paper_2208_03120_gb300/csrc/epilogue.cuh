@@ -376,3 +376,32 @@ __device__ __forceinline__ void epi_block_finish(const Task& T, const Globals& G
     }
     __syncthreads();
 }
+
+// Message-only variant of the block reduction (every task of the launch is EPI_MSG): the maximum
+// and clamp count of the messages written, no FP64 quantities.
+__device__ __forceinline__ void epi_block_finish_msg(const Task& T, double Lsrc, const EpiPartial& ep) {
+    __shared__ float s_mx[32];
+    __shared__ unsigned int s_c[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    float a = warp_max(ep.mx_out);
+    unsigned int c = ep.clamps;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) {
+        s_mx[w] = a;
+        s_c[w] = c;
+    }
+    __syncthreads();
+    if (w == 0) {
+        a = warp_max(lane < nw ? s_mx[lane] : 0.f);
+        c = lane < nw ? s_c[lane] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0 && T.out_sc) {
+            T.out_sc->ls = Lsrc;
+            atomic_max_pos(&T.out_sc->mx_bits, a);
+            if (c) atomicAdd(&T.out_sc->clamped, c);
+        }
+    }
+    __syncthreads();
+}

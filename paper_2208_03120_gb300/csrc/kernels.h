@@ -36,7 +36,18 @@ cudaError_t prepare_window();
 cudaError_t prepare_fused2d();
 bool fused2d_supported(int d, int n);
 int fused2d_cluster_size();
-cudaError_t launch_fused2d(const Task* tasks, int ntask, const Globals& G, cudaStream_t st);
+// msg_only: every task is a message product with a kernel sum (lean instance).
+cudaError_t launch_fused2d(const Task* tasks, int ntask, const Globals& G, cudaStream_t st, bool msg_only);
+// Batched 1-D fast summation of the circle (grids n <= 128): per-point window taps and base cells
+// (once per solve), the circulant of D (once per edge), and one batch Y[c] = K (phi (.) X[c]):
+// stage 0 zeroes G and spreads, stage 1 convolves, interpolates and writes the messages.
+bool c1_supported(int d, int n);
+cudaError_t launch_c1_taps(const float* u, int n, int* l0, float* w, cudaStream_t st);
+cudaError_t launch_c1_circulant(const float* D, int M, int n, float* c, cudaStream_t st);
+cudaError_t launch_c1_batch(const float* X, const VecScale* sX, const float* phi, const VecScale* sP, const int* l0s,
+                            const float* ws, int ns, const int* l0t, const float* wt, int nt, int n0, int ng,
+                            const float* cvec, float* G, float* Y, float floor_, VecScale* out_sc, cudaStream_t st,
+                            int stage);
 // One-block iteration prologue (resets, iteration counter, accumulators).
 cudaError_t launch_prologue(VecScale* const* list, int nlist, int save_prev, int bump, double* zero_d, int zero_n,
                             const Globals& G, cudaStream_t st);
@@ -84,6 +95,8 @@ cudaError_t launch_output(const float* phi, const VecScale* sc, const int* perm,
 cudaError_t launch_init_phi(float* phi, VecScale* sc, const int* perm, const double* mu_d, int n,
                             const double* u_warm, double eta, double* logphi, float* scratch_max,
                             cudaStream_t st);
+// Timing aid: a single-thread sleep of at most 0.1 s on the device clock.
+cudaError_t launch_delay(unsigned long long ns, cudaStream_t st);
 // Scatter a plain vector into sorted order and back.
 cudaError_t launch_permute_in(const float* src, const int* perm, int n, float* dst, cudaStream_t st);
 cudaError_t launch_permute_out(const float* src, const int* perm, int n, float* dst, cudaStream_t st);

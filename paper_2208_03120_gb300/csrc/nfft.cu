@@ -430,6 +430,209 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
 }
 
 // ------------------------------------------------------------------------------------------
+// Batched 1-D fast summation of the circle (Algorithm 3, N right-hand sides, d = 1).
+//
+// In one dimension the oversampled grid (n <= 128) is far smaller than the point sets, so a
+// batch Y[c] = K (phi (.) X[c]), c < n0, runs as two passes over the message matrices:
+//   k_c1_spread : G[c] = sum_j X[c][j] phi_j psi(u_j - .)   (32 columns per CTA, lane = column;
+//                 the point's taps are the same for every column and are broadcast)
+//   k_c1_gather : H[c] = C G[c] with the circulant C of Eq. (fastsum_mat) (c(m) = sum_{q<=M}
+//                 D_q cos(2 pi q m / n), the real part of IFFT(D FFT(.))), then
+//                 Y[c][i] = sum_a H[c][l0_i + a] psi_a(u_i) and the message epilogue
+// The window taps and base cells of every point are computed once per solve (k_c1_taps).
+// ------------------------------------------------------------------------------------------
+constexpr int C1_COLS = 32;      // columns per CTA
+constexpr int C1_CHUNK = 128;    // source points staged per step
+constexpr int C1_TGT = 512;      // targets per gather CTA (2 per thread)
+
+__global__ void k_c1_taps(const float* __restrict__ u, int n, int* __restrict__ l0, float* __restrict__ w) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const float x = u[j], fl = floorf(x);
+        float t[MOT_W];
+        window_taps(x - fl, t);
+        l0[j] = (int)fl - MOT_WHALF;
+#pragma unroll
+        for (int a = 0; a < MOT_W; ++a) w[(size_t)j * MOT_W + a] = t[a];
+    }
+}
+
+__global__ void k_c1_circulant(const float* __restrict__ D, int M, int n, float* __restrict__ c) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q <= M; ++q) s += (double)D[q] * cospi(2.0 * (double)((q * m) % n) / (double)n);
+        c[m] = (float)s;
+    }
+}
+
+// grid (ceil(n0 / 32), splits): CTA (b, p) spreads points [p ns / splits, (p+1) ns / splits) of
+// columns [32 b, 32 b + 32) and adds its partial grids to G (zeroed by the caller).
+__global__ void __launch_bounds__(256) k_c1_spread(const float* __restrict__ X, const VecScale* sX,
+                                                   const float* __restrict__ phi, const VecScale* sP,
+                                                   const int* __restrict__ l0, const float* __restrict__ w, int ns,
+                                                   int n0, int ng, float* __restrict__ G) {
+    __shared__ float sV[C1_CHUNK][C1_COLS + 1];
+    __shared__ __align__(16) float sW[C1_CHUNK][12];
+    __shared__ int sL[C1_CHUNK];
+    __shared__ float sG[C1_COLS][128 + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int c0 = blockIdx.x * C1_COLS, mask = ng - 1;
+    const int pb = (int)((long long)blockIdx.y * ns / gridDim.y), pe = (int)((long long)(blockIdx.y + 1) * ns / gridDim.y);
+    const float sx = 1.f / mx_of(sX, 0), sp = 1.f / mx_of(sP, 0);
+    for (int i = tid; i < C1_COLS * ng; i += blockDim.x) sG[i / ng][i % ng] = 0.f;
+    float acc[MOT_W];
+#pragma unroll
+    for (int a = 0; a < MOT_W; ++a) acc[a] = 0.f;
+    int cur = 0;
+    bool have = false;
+    auto flush = [&]() {
+#pragma unroll
+        for (int a = 0; a < MOT_W; ++a) {
+            atomicAdd(&sG[lane][(cur + a) & mask], acc[a]);
+            acc[a] = 0.f;
+        }
+    };
+    const int per_warp = C1_CHUNK / nwarps;
+    for (int jb = pb; jb < pe; jb += C1_CHUNK) {
+        const int cnt = min(C1_CHUNK, pe - jb);
+        __syncthreads();                                    // the previous chunk is consumed
+        {   // all loads of the chunk in flight at once (16 per thread), then the transposed stores
+            constexpr int PER = C1_COLS * C1_CHUNK / 256;
+            float v[PER];
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                const int idx = tid + 256 * r, q = idx / C1_CHUNK, jj = idx - q * C1_CHUNK;
+                v[r] = (jj < cnt && c0 + q < n0) ? __ldg(X + (size_t)(c0 + q) * ns + jb + jj) : 0.f;
+            }
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                const int idx = tid + 256 * r, q = idx / C1_CHUNK, jj = idx - q * C1_CHUNK;
+                sV[jj][q] = v[r] * sx;
+            }
+        }
+        for (int jj = tid; jj < cnt; jj += blockDim.x) {
+            const float pj = phi[jb + jj] * sp;
+            sL[jj] = l0[jb + jj];
+#pragma unroll
+            for (int a = 0; a < MOT_W; ++a) sW[jj][a] = w[(size_t)(jb + jj) * MOT_W + a] * pj;
+        }
+        __syncthreads();
+        const int p0 = warp * per_warp, p1 = min(cnt, p0 + per_warp);
+        for (int p = p0; p < p1; ++p) {
+            const int l = sL[p];
+            if (!have || l != cur) {                        // uniform over the warp
+                if (have) flush();
+                cur = l;
+                have = true;
+            }
+            const float v = sV[p][lane];
+            const float4 w0 = *reinterpret_cast<const float4*>(&sW[p][0]);
+            const float4 w1 = *reinterpret_cast<const float4*>(&sW[p][4]);
+            const float2 w2 = *reinterpret_cast<const float2*>(&sW[p][8]);
+            acc[0] = fmaf(v, w0.x, acc[0]);
+            acc[1] = fmaf(v, w0.y, acc[1]);
+            acc[2] = fmaf(v, w0.z, acc[2]);
+            acc[3] = fmaf(v, w0.w, acc[3]);
+            acc[4] = fmaf(v, w1.x, acc[4]);
+            acc[5] = fmaf(v, w1.y, acc[5]);
+            acc[6] = fmaf(v, w1.z, acc[6]);
+            acc[7] = fmaf(v, w1.w, acc[7]);
+            acc[8] = fmaf(v, w2.x, acc[8]);
+            acc[9] = fmaf(v, w2.y, acc[9]);
+        }
+    }
+    if (have) flush();
+    __syncthreads();
+    for (int i = tid; i < C1_COLS * ng; i += blockDim.x) {
+        const int q = i / ng, x = i - q * ng;
+        const float val = sG[q][x];
+        if (c0 + q < n0 && val != 0.f) atomicAdd(&G[(size_t)(c0 + q) * ng + x], val);
+    }
+}
+
+// grid (ceil(nt / 512), ceil(n0 / 32)): convolution of 32 columns' grids, then two targets per
+// thread for each column, message epilogue (floor, maximum, clamp count) and block reduction.
+__global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, const float* __restrict__ cvec,
+                                                   const int* __restrict__ l0, const float* __restrict__ w, int nt,
+                                                   int n0, int ng, float* __restrict__ Y, float floor_,
+                                                   VecScale* out_sc, const VecScale* sA, const VecScale* sB) {
+    __shared__ float sGc[C1_COLS][128 + 1];
+    __shared__ float sH[C1_COLS][128 + 1];
+    __shared__ float sC[128];
+    __shared__ float s_mx[8];
+    __shared__ unsigned int s_cl[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c0 = blockIdx.y * C1_COLS, mask = ng - 1;
+    const int ncol = min(C1_COLS, n0 - c0);
+    for (int i = tid; i < ng; i += blockDim.x) sC[i] = cvec[i];
+    for (int i = tid; i < ncol * ng; i += blockDim.x) sGc[i / ng][i % ng] = G[(size_t)c0 * ng + i];
+    __syncthreads();
+    for (int i = tid; i < ncol * ng; i += blockDim.x) {
+        const int q = i / ng, x = i - q * ng;
+        float s = 0.f;
+        for (int xp = 0; xp < ng; ++xp) s = fmaf(sC[(x - xp) & mask], sGc[q][xp], s);
+        sH[q][x] = s;
+    }
+    __syncthreads();
+    float mx = 0.f;
+    unsigned int clamps = 0u;
+    auto emit = [&](float s, int q, int i) {
+        if (!(s >= floor_)) {
+            s = floor_;
+            clamps++;
+        }
+        mx = fmaxf(mx, s);
+        Y[(size_t)(c0 + q) * nt + i] = s;
+    };
+    for (int k = 0; k < 2; ++k) {
+        const int i = blockIdx.x * C1_TGT + k * blockDim.x + tid;
+        if (i >= nt) break;
+        float t[MOT_W];
+        const float* hp[MOT_W];                             // column 0 of each tap's grid cell
+        const int b = l0[i];
+#pragma unroll
+        for (int a = 0; a < MOT_W; ++a) {
+            t[a] = w[(size_t)i * MOT_W + a];
+            hp[a] = &sH[0][(b + a) & mask];
+        }
+        if (ncol == C1_COLS) {
+#pragma unroll
+            for (int q = 0; q < C1_COLS; ++q) {             // constant offsets q * (128 + 1)
+                float s = 0.f;
+#pragma unroll
+                for (int a = 0; a < MOT_W; ++a) s = fmaf(hp[a][q * (128 + 1)], t[a], s);
+                emit(s, q, i);
+            }
+        } else {
+            for (int q = 0; q < ncol; ++q) {
+                float s = 0.f;
+#pragma unroll
+                for (int a = 0; a < MOT_W; ++a) s = fmaf(hp[a][q * (128 + 1)], t[a], s);
+                emit(s, q, i);
+            }
+        }
+    }
+    mx = warp_max(mx);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) clamps += __shfl_xor_sync(0xffffffffu, clamps, o);
+    if (lane == 0) {
+        s_mx[warp] = mx;
+        s_cl[warp] = clamps;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float m = 0.f;
+        unsigned int c = 0u;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            m = fmaxf(m, s_mx[k]);
+            c += s_cl[k];
+        }
+        out_sc->ls = sA->ls + (double)logf(mx_of(sA, 0)) + sB->ls + (double)logf(mx_of(sB, 0));
+        atomic_max_pos(&out_sc->mx_bits, m);
+        if (c) atomicAdd(&out_sc->clamped, c);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Fused 2-D fast summation for grids n <= 64: one thread-block cluster per task.
 //
 //   1. each CTA spreads 1/CS of the sources into a private n x n grid in shared memory;
@@ -458,7 +661,10 @@ __device__ __forceinline__ float group_sum(float v) {
     return v;
 }
 
-__global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict__ tasks, Globals G) {
+// MSG: every task of the launch is a message product (EPI_MSG, the backward levels): the
+// instance carries only that epilogue, which keeps its code (fetched cold at every launch) small.
+template <bool MSG>
+__global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restrict__ tasks, Globals G) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     __shared__ Task T;
@@ -499,8 +705,13 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
     }
     __syncthreads();
     if (r == 0 && tid == 0) task_resets(T, G, 0);
-    load_task_consts(T, G, fc, tf, sP, sC, sLsrc);   // constants visible after the next barrier
-    const bool fast = T.hgrid != nullptr;
+    if constexpr (MSG) {
+        if (warp == 0) fill_factors_warp(fc, G.fac, T.sf0, T.snf, lane);
+        __syncthreads();
+    } else {
+        load_task_consts(T, G, fc, tf, sP, sC, sLsrc);   // constants visible after the next barrier
+    }
+    const bool fast = MSG || T.hgrid != nullptr;
     EpiPartial ep;
     epi_zero(ep);
 
@@ -706,11 +917,13 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
             }
         }
         cluster.sync();      // peers may now leave; Hrow of this CTA is no longer read
-        const EpiConst C = sC;
+        EpiConst C;
+        if constexpr (!MSG) C = sC;
         const int Nt = T.tgt.n;
         const int i0 = (int)((long long)r * Nt / CS), i1 = (int)((long long)(r + 1) * Nt / CS);
         for (int i = i0 + tid; i < i1; i += nt) {
-            const EpiIn in = epi_load(T, tf, i);
+            EpiIn in;
+            if constexpr (!MSG) in = epi_load(T, tf, i);
             const float ux = T.tgt.u[i], uy = T.tgt.u[Nt + i];
             const float fx = floorf(ux), fy = floorf(uy);
             float wx[MOT_W], wy[MOT_W];
@@ -726,9 +939,19 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
                 for (int a = 0; a < MOT_W; ++a) s2 = fmaf(row[(lx + a) & mask], wx[a], s2);
                 acc = fmaf(s2, wy[b], acc);
             }
-            epilogue_point_in(T, C, G.floor_, i, acc, in, ep);
+            if constexpr (MSG) {
+                float g = acc;
+                if (!(g >= G.floor_)) {
+                    g = G.floor_;
+                    ep.clamps++;
+                }
+                T.out[i] = g;
+                ep.mx_out = fmaxf(ep.mx_out, g);
+            } else {
+                epilogue_point_in(T, C, G.floor_, i, acc, in, ep);
+            }
         }
-    } else {
+    } else if constexpr (!MSG) {
         // node step without a kernel product; the cluster barrier orders the reset above
         cluster.sync();
         const EpiConst C = sC;
@@ -736,7 +959,10 @@ __global__ void __launch_bounds__(F2_THREADS) k_fastsum2d(const Task* __restrict
         const int i0 = (int)((long long)r * Nt / CS), i1 = (int)((long long)(r + 1) * Nt / CS);
         for (int i = i0 + tid; i < i1; i += nt) epilogue_point(T, tf, C, G.floor_, i, 1.f, ep);
     }
-    epi_block_finish(T, G, tf, sLsrc, ep, sP.iter);
+    if constexpr (MSG)
+        epi_block_finish_msg(T, fc.L, ep);
+    else
+        epi_block_finish(T, G, tf, sLsrc, ep, sP.iter);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1071,10 +1297,13 @@ cudaError_t prepare_fused2d() {
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
     if (g_cluster_size != 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_fastsum2d, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) cudaGetLastError();
-    e = cudaFuncSetAttribute(k_fastsum2d, cudaFuncAttributeMaxDynamicSharedMemorySize, F2_DYN_SMEM);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    for (auto fn : {k_fastsum2d<false>, k_fastsum2d<true>}) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) cudaGetLastError();
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, F2_DYN_SMEM);
+        if (e != cudaSuccess) return e;
+    }
     for (int cs : {16, 8}) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cs, 1, 1);
@@ -1088,7 +1317,7 @@ cudaError_t prepare_fused2d() {
         cfg.attrs = &attr;
         cfg.numAttrs = 1;
         int nclusters = 0;
-        e = cudaOccupancyMaxActiveClusters(&nclusters, k_fastsum2d, &cfg);
+        e = cudaOccupancyMaxActiveClusters(&nclusters, k_fastsum2d<false>, &cfg);
         if (e == cudaSuccess && nclusters > 0) {
             g_cluster_size = cs;
             return cudaSuccess;
@@ -1099,7 +1328,7 @@ cudaError_t prepare_fused2d() {
     return cudaSuccess;
 }
 
-cudaError_t launch_fused2d(const Task* tasks, int ntask, const Globals& G, cudaStream_t st) {
+cudaError_t launch_fused2d(const Task* tasks, int ntask, const Globals& G, cudaStream_t st, bool msg_only) {
     if (ntask <= 0) return cudaSuccess;
     const int cs = g_cluster_size;
     cudaLaunchConfig_t cfg = {};
@@ -1114,7 +1343,8 @@ cudaError_t launch_fused2d(const Task* tasks, int ntask, const Globals& G, cudaS
     attr.val.clusterDim.z = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_fastsum2d, tasks, G);
+    return msg_only ? cudaLaunchKernelEx(&cfg, k_fastsum2d<true>, tasks, G)
+                    : cudaLaunchKernelEx(&cfg, k_fastsum2d<false>, tasks, G);
 }
 
 cudaError_t launch_prologue(VecScale* const* list, int nlist, int save_prev, int bump, double* zero_d, int zero_n,
@@ -1180,4 +1410,34 @@ cudaError_t prepare_window() {
     e = cudaMemcpyToSymbol(c_win, coef, sizeof(coef));
     if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
     return e;
+}
+
+bool c1_supported(int d, int n) { return d == 1 && n >= 16 && n <= 128; }
+
+cudaError_t launch_c1_taps(const float* u, int n, int* l0, float* w, cudaStream_t st) {
+    k_c1_taps<<<std::min((n + 255) / 256, 1024), 256, 0, st>>>(u, n, l0, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_c1_circulant(const float* D, int M, int n, float* c, cudaStream_t st) {
+    k_c1_circulant<<<1, 128, 0, st>>>(D, M, n, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_c1_batch(const float* X, const VecScale* sX, const float* phi, const VecScale* sP, const int* l0s,
+                            const float* ws, int ns, const int* l0t, const float* wt, int nt, int n0, int ng,
+                            const float* cvec, float* G, float* Y, float floor_, VecScale* out_sc, cudaStream_t st,
+                            int stage) {
+    const int nb = (n0 + C1_COLS - 1) / C1_COLS;
+    if (stage == 0) {
+        cudaError_t e = cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n0 * ng, st);
+        if (e != cudaSuccess) return e;
+        const int splits = std::max(1, std::min(8, (2 * 152 + nb - 1) / nb));
+        k_c1_spread<<<dim3(nb, std::min(splits, std::max(1, ns / C1_CHUNK))), 256, 0, st>>>(X, sX, phi, sP, l0s, ws,
+                                                                                            ns, n0, ng, G);
+    } else {
+        k_c1_gather<<<dim3((nt + C1_TGT - 1) / C1_TGT, nb), 256, 0, st>>>(G, cvec, l0t, wt, nt, n0, ng, Y, floor_,
+                                                                         out_sc, sP, sX);
+    }
+    return cudaGetLastError();
 }

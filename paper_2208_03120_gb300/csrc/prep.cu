@@ -459,3 +459,25 @@ cudaError_t launch_permute_out(const float* src, const int* perm, int n, float* 
     k_permute_out<<<blocks_for(n), 256, 0, st>>>(src, perm, n, dst);
     return cudaGetLastError();
 }
+
+// ------------------------------------------------------------------------------------------
+// Timing aid: one thread sleeps until `ns` nanoseconds have passed (a bounded wait on the clock,
+// on nothing else), so that the host can enqueue the launches of a timed chunk ahead of the GPU
+// and the per-launch events measure device time only.
+// ------------------------------------------------------------------------------------------
+namespace {
+__global__ void k_delay(unsigned long long ns) {
+    if (threadIdx.x != 0) return;
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    do {
+        __nanosleep(20000);
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    } while (t - t0 < ns);
+}
+}  // namespace
+
+cudaError_t launch_delay(unsigned long long ns, cudaStream_t st) {
+    k_delay<<<1, 32, 0, st>>>(ns < 100000000ull ? ns : 100000000ull);
+    return cudaGetLastError();
+}

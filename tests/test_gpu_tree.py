@@ -232,3 +232,19 @@ def test_barycenter_free_centre(M, path):
     assert abs(dg - do) <= REL * abs(do)
     assert abs(out.cost_dual - do) <= REL * abs(do)
     assert np.sum(np.abs(Pg[0] - Po[0])) <= REL
+
+
+def test_timing_mode_same_result(M):
+    """options.timing (per-launch events, sweeps captured into timed graphs) computes the same
+    sweeps as the untimed solve (up to the order of atomic FP32 additions, which differs from
+    run to run) and reports device time per kernel class."""
+    prob = W.path10_d2(n=3000)
+    prob.root = -1
+    o1, u1 = gpu_solve(M, prob, tol_viol=-1.0, max_iter=30)
+    o2, u2 = gpu_solve(M, prob, tol_viol=-1.0, max_iter=30, timing=1)
+    assert o1.iters == o2.iters == 30
+    assert abs(o1.cost_dual - o2.cost_dual) <= 1e-6 * abs(o1.cost_dual)
+    a, b = OS.gauge_fix(u1, prob.mu), OS.gauge_fix(u2, prob.mu)
+    for va, vb in zip(a, b):
+        assert np.max(np.abs(va - vb)) <= 1e-5 * (np.max(np.abs(vb)) + prob.eta)
+    assert o2.kernel_launches["fused"] >= 30 * 6 and sum(o2.kernel_ms.values()) > 0
