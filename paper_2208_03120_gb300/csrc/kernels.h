@@ -6,10 +6,12 @@
 
 // Binning geometry of the oversampled grid, shared by the binning and the spread / gather kernels.
 inline __host__ __device__ int mot_tile_size(int d, int n) {
-    int t = d == 1 ? 256 : (d == 2 ? 16 : 8);
+    int t = d == 1 ? 256 : 16;
     return t < n ? t : n;
 }
-inline __host__ __device__ int mot_sub_points(int d) { return d == 1 ? 1024 : 256; }
+// Subproblem size: 3-D tiles (16^3 cells, ~10^3 points at the workloads' densities) are loaded and
+// flushed once per subproblem, so a subproblem takes about a tile's points.
+inline __host__ __device__ int mot_sub_points(int d) { return d == 2 ? 256 : 1024; }
 inline __host__ __device__ int mot_ncells(int d, int n) {
     int t = 1;
     for (int i = 0; i < d; ++i) t *= n;

@@ -27,6 +27,31 @@ __device__ __forceinline__ void tile_origin(int tile, int ntd, int TS, int* o) {
     }
 }
 
+// Visit every element of a padded tile (P^D, origin o on the periodic grid of length n): a warp
+// per row of P elements, lanes along x; f(tile index, grid index).  Indices advance row by row,
+// with one wrap per coordinate instead of a division per element.
+template <int D, class F>
+__device__ __forceinline__ void for_tile(int P, const int* o, int n, F f) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    auto wrap = [n](int v) { return v < 0 ? v + n : (v >= n ? v - n : v); };
+    if (D == 1) {
+        for (int x = threadIdx.x; x < P; x += blockDim.x) f(x, wrap(o[0] + x));
+        return;
+    }
+    const int rows = D == 2 ? P : P * P;
+    for (int row = warp; row < rows; row += nwarps) {
+        int ty = row, gz = 0;
+        if (D == 3) {
+            const int tz = row / P;
+            ty = row - tz * P;
+            gz = wrap(o[2] + tz);
+        }
+        const int gy = wrap(o[1] + ty);
+        const int gbase = (gz * n + gy) * n, tbase = row * P;
+        for (int x = lane; x < P; x += 32) f(tbase + x, gbase + wrap(o[0] + x));
+    }
+}
+
 template <int D>
 __device__ __forceinline__ int tile_to_global(int idx, int P, const int* o, int n) {
     int g = 0, stride = 1;
@@ -246,10 +271,10 @@ __global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, 
     int o[3] = {0, 0, 0};
     auto flush_tile = [&]() {
         __syncthreads();
-        for (int i = threadIdx.x; i < npad; i += blockDim.x) {
-            const float val = tile[i];
-            if (val != 0.f) atomicAdd(&T.grid[tile_to_global<D>(i, P, o, n)], val);
-        }
+        for_tile<D>(P, o, n, [&](int ti, int gi) {
+            const float val = tile[ti];
+            if (val != 0.f) atomicAdd(&T.grid[gi], val);
+        });
     };
     for (int s = sbeg; s < send; ++s) {
         const Sub sb = T.src.subs[s];
@@ -376,7 +401,7 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
             if (sb.tile != cur_tile) {      // consecutive subproblems mostly share the tile
                 __syncthreads();
                 tile_origin<D>(sb.tile, ntd, TS, o);
-                for (int i = threadIdx.x; i < npad; i += blockDim.x) tile[i] = __ldg(&T.hgrid[tile_to_global<D>(i, P, o, n)]);
+                for_tile<D>(P, o, n, [&](int ti, int gi) { tile[ti] = __ldg(&T.hgrid[gi]); });
                 cur_tile = sb.tile;
                 __syncthreads();
             }
@@ -1251,9 +1276,19 @@ size_t fftconv_smem(int d, int n) {
 }
 
 cudaError_t prepare_fftconv(int d, int n) {
-    static int c1 = 0, c2 = 0, c3a = 0, c3b = 0;
+    static int c1 = 0, c2 = 0, c3a = 0, c3b = 0, s1 = 0, s2 = 0, s3 = 0, g1 = 0, g2 = 0, g3 = 0;
     size_t sm = fftconv_smem(d, n);
     cudaError_t e = cudaSuccess;
+    // padded tiles of the spread / gather kernels (3-D: 25^3 floats)
+    const size_t ss = (size_t)spread_smem_bytes(d, n), gs = (size_t)gather_smem_bytes(d, n);
+    if (d == 1) e = ensure_smem(k_spread<1>, ss, &s1);
+    else if (d == 2) e = ensure_smem(k_spread<2>, ss, &s2);
+    else e = ensure_smem(k_spread<3>, ss, &s3);
+    if (e != cudaSuccess) return e;
+    if (d == 1) e = ensure_smem(k_gather<1>, gs, &g1);
+    else if (d == 2) e = ensure_smem(k_gather<2>, gs, &g2);
+    else e = ensure_smem(k_gather<3>, gs, &g3);
+    if (e != cudaSuccess) return e;
     if (d == 1) e = ensure_smem(k_fftconv1, sm, &c1);
     else if (d == 2) e = ensure_smem(k_fftconv2, sm, &c2);
     else {
