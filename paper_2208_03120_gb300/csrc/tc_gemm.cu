@@ -30,7 +30,7 @@
 namespace {
 
 constexpr int TC_BM = 128;
-constexpr int TC_BK = 64;                       // 64 BF16 = one 128-byte swizzle row
+constexpr int TC_BK = 32;                       // 32 BF16 = one 64-byte swizzle row per stage
 constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -85,14 +85,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major tile, 64-byte swizzle (rows of 32 BF16), 8-row groups
+// 512 bytes apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);           // start address
     d |= (uint64_t)1u << 16;                           // leading byte offset (unused when swizzled)
-    d |= (uint64_t)(1024u >> 4) << 32;                 // stride byte offset: next 8-row group
+    d |= (uint64_t)(512u >> 4) << 32;                  // stride byte offset: next 8-row group
     d |= (uint64_t)1u << 46;                           // descriptor version
-    d |= (uint64_t)2u << 61;                           // 128-byte swizzle
+    d |= (uint64_t)4u << 61;                           // 64-byte swizzle
     return d;
 }
 
@@ -132,19 +133,28 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-template <int BN, int STAGES>
+constexpr uint32_t kMaxSmem = 232448;               // opt-in shared memory per CTA
+
+template <int BN>
 struct TcCfg {
     static constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;
     static constexpr uint32_t B_BYTES = BN * TC_BK * 2;
     static constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    static constexpr int STAGES_FIT = (int)((kMaxSmem - 1024 - 256) / STAGE);
+    static constexpr int STAGES = STAGES_FIT < 6 ? STAGES_FIT : 6;
     static constexpr uint32_t SMEM = STAGES * STAGE + 1024 /* alignment */ + 256 /* barriers */;
+    static constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    static_assert(BN % 16 == 0 && BN <= 256, "MMA N");
+    static_assert(STAGES >= 2, "pipeline depth");
+    static_assert(STAGE % 1024 == 0 || (A_BYTES % 512 == 0 && B_BYTES % 512 == 0), "tile alignment");
 };
 
-template <int BN, int STAGES>
+template <int BN>
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, TcEpi E) {
-    using Cfg = TcCfg<BN, STAGES>;
+    using Cfg = TcCfg<BN>;
+    constexpr int STAGES = Cfg::STAGES;
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte alignment of the shared-window address (the 128-byte swizzle repeats every 1 KB)
     const uint32_t raw_base = smem_u32(smem_raw);
@@ -160,7 +170,11 @@ __global__ void __launch_bounds__(128, 1)
     unsigned int* s_cl = reinterpret_cast<unsigned int*>(s_mx + 4);   // [4]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * BN;
+    // grouped raster over a 1-D grid: 8 tile rows share the B panels in flight (L2 reuse)
+    const int num_m = (E.M + TC_BM - 1) / TC_BM, num_n = (E.N + BN - 1) / BN;
+    const int group = (int)blockIdx.x / (8 * num_n), first_m = group * 8;
+    const int gm = min(num_m - first_m, 8), in_group = (int)blockIdx.x - group * 8 * num_n;
+    const int m0 = (first_m + in_group % gm) * TC_BM, n0 = (in_group / gm) * BN;
     const int nkb = (E.K + TC_BK - 1) / TC_BK;
 
     if (threadIdx.x == 0) {
@@ -176,7 +190,7 @@ __global__ void __launch_bounds__(128, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_taddr)),
-                     "r"((uint32_t)BN)
+                     "r"(Cfg::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -217,9 +231,9 @@ __global__ void __launch_bounds__(128, 1)
             }
             tc_fence_after();
             const uint32_t base = smem_u32(smem + s * Cfg::STAGE);
-            const uint64_t ah = sw128_desc(base), al = sw128_desc(base + Cfg::A_BYTES);
-            const uint64_t bh = sw128_desc(base + 2 * Cfg::A_BYTES);
-            const uint64_t bl = sw128_desc(base + 2 * Cfg::A_BYTES + Cfg::B_BYTES);
+            const uint64_t ah = sw64_desc(base), al = sw64_desc(base + Cfg::A_BYTES);
+            const uint64_t bh = sw64_desc(base + 2 * Cfg::A_BYTES);
+            const uint64_t bl = sw64_desc(base + 2 * Cfg::A_BYTES + Cfg::B_BYTES);
 #pragma unroll
             for (int kk = 0; kk < TC_BK / 16; ++kk) {
                 const uint64_t adv = (uint64_t)(kk * 32 >> 4);   // 16 BF16 = 32 bytes along K
@@ -245,7 +259,7 @@ __global__ void __launch_bounds__(128, 1)
     if (ok) {
         float* stage = reinterpret_cast<float*>(smem) + warp * (32 * 33);   // stages are idle now
         const int row_base = m0 + warp * 32;
-        for (int j = 0; j < BN / 32; ++j) {
+        for (int j = 0; j < (BN + 31) / 32; ++j) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 32), v);
             const bool row_ok = row_base + lane < E.M;
@@ -305,7 +319,8 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tc_fence_after();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS)
+                     : "memory");
 }
 
 // A[c][j] = (phi_j / max phi) (X[c][j] / max X), split into BF16 hi / lo; row stride ld.
@@ -392,7 +407,7 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// rows x cols BF16 matrix with row stride ld elements; box = 64 columns x box_rows rows.
+// rows x cols BF16 matrix with row stride ld elements; box = 32 columns x box_rows rows.
 bool encode_bf16(unsigned char* out, const void* base, int rows, int cols, int ld, int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
@@ -402,18 +417,25 @@ bool encode_bf16(unsigned char* out, const void* base, int rows, int cols, int l
     cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
-                    dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES>
+template <int BN>
 cudaError_t launch_cfg(const TcGemm& g, const TcEpi& e, cudaStream_t st) {
     const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(g.maps);
-    dim3 grid((g.N + BN - 1) / BN, (g.M + TC_BM - 1) / TC_BM);
-    k_tc_gemm<BN, STAGES><<<grid, 128, TcCfg<BN, STAGES>::SMEM, st>>>(m[0], m[1], m[2], m[3], e);
+    const unsigned grid = (unsigned)(((g.N + BN - 1) / BN) * ((g.M + TC_BM - 1) / TC_BM));
+    k_tc_gemm<BN><<<grid, 128, TcCfg<BN>::SMEM, st>>>(m[0], m[1], m[2], m[3], e);
     return cudaGetLastError();
 }
+
+template <int BN>
+cudaError_t set_smem() {
+    return cudaFuncSetAttribute(k_tc_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN>::SMEM);
+}
+
+constexpr int kTileN[5] = {256, 224, 192, 160, 128};
 
 }  // namespace
 
@@ -429,10 +451,11 @@ cudaError_t prepare_tc_gemm() {
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(mu);
     if (done_dev == dev) return cudaSuccess;
-    e = cudaFuncSetAttribute(k_tc_gemm<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<256, 2>::SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_tc_gemm<128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 TcCfg<128, 3>::SMEM);
+    e = set_smem<256>();
+    if (e == cudaSuccess) e = set_smem<224>();
+    if (e == cudaSuccess) e = set_smem<192>();
+    if (e == cudaSuccess) e = set_smem<160>();
+    if (e == cudaSuccess) e = set_smem<128>();
     if (e == cudaSuccess) done_dev = dev;
     return e;
 }
@@ -442,9 +465,16 @@ bool tc_prepare(TcGemm* g, const void* a_hi, const void* a_lo, int M, int lda, c
     g->M = M;
     g->N = N;
     g->K = K;
-    // 128 x 256 tiles when there are enough of them to occupy most SMs, else 128 x 128 tiles
-    const long long t256 = (long long)((N + 255) / 256) * ((M + TC_BM - 1) / TC_BM);
-    g->bn = t256 >= 96 ? 256 : 128;
+    // tile width: fewest waves over the 152 SMs times the per-tile work (ties: wider tiles)
+    long long best = -1;
+    for (int bn : kTileN) {
+        const long long tiles = (long long)((N + bn - 1) / bn) * ((M + TC_BM - 1) / TC_BM);
+        const long long cost = ((tiles + 151) / 152) * bn;
+        if (best < 0 || cost < best) {
+            best = cost;
+            g->bn = bn;
+        }
+    }
     return encode_bf16(g->maps[0], a_hi, M, K, lda, TC_BM) && encode_bf16(g->maps[1], a_lo, M, K, lda, TC_BM) &&
            encode_bf16(g->maps[2], b_hi, N, K, ldb, g->bn) && encode_bf16(g->maps[3], b_lo, N, K, ldb, g->bn);
 }
@@ -454,7 +484,13 @@ cudaError_t launch_tc_gemm(const TcGemm& g, TcEpi e, cudaStream_t st) {
     e.M = g.M;
     e.N = g.N;
     e.K = g.K;
-    return g.bn == 256 ? launch_cfg<256, 2>(g, e, st) : launch_cfg<128, 3>(g, e, st);
+    switch (g.bn) {
+    case 256: return launch_cfg<256>(g, e, st);
+    case 224: return launch_cfg<224>(g, e, st);
+    case 192: return launch_cfg<192>(g, e, st);
+    case 160: return launch_cfg<160>(g, e, st);
+    default: return launch_cfg<128>(g, e, st);
+    }
 }
 
 cudaError_t launch_split_src(const float* X, const VecScale* sX, const float* phi, const VecScale* sP, int ns,

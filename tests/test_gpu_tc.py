@@ -79,3 +79,22 @@ def test_tc_fastsum_tiny_and_large_dynamic_range(M):
     beta = _run(M, xs, xt, np.array([0.75], dtype=np.float32), 0.005)
     ref = OK.direct_sum(xt.astype(np.float64), xs.astype(np.float64), np.array([0.75]), 0.005)
     assert np.all(np.abs(beta - ref) <= TC_TOL * ref)
+
+
+@pytest.mark.parametrize("nrhs,n_src,n_tgt", [
+    (2560, 300, 1000),   # 128-row tiles x 160-wide tiles (140 tiles)
+    (3200, 301, 1000),   # 192-wide tiles (150 tiles), ragged source count
+    (2000, 700, 2000),   # 224-wide tiles (144 tiles): the circle workload's shape
+])
+def test_tc_fastsum_tile_widths(M, nrhs, n_src, n_tgt):
+    """Every tile width the launcher picks (fewest waves over the SMs) against the FP64 product
+    of the kernel matrix with the weights."""
+    rng = np.random.default_rng(nrhs + n_src)
+    xs = W.uniform_ball(rng, n_src, 1, 0.24).astype(np.float32)
+    xt = W.uniform_ball(rng, n_tgt, 1, 0.24).astype(np.float32)
+    alpha = rng.uniform(0.0, 1.0, size=(nrhs, n_src)).astype(np.float32)
+    beta = _run(M, xs, xt, alpha, 0.05).reshape(nrhs, n_tgt)
+    Kmat = OK.kernel_matrix(xt.astype(np.float64), xs.astype(np.float64), 0.05)
+    ref = alpha.astype(np.float64) @ Kmat.T
+    err = np.max(np.abs(beta - ref), axis=1) / np.max(np.abs(ref), axis=1)
+    assert np.max(err) <= TC_TOL
