@@ -37,6 +37,7 @@ cudaError_t prepare_window();
 // Fused 2-D fast summation (one thread-block cluster per task) for grids n <= 64.
 cudaError_t prepare_fused2d();
 bool fused2d_supported(int d, int n);
+int fused2d_max_points();     // largest point set per product the fused kernel takes
 int fused2d_cluster_size();
 // msg_only: every task is a message product with a kernel sum (lean instance).
 cudaError_t launch_fused2d(const Task* tasks, int ntask, const Globals& G, cudaStream_t st, bool msg_only);

@@ -676,7 +676,11 @@ __global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, 
 #define F2_MAXR 8          // rows per CTA (n / CS) for CS >= 8
 #define F2_MAXC 3          // columns per CTA (ceil((M+1) / CS)) for CS >= 8
 #define F2_THREADS 640
-#define F2_DYN_SMEM (F2_THREADS / 32 * SP2_WARP * 4)   // spread staging
+#define F2_MAXPTS 32768    // largest point set of the fused kernel (per-rank source slots below)
+#define F2_SLOTS (F2_MAXPTS / 8)
+// dynamic shared memory: spread staging (SP2_WARP floats per warp), then the rank's source
+// coordinates and values (3 x F2_SLOTS floats; a rank holds at most 1/8 of the sources)
+#define F2_DYN_SMEM ((F2_THREADS / 32 * SP2_WARP + 3 * F2_SLOTS) * 4)
 
 // Sum of `v` over groups of G consecutive lanes (G a power of two <= 32).
 template <int G>
@@ -710,9 +714,12 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
     __shared__ float2 tw[F2_N];
     extern __shared__ float4 f2_dyn[];             // spread staging, SP2_WARP floats per warp
     float* f2_stage = reinterpret_cast<float*>(f2_dyn);
+    float* sUx = f2_stage + (F2_THREADS / 32) * SP2_WARP;   // this rank's sources: x, y, value
+    float* sUy = sUx + F2_SLOTS;
+    float* sVv = sUy + F2_SLOTS;
 
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+    const int lane = tid & 31, warp = tid >> 5;
     const int CS = (int)cluster.num_blocks();
     const int r = (int)cluster.block_rank();
     load_task(T, tasks + blockIdx.y);
@@ -728,6 +735,13 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
         sincospif(2.f * (float)k / (float)n, &sn, &cs);
         tw[k] = make_float2(cs, -sn);                  // e^{-2 pi i k / n}
     }
+    // Launched with programmatic stream serialisation: everything above uses only this launch's
+    // own (static) task; from here on the kernel reads what the previous launch wrote (scale
+    // records, messages, scalings), so it waits for that grid to complete and flush.  The next
+    // launch may then be scheduled: its blocks do their own set-up and wait in the same way, so
+    // at most one launch runs ahead.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __syncthreads();
     if (r == 0 && tid == 0) task_resets(T, G, 0);
     if constexpr (MSG) {
@@ -739,6 +753,17 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
     const bool fast = MSG || T.hgrid != nullptr;
     EpiPartial ep;
     epi_zero(ep);
+    // the first target of this thread: coordinates and epilogue inputs fetched now, used after
+    // the spread and the transforms (their latency hides behind those phases)
+    const int Nt = T.tgt.n;
+    const int ti0 = (int)((long long)r * Nt / CS), ti1 = (int)((long long)(r + 1) * Nt / CS);
+    float pux = 0.f, puy = 0.f;
+    EpiIn pin;
+    if (fast && ti0 + tid < ti1) {
+        pux = T.tgt.u[ti0 + tid];
+        puy = T.tgt.u[Nt + ti0 + tid];
+        if constexpr (!MSG) pin = epi_load(T, tf, ti0 + tid);
+    }
 
     if (fast) {
         // ---- 1. spread: warps walk contiguous runs of cell-sorted points ----------------------
@@ -748,11 +773,23 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
         const int Ns = T.src.n;
         {
             const int nbatch = (Ns + SP2_B - 1) / SP2_B;
+            // prepass: this rank's batches r, r + CS, ... (coordinates and values) into shared
+            // memory in one round of loads; the batch loop then reads no global memory
+            const int nbr = r < nbatch ? (nbatch - r + CS - 1) / CS : 0;
+            for (int q = tid; q < nbr * SP2_B; q += nt) {
+                const int j = (r + CS * (q / SP2_B)) * SP2_B + (q % SP2_B);
+                if (j < Ns) {
+                    sUx[q] = T.src.u[j];
+                    sUy[q] = T.src.u[Ns + j];
+                    sVv[q] = T.alpha ? T.alpha[j] : eval_prod(fc, j);
+                }
+            }
+            __syncthreads();
             float* stg = f2_stage + warp * SP2_WARP;
             Spread2Acc A;
             A.init(lane);
             int cur = -1;
-            auto value = [&](int j) { return T.alpha ? T.alpha[j] : eval_prod(fc, j); };
+            auto value = [&](int q) { return sVv[q]; };
             auto cell = [&](int lx, int ly) { return ((ly & mask) << 8) | (lx & mask); };
             auto flush = [&](int key, const Spread2Acc& S) {
                 const int clx = key & 255, cly = key >> 8;
@@ -764,21 +801,20 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
             for (;;) {
                 int k = 0;
                 if (lane == 0) k = atomicAdd(&s_next, 1);
-                const int b = r + CS * __shfl_sync(0xffffffffu, k, 0);
-                if (b >= nbatch) break;
-                const int jb = b * SP2_B, cnt = min(SP2_B, Ns - jb);
+                k = __shfl_sync(0xffffffffu, k, 0);
+                if (k >= nbr) break;
+                const int cnt = min(SP2_B, Ns - (r + CS * k) * SP2_B);
                 cur = -1;
-                const int key = spread2_stage(stg, lane, jb, cnt, T.src.u, T.src.u + Ns, value, cell);
+                const int key = spread2_stage(stg, lane, k * SP2_B, cnt, sUx, sUy, value, cell);
                 spread2_accumulate(stg, cnt, key, lane, A, cur, flush);
                 flush(cur, A);
             }
         }
         {   // rows of h this CTA's targets will read: [min ly, max ly + 9] (targets are cell-sorted)
-            const int Nt = T.tgt.n;
-            const int i0 = (int)((long long)r * Nt / CS), i1 = (int)((long long)(r + 1) * Nt / CS);
+            const int i0 = ti0, i1 = ti1;
             int lo = 1 << 30, hi = -(1 << 30);
             for (int i = i0 + tid; i < i1; i += nt) {
-                const int ly = (int)floorf(T.tgt.u[Nt + i]) - MOT_WHALF;
+                const int ly = (int)floorf(i == i0 + tid ? puy : T.tgt.u[Nt + i]) - MOT_WHALF;
                 lo = min(lo, ly);
                 hi = max(hi, ly);
             }
@@ -944,12 +980,12 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
         cluster.sync();      // peers may now leave; Hrow of this CTA is no longer read
         EpiConst C;
         if constexpr (!MSG) C = sC;
-        const int Nt = T.tgt.n;
-        const int i0 = (int)((long long)r * Nt / CS), i1 = (int)((long long)(r + 1) * Nt / CS);
+        const int i0 = ti0, i1 = ti1;
         for (int i = i0 + tid; i < i1; i += nt) {
+            const bool first = i == i0 + tid;       // prefetched at the kernel's start
             EpiIn in;
-            if constexpr (!MSG) in = epi_load(T, tf, i);
-            const float ux = T.tgt.u[i], uy = T.tgt.u[Nt + i];
+            if constexpr (!MSG) in = first ? pin : epi_load(T, tf, i);
+            const float ux = first ? pux : T.tgt.u[i], uy = first ? puy : T.tgt.u[Nt + i];
             const float fx = floorf(ux), fy = floorf(uy);
             float wx[MOT_W], wy[MOT_W];
             window_taps(ux - fx, wx);
@@ -980,9 +1016,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
         // node step without a kernel product; the cluster barrier orders the reset above
         cluster.sync();
         const EpiConst C = sC;
-        const int Nt = T.tgt.n;
-        const int i0 = (int)((long long)r * Nt / CS), i1 = (int)((long long)(r + 1) * Nt / CS);
-        for (int i = i0 + tid; i < i1; i += nt) epilogue_point(T, tf, C, G.floor_, i, 1.f, ep);
+        for (int i = ti0 + tid; i < ti1; i += nt) epilogue_point(T, tf, C, G.floor_, i, 1.f, ep);
     }
     if constexpr (MSG)
         epi_block_finish_msg(T, fc.L, ep);
@@ -997,6 +1031,10 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
 // ------------------------------------------------------------------------------------------
 __global__ void k_prologue(VecScale* const* __restrict__ list, int nlist, int save_prev, int bump,
                            double* zero_d, int zero_n, Globals G) {
+    // launched with programmatic stream serialisation: wait for the previous grid, then let the
+    // next launch get scheduled (it waits for this one in the same way)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int t = threadIdx.x;
     for (int i = t; i < nlist; i += blockDim.x) {
         VecScale* s = list[i];
@@ -1327,6 +1365,7 @@ int g_cluster_size = 0;
 int fused2d_cluster_size() { return g_cluster_size; }
 
 bool fused2d_supported(int d, int n) { return d == 2 && n >= 16 && n <= F2_N && g_cluster_size > 0; }
+int fused2d_max_points() { return F2_MAXPTS; }
 
 cudaError_t prepare_fused2d() {
     static std::mutex mu;
@@ -1371,21 +1410,31 @@ cudaError_t launch_fused2d(const Task* tasks, int ntask, const Globals& G, cudaS
     cfg.blockDim = dim3(F2_THREADS, 1, 1);
     cfg.dynamicSmemBytes = F2_DYN_SMEM;
     cfg.stream = st;
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = cs;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // see griddepcontrol in the kernel
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
     return msg_only ? cudaLaunchKernelEx(&cfg, k_fastsum2d<true>, tasks, G)
                     : cudaLaunchKernelEx(&cfg, k_fastsum2d<false>, tasks, G);
 }
 
 cudaError_t launch_prologue(VecScale* const* list, int nlist, int save_prev, int bump, double* zero_d, int zero_n,
                             const Globals& G, cudaStream_t st) {
-    k_prologue<<<1, 256, 0, st>>>(list, nlist, save_prev, bump, zero_d, zero_n, G);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_prologue, list, nlist, save_prev, bump, zero_d, zero_n, G);
 }
 
 // ---- window coefficients ----------------------------------------------------------------------

@@ -328,9 +328,6 @@ int validate_problem(const mot_problem* P) {
     return MOT_OK;
 }
 
-// Largest point set for which a tree uses the fused 2-D cluster kernel.
-constexpr int kFusedMaxPoints = 32768;
-
 // BFS relabelling so that p(k) < k (Section 4.1).
 int tree_structure(const mot_problem* P, TreePlan& T) {
     const int K = P->K;
@@ -982,7 +979,7 @@ int tree_plan_setup(const mot_problem* P, const mot_options& o, TreePlan& T, voi
         // kernel's fixed phases dominate; larger sets use the whole GPU through the 3-kernel path
         int nmax = 0;
         for (int k = 0; k < T.K; ++k) nmax = std::max(nmax, T.n[k]);
-        T.fused = fused2d_supported(T.d, g.n) && nmax <= kFusedMaxPoints;
+        T.fused = fused2d_supported(T.d, g.n) && nmax <= fused2d_max_points();
         size_t gsz = 1;
         for (int t = 0; t < T.d; ++t) gsz *= g.n;
         for (int k = 1; k < T.K; ++k) {
