@@ -1516,7 +1516,8 @@ cudaError_t launch_c1_batch(const float* X, const VecScale* sX, const float* phi
     if (stage == 0) {
         cudaError_t e = cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n0 * ng, st);
         if (e != cudaSuccess) return e;
-        const int splits = std::max(1, std::min(8, (2 * 152 + nb - 1) / nb));
+        // point splits per column group: stay within one wave of resident CTAs (two per SM)
+        const int splits = std::max(1, std::min(8, (2 * 152) / nb));
         k_c1_spread<<<dim3(nb, std::min(splits, std::max(1, ns / C1_CHUNK))), 256, 0, st>>>(X, sX, phi, sP, l0s, ws,
                                                                                             ns, n0, ng, G);
     } else {
