@@ -54,6 +54,20 @@ def parse():
     return ap.parse_args()
 
 
+def reduce_over_ranks(total_s, iters, world, device=None):
+    """Whole-job figures of `world` replicas: the slowest rank's timed seconds and the sum of the
+    ranks' iterations (each rank solves its own copy; there is no exchange step)."""
+    if world <= 1:
+        return total_s, float(iters)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_s], dtype=torch.float64, device=device)
+    n = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(n[0])
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -428,14 +442,7 @@ def main():
     barrier()
     clk = clocks.stop()
     total = sum(times)
-    if world > 1:
-        t = torch.tensor([total, float(iters)], dtype=torch.float64, device=dev)
-        tmax = t[:1].clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        total, iters_all = float(tmax[0]), float(t[1])
-    else:
-        iters_all = float(iters)
+    total, iters_all = reduce_over_ranks(total, iters, world, dev)
     value = iters_all / total
     last = out
 
