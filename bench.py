@@ -532,6 +532,35 @@ def main():
                 del wws
             others[wname] = entry
 
+    # ---- the circle at N = 10^4: NFFT against the dense tensor-core path --------------------
+    if not args.no_dense and args.workload == WORKLOAD:
+        wp = W.circle5_d1(n=10_000)
+        wx = [torch.from_numpy(a).to(dev) for a in wp.x]
+        wm = [torch.from_numpy(m).to(dev) for m in wp.mu]
+        entry = {}
+        for pname, path_ in (("nfft", M.MOT_PATH_NFFT), ("dense_bf16x3", M.MOT_PATH_DENSE_BF16X3)):
+            wo = M.options(path=path_, tol_viol=TOL, max_iter=200)
+            wws = torch.empty(M.mot_workspace_bytes(wx, wm, wp.eta, M.MOT_CIRCLE, opt=wo), dtype=torch.uint8,
+                              device=dev)
+            tt, ti = 0.0, 0
+            for r in range(2):
+                with torch.cuda.stream(stream):
+                    flush.random_(0, 255)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ow = M.mot_solve(wx, wm, wp.eta, M.MOT_CIRCLE, opt=wo, workspace=wws, stream=stream)
+                    e1.record(stream)
+                e1.synchronize()
+                if r > 0:
+                    tt += e0.elapsed_time(e1) / 1e3
+                    ti += ow.iters
+            entry[pname] = {"value": ti / tt, "unit": "iters/s", "iters_per_solve": ow.iters,
+                            "violation": ow.violation, "status": ow.status, "ms_per_solve": 1e3 * tt}
+            if path_ == M.MOT_PATH_DENSE_BF16X3:
+                entry[pname]["roofline"] = tc_roofline(M, wp, wx, wm, M.MOT_CIRCLE, wo, wws, stream, flush)
+            del wws
+        others["circle5_d1_N1e4"] = entry
+
     # ---- scale-up of the headline workload (N = 10^6) ---------------------------------------
     if not args.no_dense and args.workload == WORKLOAD:
         others["path10_d2_N1e6"] = scaleup_tree(M, W, dev, stream, flush)

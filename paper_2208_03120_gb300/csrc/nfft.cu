@@ -494,15 +494,19 @@ __global__ void k_c1_circulant(const float* __restrict__ D, int M, int n, float*
 __global__ void __launch_bounds__(256) k_c1_spread(const float* __restrict__ X, const VecScale* sX,
                                                    const float* __restrict__ phi, const VecScale* sP,
                                                    const int* __restrict__ l0, const float* __restrict__ w, int ns,
-                                                   int n0, int ng, float* __restrict__ G) {
+                                                   int n0, int ng, int splits, float* __restrict__ G) {
     __shared__ float sV[C1_CHUNK][C1_COLS + 1];
     __shared__ __align__(16) float sW[C1_CHUNK][12];
     __shared__ int sL[C1_CHUNK];
     __shared__ float sG[C1_COLS][128 + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    const int c0 = blockIdx.x * C1_COLS, mask = ng - 1;
-    const int pb = (int)((long long)blockIdx.y * ns / gridDim.y), pe = (int)((long long)(blockIdx.y + 1) * ns / gridDim.y);
+    const int mask = ng - 1;
     const float sx = 1.f / mx_of(sX, 0), sp = 1.f / mx_of(sP, 0);
+    const int nitems = ((n0 + C1_COLS - 1) / C1_COLS) * splits;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {   // (column group, point split)
+    const int c0 = (item / splits) * C1_COLS, sidx = item % splits;
+    const int pb = (int)((long long)sidx * ns / splits), pe = (int)((long long)(sidx + 1) * ns / splits);
+    __syncthreads();                                        // the previous item's grid is written out
     for (int i = tid; i < C1_COLS * ng; i += blockDim.x) sG[i / ng][i % ng] = 0.f;
     float acc[MOT_W];
 #pragma unroll
@@ -572,6 +576,7 @@ __global__ void __launch_bounds__(256) k_c1_spread(const float* __restrict__ X, 
         const float val = sG[q][x];
         if (c0 + q < n0 && val != 0.f) atomicAdd(&G[(size_t)(c0 + q) * ng + x], val);
     }
+    }   // item
 }
 
 // grid (ceil(nt / 512), ceil(n0 / 32)): convolution of 32 columns' grids, then two targets per
@@ -1516,10 +1521,11 @@ cudaError_t launch_c1_batch(const float* X, const VecScale* sX, const float* phi
     if (stage == 0) {
         cudaError_t e = cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n0 * ng, st);
         if (e != cudaSuccess) return e;
-        // point splits per column group: stay within one wave of resident CTAs (two per SM)
-        const int splits = std::max(1, std::min(8, (2 * 152) / nb));
-        k_c1_spread<<<dim3(nb, std::min(splits, std::max(1, ns / C1_CHUNK))), 256, 0, st>>>(X, sX, phi, sP, l0s, ws,
-                                                                                            ns, n0, ng, G);
+        // work items (column group, point split); a grid of at most one wave of resident CTAs (two
+        // per SM) loops over them
+        const int splits = std::max(1, std::min(std::min(8, std::max(1, (2 * 152) / nb)), std::max(1, ns / C1_CHUNK)));
+        const int items = nb * splits;
+        k_c1_spread<<<std::min(items, 2 * 152), 256, 0, st>>>(X, sX, phi, sP, l0s, ws, ns, n0, ng, splits, G);
     } else {
         k_c1_gather<<<dim3((nt + C1_TGT - 1) / C1_TGT, nb), 256, 0, st>>>(G, cvec, l0t, wt, nt, n0, ng, Y, floor_,
                                                                          out_sc, sP, sX);
