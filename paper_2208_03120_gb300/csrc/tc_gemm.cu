@@ -10,10 +10,13 @@
 // and the product is accumulated in FP32 as  Ahi Bhi + Ahi Blo + Alo Bhi  (the Alo Blo term is
 // below 2^-16 relative and dropped), which keeps ~16 significant bits per term.
 //
-// Kernel structure (one 128 x BN output tile per CTA, 128 threads):
-//   warp 0 / lane 0   TMA producer: per stage of 64 k-values four tiles (Ahi, Alo, Bhi, Blo),
-//                     128-byte swizzled, completion counted on the stage's full mbarrier;
-//   warp 1            allocates BN TMEM columns; lane 0 issues tcgen05.mma (M=128, N=BN, K=16,
+// Kernel structure (one 128 x BN output tile per CTA, 128 threads; BN in {128, 160, 192, 224,
+// 256} chosen so the tiles fill the SMs in as few waves as possible; a 1-D grid rasterised in
+// groups of 8 tile rows so that the B panels of a wave are reused from L2):
+//   warp 0 / lane 0   TMA producer: per stage of 32 k-values four tiles (Ahi, Alo, Bhi, Blo),
+//                     64-byte swizzled, 4-6 stages, completion counted on the stage's full
+//                     mbarrier;
+//   warp 1            allocates the TMEM columns; lane 0 issues tcgen05.mma (M=128, N=BN, K=16,
 //                     BF16 in, FP32 accumulate in TMEM) and frees stages with tcgen05.commit;
 //   warps 0..3        epilogue: tcgen05.ld of their 32 TMEM lanes (= 32 output rows), floor /
 //                     maximum / clamp count of a message (Algorithm 3 normalisation), staged
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(128, 1)
     using Cfg = TcCfg<BN>;
     constexpr int STAGES = Cfg::STAGES;
     extern __shared__ uint8_t smem_raw[];
-    // 1024-byte alignment of the shared-window address (the 128-byte swizzle repeats every 1 KB)
+    // 1024-byte alignment of the shared-window address (swizzle atoms must start on their own size)
     const uint32_t raw_base = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + (((raw_base + 1023u) & ~1023u) - raw_base);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE);
