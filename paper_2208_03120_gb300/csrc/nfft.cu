@@ -16,6 +16,8 @@
 #include "fft_smem.cuh"
 #include "window.cuh"
 
+constexpr int kMaxDevices = 64;   // per-device one-time set-up tables
+
 namespace {
 
 template <int D>
@@ -1319,9 +1321,17 @@ size_t fftconv_smem(int d, int n) {
 }
 
 cudaError_t prepare_fftconv(int d, int n) {
-    static int c1 = 0, c2 = 0, c3a = 0, c3b = 0, s1 = 0, s2 = 0, s3 = 0, g1 = 0, g2 = 0, g3 = 0;
+    // limits raised so far, per device (kernel attributes belong to the current device)
+    static std::mutex mu;
+    static int lim[kMaxDevices][10] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    int &c1 = lim[dev][0], &c2 = lim[dev][1], &c3a = lim[dev][2], &c3b = lim[dev][3], &s1 = lim[dev][4],
+        &s2 = lim[dev][5], &s3 = lim[dev][6], &g1 = lim[dev][7], &g2 = lim[dev][8], &g3 = lim[dev][9];
     size_t sm = fftconv_smem(d, n);
-    cudaError_t e = cudaSuccess;
     // padded tiles of the spread / gather kernels (3-D: 25^3 floats)
     const size_t ss = (size_t)spread_smem_bytes(d, n), gs = (size_t)gather_smem_bytes(d, n);
     if (d == 1) e = ensure_smem(k_spread<1>, ss, &s1);
@@ -1364,18 +1374,28 @@ cudaError_t launch_fftconv(int d, const Task* tasks, int ntask, const Globals& G
 
 // ---- fused 2-D path -------------------------------------------------------------------------
 namespace {
-int g_cluster_size = 0;
+// cluster size of the fused kernel per device: 0 not yet probed, -1 no cluster fits
+int g_cluster_size[kMaxDevices] = {};
+
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+    return dev;
+}
 }
 
-int fused2d_cluster_size() { return g_cluster_size; }
+int fused2d_cluster_size() { return g_cluster_size[current_device()]; }
 
-bool fused2d_supported(int d, int n) { return d == 2 && n >= 16 && n <= F2_N && g_cluster_size > 0; }
+bool fused2d_supported(int d, int n) {
+    return d == 2 && n >= 16 && n <= F2_N && g_cluster_size[current_device()] > 0;
+}
 int fused2d_max_points() { return F2_MAXPTS; }
 
 cudaError_t prepare_fused2d() {
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
-    if (g_cluster_size != 0) return cudaSuccess;
+    int& csz = g_cluster_size[current_device()];
+    if (csz != 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     for (auto fn : {k_fastsum2d<false>, k_fastsum2d<true>}) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -1398,18 +1418,18 @@ cudaError_t prepare_fused2d() {
         int nclusters = 0;
         e = cudaOccupancyMaxActiveClusters(&nclusters, k_fastsum2d<false>, &cfg);
         if (e == cudaSuccess && nclusters > 0) {
-            g_cluster_size = cs;
+            csz = cs;
             return cudaSuccess;
         }
         cudaGetLastError();
     }
-    g_cluster_size = -1;
+    csz = -1;
     return cudaSuccess;
 }
 
 cudaError_t launch_fused2d(const Task* tasks, int ntask, const Globals& G, cudaStream_t st, bool msg_only) {
     if (ntask <= 0) return cudaSuccess;
-    const int cs = g_cluster_size;
+    const int cs = g_cluster_size[current_device()];
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, ntask, 1);
     cfg.blockDim = dim3(F2_THREADS, 1, 1);

@@ -448,18 +448,19 @@ int tc_ld(int k) { return (k + 7) & ~7; }
 
 cudaError_t prepare_tc_gemm() {
     static std::mutex mu;
-    static int done_dev = -1;
+    static bool done[64] = {};                  // per device: kernel attributes are per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
-    if (done_dev == dev) return cudaSuccess;
+    if (done[dev]) return cudaSuccess;
     e = set_smem<256>();
     if (e == cudaSuccess) e = set_smem<224>();
     if (e == cudaSuccess) e = set_smem<192>();
     if (e == cudaSuccess) e = set_smem<160>();
     if (e == cudaSuccess) e = set_smem<128>();
-    if (e == cudaSuccess) done_dev = dev;
+    if (e == cudaSuccess) done[dev] = true;
     return e;
 }
 
