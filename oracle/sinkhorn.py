@@ -12,6 +12,8 @@ Paper passages followed:
     Eq. comp_wise_multi_beta_tree) and Algorithm 2.
   * Section 4.2: circle; Theorems 4.2 / 4.3, the alpha / lambda matrix
     recursions and Algorithm 3.
+  * Section 6.3 (generalised Euler flows): the circle whose closing edge
+    {K, 1} compares x^K with sigma(x^1), and the pair marginals Pi_{1,k}.
 
 Conventions: node labels are 0-based (the paper's node 1 is label 0).  A
 problem's edge list may use any labels; :func:`tree_structure` relabels by
@@ -292,18 +294,24 @@ class CircleSinkhorn:
 
     Edges {k, k+1} for k = 1..K with K+1 = 1 (0-based: {k, (k+1) mod K}).
     ``edge_w[k]`` weights edge {k, k+1}; a zero weight makes that kernel the
-    all-ones matrix.
+    all-ones matrix.  ``x_close`` (Section 6.3) replaces the points of node 1
+    on the closing edge {K, 1} only: its kernel becomes
+    exp(-w ||x^K_i - x_close_j||^2 / eta), x_close = sigma(x^1) for a
+    connection map sigma.
     """
 
-    def __init__(self, x: Sequence[np.ndarray], mu: Sequence[np.ndarray], eta: float, edge_w=None):
+    def __init__(self, x: Sequence[np.ndarray], mu: Sequence[np.ndarray], eta: float, edge_w=None,
+                 x_close=None):
         self.K = len(x)
         self.eta = float(eta)
         self.x = [np.asarray(a, dtype=np.float64) for a in x]
         self.mu = [np.asarray(m, dtype=np.float64) for m in mu]
         self.n = [a.shape[0] for a in self.x]
         w = [1.0] * self.K if edge_w is None else [float(v) for v in edge_w]
+        closing = self.x[0] if x_close is None else np.asarray(x_close, dtype=np.float64).reshape(self.x[0].shape)
         # Kn[k] = K^{(k, k+1)} in ℝ^{n_k x n_{k+1}}
-        self.Kn = [EdgeKernel(self.x[k], self.x[(k + 1) % self.K], eta, w[k]).dense() for k in range(self.K)]
+        self.Kn = [EdgeKernel(self.x[k], closing if k == self.K - 1 else self.x[k + 1], eta, w[k]).dense()
+                   for k in range(self.K)]
 
     def compute_betas(self, phi):
         """beta_K = K^{(K,1)}; beta_k = K^{(k,k+1)} (phi^{k+1} (.) beta_{k+1}), k = K-1..2 (steps 3-5)."""
@@ -344,10 +352,10 @@ class CircleSinkhorn:
         return SolveResult(phi, S_trace, r)
 
 
-def circle_marginals(x, phi, eta, edge_w=None) -> List[np.ndarray]:
+def circle_marginals(x, phi, eta, edge_w=None, x_close=None) -> List[np.ndarray]:
     """Theorem 4.3: P_1 = phi^1 (.) <K^{(1,2)}, (phi^2 (.) alpha^{(2,1)})^T>,
     P_k = phi^k (.) <alpha^{(k,1)}, (phi^1 (.) lambda^{(1,k)})^T> for k >= 2."""
-    cs = CircleSinkhorn(x, [np.ones(len(a)) for a in x], eta, edge_w)
+    cs = CircleSinkhorn(x, [np.ones(len(a)) for a in x], eta, edge_w, x_close)
     K = cs.K
     ph = [np.asarray(p, dtype=np.float64) for p in phi]
     alpha = cs.compute_betas(ph)                 # alpha^{(k,1)} for k = 2..K
@@ -358,6 +366,29 @@ def circle_marginals(x, phi, eta, edge_w=None) -> List[np.ndarray]:
         lam = cs.Kn[0] if k == 1 else lam @ (ph[k - 1][:, None] * cs.Kn[k - 1])
         P[k] = ph[k] * _row_dot(alpha[k], (ph[0][:, None] * lam).T)
     return P
+
+
+def circle_pair_marginals(x, phi, eta, edge_w=None, x_close=None) -> List[Optional[np.ndarray]]:
+    """Pair marginals Pi_{1,k} of K (.) Phi for a circle (Section 6.3), k = 2..K.
+
+    Summing the plan over every index but i_1 and i_k splits the circle at
+    nodes 1 and k into the chain 1 -> 2 -> ... -> k, whose summed kernel is
+    lambda^{(1,k)} (Theorem 4.3's matrix, phi^2..phi^{k-1} inside), and the
+    chain k -> k+1 -> ... -> K -> 1, whose summed kernel is alpha^{(k,1)}
+    (phi^{k+1}..phi^K inside).  So
+    Pi_{1,k}[i_1, i_k] = phi^1_{i_1} lambda^{(1,k)}[i_1, i_k] alpha^{(k,1)}[i_k, i_1] phi^k_{i_k}.
+    Returns a list of K entries: [0] is None, [k] has shape (n_1, n_k).
+    """
+    cs = CircleSinkhorn(x, [np.ones(len(a)) for a in x], eta, edge_w, x_close)
+    K = cs.K
+    ph = [np.asarray(p, dtype=np.float64) for p in phi]
+    alpha = cs.compute_betas(ph)
+    out: List[Optional[np.ndarray]] = [None] * K
+    lam = None
+    for k in range(1, K):
+        lam = cs.Kn[0] if k == 1 else lam @ (ph[k - 1][:, None] * cs.Kn[k - 1])
+        out[k] = ph[0][:, None] * lam * alpha[k].T * ph[k][None, :]
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -409,11 +440,13 @@ def gauge_fix(u: Sequence[np.ndarray], mu: Sequence[np.ndarray]) -> List[np.ndar
 # brute force over the full N^K tensor (tiny cases)
 # ---------------------------------------------------------------------------
 
-def full_kernel_tensor(x, graph_edges, eta, edge_w=None) -> np.ndarray:
+def full_kernel_tensor(x, graph_edges, eta, edge_w=None, x_close=None) -> np.ndarray:
     """Eq. (cost_sparse) / Eq. (K-sparse): K_i = exp(-sum_{edges} w_e ||x^{k1}_{i_k1} - x^{k2}_{i_k2}||^2 / eta).
 
     Built directly from the cost tensor C (not from the factorisation), as
-    the independent reference for the message-passing recursions.
+    the independent reference for the message-passing recursions.  With
+    ``x_close`` the edge (K, 1) compares x^K with x_close in place of x^1:
+    the generalised Euler-flow cost of Section 6.3 with x_close = sigma(x^1).
     """
     K = len(x)
     xs = [np.asarray(a, dtype=np.float64).reshape(len(a), -1) for a in x]
@@ -421,7 +454,10 @@ def full_kernel_tensor(x, graph_edges, eta, edge_w=None) -> np.ndarray:
     C = np.zeros(shape)
     for e, (a, b) in enumerate(graph_edges):
         w = 1.0 if edge_w is None else float(edge_w[e])
-        diff = xs[a][:, None, :] - xs[b][None, :, :]
+        xa, xb = xs[a], xs[b]
+        if x_close is not None and (a, b) == (K - 1, 0):
+            xb = np.asarray(x_close, dtype=np.float64).reshape(xb.shape)
+        diff = xa[:, None, :] - xb[None, :, :]
         D2 = (diff * diff).sum(axis=-1)
         sh = [1] * K
         sh[a] = shape[a]
@@ -448,6 +484,11 @@ def tensor_marginals(Pi: np.ndarray) -> List[np.ndarray]:
     """Eq. (Pk): P_k(Pi) = sum over all indices but i_k."""
     K = Pi.ndim
     return [Pi.sum(axis=tuple(a for a in range(K) if a != k)) for k in range(K)]
+
+
+def tensor_pair_marginal(Pi: np.ndarray, a: int, b: int) -> np.ndarray:
+    """Pi_{a,b}: the sum of Pi over all indices but i_a and i_b (a < b), shape (n_a, n_b)."""
+    return Pi.sum(axis=tuple(t for t in range(Pi.ndim) if t not in (a, b)))
 
 
 def sinkhorn_bruteforce(Kt: np.ndarray, mu, iters: int, phi0=None):

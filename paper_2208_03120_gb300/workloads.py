@@ -23,6 +23,10 @@ Workloads (seed = 2208031200 + workload index):
   (barycenter-like tree of Section 6.2).
 * ``circle5_d1`` -- circle of K=5 marginals, d=1, N=2,000 uniform in
   [-0.24, 0.24], weights U(0,1) normalised, eta=0.05 (Section 6.1 circle).
+* ``euler5_d1``  -- generalised Euler flow (Section 6.3): circle of K=5
+  marginals, d=1, N=400 points uniform on [0, 1] per time step, uniform
+  weights, eta=0.05, closing edge against sigma(x^1) with the connection map
+  sigma(x) = 1 - x or sigma(x) = min(2x, 2 - 2x).
 * ``serving``    -- a Poisson-arrival stream of solve requests mixing the
   three topologies (see :func:`serving_stream`).
 """
@@ -55,6 +59,8 @@ class Problem:
     edge_w: Optional[np.ndarray] = None  # per-edge cost weights (None = 1)
     root: int = 0
     iters: int = 0                     # suggested iteration count (0 = to tolerance)
+    x_close: Optional[np.ndarray] = None  # circle: sigma(x^1), float32 (n_1, d), used by the
+                                          # closing edge {K, 1} in place of x^1 (Section 6.3)
 
     @property
     def n(self) -> List[int]:
@@ -62,6 +68,9 @@ class Problem:
 
     def x64(self) -> List[np.ndarray]:
         return [a.astype(np.float64) for a in self.x]
+
+    def x_close64(self) -> Optional[np.ndarray]:
+        return None if self.x_close is None else self.x_close.astype(np.float64)
 
 
 def _rng(index: int, seed: Optional[int] = None) -> np.random.Generator:
@@ -131,6 +140,23 @@ def circle5_d1(n: int = 2_000, K: int = 5, seed: Optional[int] = None) -> Proble
     x = [rng.uniform(-0.24, 0.24, size=(n, d)).astype(np.float32) for _ in range(K)]
     mu = [_normalised(rng.uniform(0.0, 1.0, size=n)) for _ in range(K)]
     return Problem("circle5_d1", CIRCLE, K, d, x, mu, 0.05, None)
+
+
+# Connection maps of Section 6.3 (the problem's input, applied to the initial positions).
+# "fold" reads the printed min(2x, 1 - 2x), which leaves [0, 1], as the tent map min(2x, 2 - 2x).
+CONNECTION_MAPS = {
+    "reflect": lambda x: 1.0 - x,
+    "fold": lambda x: np.minimum(2.0 * x, 2.0 - 2.0 * x),
+}
+
+
+def euler5_d1(n: int = 400, K: int = 5, sigma: str = "reflect", seed: Optional[int] = None) -> Problem:
+    rng = _rng(4, seed)
+    d = 1
+    x = [rng.uniform(0.0, 1.0, size=(n, d)).astype(np.float32) for _ in range(K)]
+    mu = [np.full(n, 1.0 / n) for _ in range(K)]
+    x_close = CONNECTION_MAPS[sigma](x[0].astype(np.float64)).astype(np.float32)
+    return Problem(f"euler5_d1_{sigma}", CIRCLE, K, d, x, mu, 0.05, None, x_close=x_close)
 
 
 def random_tree_edges(rng: np.random.Generator, K: int) -> np.ndarray:

@@ -284,3 +284,88 @@ def test_free_root_sibling_updates_do_not_converge():
     assert np.max(np.abs(np.log(tail))) > 1e-3          # mass stays away from 1
     assert np.allclose(tail[::2], tail[0], rtol=1e-9) and np.allclose(tail[1::2], tail[1], rtol=1e-9)
     assert abs(np.log(tail[0]) + np.log(tail[1])) < 1e-6  # period 2: c and 1/c
+
+
+# ---------------------------------------------------------------------------
+# generalised Euler flows (Section 6.3): closing edge against sigma(x^1), pair marginals
+# ---------------------------------------------------------------------------
+
+def _euler_problem(rng, K, n, sigma="fold"):
+    x = [rng.uniform(0.0, 1.0, size=(m, 1)).astype(np.float32) for m in n]
+    mu = [np.full(m, 1.0 / m) for m in n]
+    x_close = W.CONNECTION_MAPS[sigma](x[0].astype(np.float64)).astype(np.float32)
+    return W.Problem("euler-test", W.CIRCLE, K, 1, x, mu, 0.3, None, x_close=x_close)
+
+
+def _euler_tensor_by_loops(prob):
+    """The Section 6.3 cost C_i = |x^K_{i_K} - sigma(x^1_{i_1})|^2 + sum_k |x^{k+1}_{i_{k+1}} - x^k_{i_k}|^2,
+    entry by entry, and K = exp(-C / eta)."""
+    import itertools
+    xs = [a[:, 0].astype(np.float64) for a in prob.x]
+    xc = prob.x_close[:, 0].astype(np.float64)
+    Kt = np.empty(tuple(prob.n))
+    for idx in itertools.product(*[range(m) for m in prob.n]):
+        c = (xs[-1][idx[-1]] - xc[idx[0]]) ** 2
+        for k in range(prob.K - 1):
+            c += (xs[k + 1][idx[k + 1]] - xs[k][idx[k]]) ** 2
+        Kt[idx] = math.exp(-c / prob.eta)
+    return Kt
+
+
+@pytest.mark.parametrize("sigma", ["fold", "reflect"])
+def test_euler_circle_marginals_and_pairs_match_bruteforce(sigma):
+    """Section 6.3: with the closing edge measured against sigma(x^1), the circle's matrix
+    recursions (Theorem 4.3) still give the marginals of the full tensor, and
+    phi^1 lambda^{(1,k)} alpha^{(k,1)} phi^k gives its pair marginals Pi_{1,k}, for
+    arbitrary positive phi; the tensor is built entry by entry from the printed cost."""
+    rng = np.random.default_rng(41)
+    prob = _euler_problem(rng, 4, [3, 4, 2, 3], sigma)
+    phi = _rand_phi(rng, prob.n)
+    Kt = _euler_tensor_by_loops(prob)
+    np.testing.assert_allclose(OS.full_kernel_tensor(prob.x64(), _circle_graph_edges(4), prob.eta,
+                                                     x_close=prob.x_close64()), Kt, rtol=1e-13)
+    Pi = OS.plan_tensor(Kt, phi)
+    P_mp = OS.circle_marginals(prob.x64(), phi, prob.eta, x_close=prob.x_close64())
+    for a, b in zip(P_mp, OS.tensor_marginals(Pi)):
+        np.testing.assert_allclose(a, b, rtol=1e-12)
+    pairs = OS.circle_pair_marginals(prob.x64(), phi, prob.eta, x_close=prob.x_close64())
+    assert pairs[0] is None
+    for k in range(1, 4):
+        np.testing.assert_allclose(pairs[k], OS.tensor_pair_marginal(Pi, 0, k), rtol=1e-12)
+        np.testing.assert_allclose(pairs[k].sum(axis=1), P_mp[0], rtol=1e-12)
+        np.testing.assert_allclose(pairs[k].sum(axis=0), P_mp[k], rtol=1e-12)
+
+
+def test_euler_circle_algorithm3_equals_algorithm1():
+    """Algorithm 3 with the sigma-closing edge is the Gauss-Seidel sweep of Algorithm 1 on
+    the Section 6.3 cost tensor: the iterates agree sweep by sweep."""
+    rng = np.random.default_rng(42)
+    prob = _euler_problem(rng, 4, [4, 3, 5, 4])
+    cs = OS.CircleSinkhorn(prob.x64(), prob.mu, prob.eta, x_close=prob.x_close64())
+    hist = []
+    cs.run(6, callback=lambda r, phi: hist.append([p.copy() for p in phi]))
+    bf = OS.sinkhorn_bruteforce(_euler_tensor_by_loops(prob), prob.mu, 6)
+    for a, b in zip(hist, bf):
+        for pa, pb in zip(a, b):
+            np.testing.assert_allclose(pa, pb, rtol=1e-11)
+
+
+def test_euler_identity_map_is_plain_circle():
+    """sigma = identity gives back the plain circle of Algorithm 3."""
+    rng = np.random.default_rng(43)
+    prob = W.random_problem(rng, W.CIRCLE, 4, 2, [5, 4, 6, 3], eta=0.15)
+    ra = OS.CircleSinkhorn(prob.x64(), prob.mu, prob.eta).run(5)
+    rb = OS.CircleSinkhorn(prob.x64(), prob.mu, prob.eta, x_close=prob.x64()[0]).run(5)
+    for a, b in zip(ra.phi, rb.phi):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_euler_pair_marginals_at_convergence_carry_the_measures():
+    """At the Sinkhorn fixed point of the Section 6.3 problem every pair marginal Pi_{1,k} is
+    a coupling of mu^1 and mu^k (row sums mu^1, column sums mu^k)."""
+    prob = W.euler5_d1(n=40)
+    res = OS.CircleSinkhorn(prob.x64(), prob.mu, prob.eta, x_close=prob.x_close64()).run(400)
+    pairs = OS.circle_pair_marginals(prob.x64(), res.phi, prob.eta, x_close=prob.x_close64())
+    for k in range(1, prob.K):
+        np.testing.assert_allclose(pairs[k].sum(axis=1), prob.mu[0], atol=1e-8)
+        np.testing.assert_allclose(pairs[k].sum(axis=0), prob.mu[k], atol=1e-8)
