@@ -30,7 +30,7 @@
 extern "C" {
 #endif
 
-#define MOT_ABI_VERSION 2
+#define MOT_ABI_VERSION 3
 
 /* ---- status codes ---------------------------------------------------------------- */
 #define MOT_OK           0
@@ -88,6 +88,13 @@ typedef struct {
                                        MOT_ROOT_CENTRE: a centre of the tree (least
                                        eccentricity, smallest label on ties), which gives
                                        the backward pass the fewest sequential levels         */
+    const float* x_close;           /* MOT_CIRCLE only, device [n_1][d] or NULL: the points that
+                                       the closing edge {K, 1} compares x^K with, in place of
+                                       x^1 -- sigma(x^1) for the connection map sigma of the
+                                       generalised Euler flow (Section 6.3).  The edge's kernel
+                                       is exp(-w ||x^K_i - x_close_j||^2 / eta); every other
+                                       use of node 1 keeps x^1.  Non-NULL for a tree:
+                                       MOT_EINVAL                                             */
 } mot_problem;
 
 /* ---- options (zero-initialised fields take the defaults in brackets) ------------- */
@@ -130,6 +137,12 @@ typedef struct {
     int n_grid, M;          /* grid length per dimension and Fourier half-degree used          */
     double kernel_ms[MOT_NKCLASS];        /* with options.timing: device ms per kernel class   */
     long long kernel_launches[MOT_NKCLASS];
+    double* const* pair;    /* in: MOT_CIRCLE only, host [K] of device pointers or NULL (entry 0
+                               is ignored and entries may be NULL).  out: pair[k] (k = 1..K-1)
+                               = the pair marginal Pi_{1,k+1} of K (.) Phi at the returned
+                               scalings (Section 6.3), FP64 row-major [n_1][n_{k+1}] in the
+                               caller's point order; row sums are P_1, column sums P_{k+1}.
+                               Non-NULL for a tree: MOT_EINVAL                                */
 } mot_result;
 
 /* ---- entry points ---------------------------------------------------------------- */

@@ -101,7 +101,58 @@ __global__ void k_kernel_matrix(const float* __restrict__ ui, int ni, const floa
     }
 }
 
+// Closing-edge points of the generalised Euler flow (Section 6.3): x_close (caller order,
+// [n][d]) in node 1's sorted order and in grid units, u[t][j] = (x_close[perm[j]][t] - c_t) n / s
+// + n/2.  Not wrapped onto the torus: the closing kernel matrix is formed directly.
+__global__ void k_close_points(const float* __restrict__ x, const int* __restrict__ perm, int n, int d, double c0,
+                               double c1, double c2, double inv_s, int n_grid, float* u, int* err) {
+    const double c[3] = {c0, c1, c2};
+    const double half = 0.5 * n_grid;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const size_t src = (size_t)perm[j] * d;
+        for (int t = 0; t < d; ++t) {
+            const float xf = x[src + t];
+            if (!isfinite(xf)) atomicOr(err, 1);
+            u[(size_t)t * n + j] = (float)(((double)xf - c[t]) * inv_s * n_grid + half);
+        }
+    }
+}
+
+// Pair marginal of a circle (Section 6.3): Pi[c][i] = phi^1_c Gam_k[c][i] beta_k[c][i] phi^k_i with
+// every factor at its true scale (mantissa x exp(ls)), FP64, written row-major [n1][nk] in the
+// caller's point order.  Gam_k and beta_k are column-major [c][i] in the sorted orders.
+__global__ void k_pair(const float* __restrict__ phi1, const VecScale* s1, const int* __restrict__ perm1, int n1,
+                       const float* __restrict__ phik, const VecScale* sk, const int* __restrict__ permk, int nk,
+                       const float* __restrict__ G, const VecScale* sG, const float* __restrict__ B,
+                       const VecScale* sB, double* out) {
+    const double L = ls_of(s1, 0) + ls_of(sk, 0) + ls_of(sG, 0) + ls_of(sB, 0);
+    const long long total = (long long)n1 * nk;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(idx / nk), i = (int)(idx - (long long)c * nk);
+        const double p = (double)phi1[c] * (double)phik[i] * (double)G[idx] * (double)B[idx];
+        out[(size_t)perm1[c] * nk + permk[i]] = p > 0.0 ? exp(log(p) + L) : 0.0;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_close_points(const float* x, const int* perm, int n, int d, const double* c, double s, int n_grid,
+                                float* u, int* err, cudaStream_t st) {
+    const int blocks = std::max(1, std::min((n + 255) / 256, 1024));
+    k_close_points<<<blocks, 256, 0, st>>>(x, perm, n, d, c[0], d > 1 ? c[1] : 0.0, d > 2 ? c[2] : 0.0, 1.0 / s,
+                                           n_grid, u, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair(const float* phi1, const VecScale* s1, const int* perm1, int n1, const float* phik,
+                        const VecScale* sk, const int* permk, int nk, const float* G, const VecScale* sG,
+                        const float* B, const VecScale* sB, double* out, cudaStream_t st) {
+    const long long total = (long long)n1 * nk;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 4 * 152 * 8));
+    k_pair<<<blocks, 256, 0, st>>>(phi1, s1, perm1, n1, phik, sk, permk, nk, G, sG, B, sB, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_rowdot(const float* B, const VecScale* sB, const float* G, const VecScale* sG, const float* phi,
                           const VecScale* sP, int ni, int nc, float* raw, cudaStream_t st) {

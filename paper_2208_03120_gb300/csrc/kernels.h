@@ -115,6 +115,14 @@ cudaError_t launch_colsum(const float* A, const VecScale* sA, const float* B, co
 // K[c][i] = exp(-||u_i - u_c||^2 / eta_u) (column-major, grid units); scale record ls = 0, mx = 1.
 cudaError_t launch_kernel_matrix(const float* ui, int ni, const float* uc, int nc, int d, float eta_u, float* K,
                                  VecScale* sc, cudaStream_t st);
+// Generalised Euler flow (Section 6.3): the closing edge's node-1 points sigma(x^1), sorted like
+// node 1 and in grid units (not wrapped); non-finite input sets bit 0 of *err.
+cudaError_t launch_close_points(const float* x, const int* perm, int n, int d, const double* c, double s, int n_grid,
+                                float* u, int* err, cudaStream_t st);
+// Pair marginal Pi_{1,k}[perm1[c]][permk[i]] = phi^1_c Gam_k[c][i] beta_k[c][i] phi^k_i (FP64).
+cudaError_t launch_pair(const float* phi1, const VecScale* s1, const int* perm1, int n1, const float* phik,
+                        const VecScale* sk, const int* permk, int nk, const float* G, const VecScale* sG,
+                        const float* B, const VecScale* sB, double* out, cudaStream_t st);
 
 // ---- dense products on the tensor cores, BF16 hi + lo split (tc_gemm.cu) ------------------
 // Y[c][i] = sum_j A[c][j] B[i][j] with A = Ahi + Alo (M x K), B = Bhi + Blo (N x K), BF16,

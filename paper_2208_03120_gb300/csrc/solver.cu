@@ -318,7 +318,7 @@ int validate_problem(const mot_problem* P) {
     }
     if (P->topology != MOT_TREE && P->topology != MOT_CIRCLE) return MOT_EINVAL;
     if (P->topology == MOT_TREE) {
-        if (!P->edges) return MOT_EINVAL;
+        if (!P->edges || P->x_close) return MOT_EINVAL;
         if (P->root < MOT_ROOT_CENTRE || P->root >= P->K) return MOT_EINVAL;
     }
     int ne = P->topology == MOT_TREE ? P->K - 1 : P->K;
@@ -1073,6 +1073,8 @@ struct CirclePlan {
     std::vector<float*> c1_w;       // per node: window taps [n_k][10]
     std::vector<float*> c1_c;       // per edge: circulant of D (n floats)
     float* c1_G = nullptr;          // n0 x n spread grids of one batch
+    bool has_close = false;         // closing edge against sigma(x^0) (Section 6.3)
+    float* u_close = nullptr;       // [d][n0] sigma(x^0) in node 0's sorted order, grid units
     uint16_t* a_hi = nullptr;       // tensor-core path: split source matrix, n0 x ld (BF16 pairs)
     uint16_t* a_lo = nullptr;
     std::vector<uint16_t*> ktf_hi, ktf_lo, ktb_hi, ktb_lo;   // split kernel matrices per batch
@@ -1167,6 +1169,7 @@ void layout_circle(Arena& A, CirclePlan& C) {
         C.err = reinterpret_cast<int*>(C.stats_begin + stats - 16);
         C.iter = C.err + 1;
     }
+    if (C.has_close) C.u_close = A.take<float>((size_t)d * C.n0);
     C.d_sets = A.take<PrepSet>(K);
     C.box_scratch = A.take<float>(8);
     C.box_out = A.take<float>(8);
@@ -1496,6 +1499,7 @@ int circle_setup(const mot_problem* P, const mot_options& o, CirclePlan& C, void
     C.n.resize(K);
     for (int k = 0; k < K; ++k) C.n[k] = (int)P->n[k];
     C.n0 = C.n[0];
+    C.has_close = P->x_close != nullptr;
     C.w.assign(K, 1.0);
     if (P->edge_w)
         for (int k = 0; k < K; ++k) C.w[k] = P->edge_w[k];
@@ -1534,6 +1538,7 @@ int circle_setup(const mot_problem* P, const mot_options& o, CirclePlan& C, void
     }
     CK(cudaMemcpyAsync(C.d_sets, s2.data(), sizeof(PrepSet) * s2.size(), cudaMemcpyHostToDevice, st));
     CK(launch_prep(C.d_sets, s2.data(), K, C.d, g.n, g.c, g.s, C.err, st));
+    if (C.has_close) CK(launch_close_points(P->x_close, C.sets[0].perm, C.n0, C.d, g.c, g.s, g.n, C.u_close, C.err, st));
     for (int k = 0; k < K; ++k) CK(cudaMemsetAsync(C.raw[k], 0, sizeof(float) * C.n[k], st));
     if (C.path == MOT_PATH_NFFT) {
         CK(prepare_window());
@@ -1560,7 +1565,8 @@ int circle_setup(const mot_problem* P, const mot_options& o, CirclePlan& C, void
         for (int k = 0; k < K; ++k) nmax = std::max(nmax, C.n[k]);
         for (int c = 0; c < C.CB; ++c) CK(cudaMemsetAsync(C.rawm[c], 0, sizeof(float) * nmax, st));
     }
-    // fixed dense kernel matrices: beta_{K-1} = K^{(K-1,0)}, Gam_1 = K^{(1,0)}
+    // fixed dense kernel matrices: beta_{K-1} = K^{(K-1,0)} (against sigma(x^0) for an Euler flow,
+    // Section 6.3), Gam_1 = K^{(1,0)}
     auto eta_u = [&](int edge) { return (float)((C.eta / C.w[edge]) / (g.s * g.s) * (double)g.n * (double)g.n); };
     if (C.path == MOT_PATH_DENSE_BF16X3) {
         // split kernel matrices of the batched products (fixed for the solve)
@@ -1572,8 +1578,8 @@ int circle_setup(const mot_problem* P, const mot_options& o, CirclePlan& C, void
             CK(launch_kernel_split(C.sets[k].u, C.n[k], C.sets[k + 1].u, C.n[k + 1], C.d, eta_u(k),
                                    tc_ld(C.n[k + 1]), C.ktb_hi[k], C.ktb_lo[k], st));
     }
-    CK(launch_kernel_matrix(C.sets[K - 1].u, C.n[K - 1], C.sets[0].u, C.n0, C.d, eta_u(K - 1), C.beta[K - 1],
-                            C.beta_sc(K - 1), st));
+    CK(launch_kernel_matrix(C.sets[K - 1].u, C.n[K - 1], C.has_close ? C.u_close : C.sets[0].u, C.n0, C.d,
+                            eta_u(K - 1), C.beta[K - 1], C.beta_sc(K - 1), st));
     CK(launch_kernel_matrix(C.sets[1].u, C.n[1], C.sets[0].u, C.n0, C.d, eta_u(0), C.gam[1], C.gam_sc(1), st));
     c_build(C);
     if (C.path == MOT_PATH_DENSE_BF16X3) {
@@ -1606,7 +1612,7 @@ struct PlanOps {
     virtual int K() const = 0;
     virtual bool constrained(int k) const = 0;
     virtual double eta() const = 0;
-    virtual int output(double* const* u, cudaStream_t st, long long& nl) = 0;
+    virtual int output(double* const* u, double* const* pair, cudaStream_t st, long long& nl) = 0;
     virtual void geometry(mot_result* r) const = 0;
 };
 
@@ -1633,8 +1639,8 @@ struct TreeOps : PlanOps {
     int K() const override { return T.K; }
     bool constrained(int k) const override { return !T.free_[k]; }
     double eta() const override { return T.eta; }
-    int output(double* const* u, cudaStream_t st, long long& nl) override {
-        for (int k = 0; k < T.K; ++k) {
+    int output(double* const* u, double* const*, cudaStream_t st, long long& nl) override {
+        for (int k = 0; k < T.K && u; ++k) {
             if (!u[T.order[k]]) continue;
             CK(launch_output(T.phi[k], T.phi_sc(k), T.sets[k].perm, T.n[k], T.eta, u[T.order[k]], st));
             nl += 1;
@@ -1678,10 +1684,18 @@ struct CircleOps : PlanOps {
     int K() const override { return C.K; }
     bool constrained(int) const override { return true; }
     double eta() const override { return C.eta; }
-    int output(double* const* u, cudaStream_t st, long long& nl) override {
-        for (int k = 0; k < C.K; ++k) {
+    int output(double* const* u, double* const* pair, cudaStream_t st, long long& nl) override {
+        for (int k = 0; k < C.K && u; ++k) {
             if (!u[k]) continue;
             CK(launch_output(C.phi[k], C.phi_sc(k), C.sets[k].perm, C.n[k], C.eta, u[k], st));
+            nl += 1;
+        }
+        // pair marginals Pi_{0,k} (Section 6.3): after a full sweep and the check pass, Gam_k and
+        // beta_k are the chains 0 -> k and k -> 0 at the returned scalings
+        for (int k = 1; k < C.K && pair; ++k) {
+            if (!pair[k]) continue;
+            CK(launch_pair(C.phi[0], C.phi_sc(0), C.sets[0].perm, C.n0, C.phi[k], C.phi_sc(k), C.sets[k].perm,
+                           C.n[k], C.gam[k], C.gam_sc(k), C.beta[k], C.beta_sc(k), pair[k], st));
             nl += 1;
         }
         return MOT_OK;
@@ -1774,12 +1788,12 @@ struct Solve {
         return MOT_OK;
     }
     // fill the scalar results and enqueue u^k
-    int finish(mot_result* res, double* const* u) {
+    int finish(mot_result* res, double* const* u, double* const* pair) {
         const int K = ops->K();
         const IterAcc* acc = reinterpret_cast<const IterAcc*>(hstats);
         const double* node = reinterpret_cast<const double*>(hstats + sizeof(IterAcc) * kRing);
         const VecScale* scs = reinterpret_cast<const VecScale*>(hstats + sizeof(IterAcc) * kRing + sizeof(double) * 3 * K);
-        if (u) RET(ops->output(u, st, nl));
+        if (u || pair) RET(ops->output(u, pair, st, nl));
         if (res) {
             double mass = node[2], plogphi = 0.0;
             for (int k = 0; k < K; ++k) plogphi += node[3 * k + 1];
@@ -1824,7 +1838,7 @@ int solve_blocking(const mot_problem* P, const mot_options& o, void* ws, size_t 
         }
         rc = S.evaluate(res);
     }
-    if (rc == MOT_OK) rc = S.finish(res, res ? res->u : nullptr);
+    if (rc == MOT_OK) rc = S.finish(res, res ? res->u : nullptr, res ? res->pair : nullptr);
     if (rc == MOT_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = MOT_ECUDA;
     if (S.ev) cudaEventDestroy(S.ev);
     delete S.ops;
@@ -2186,10 +2200,13 @@ int mot_solve(const mot_problem* prob, const mot_options* opt, void* ws, size_t 
     if (o.m != 4) return MOT_EUNSUPPORTED;
     if (!ws) return MOT_EINVAL;
     if (reinterpret_cast<uintptr_t>(ws) & 255) return MOT_EINVAL;
+    if (res && res->pair && prob->topology != MOT_CIRCLE) return MOT_EINVAL;
     if (res) {
         double* const* u = res->u;
+        double* const* pair = res->pair;
         std::memset(res, 0, sizeof(*res));
         *const_cast<double* const**>(&res->u) = u;
+        *const_cast<double* const**>(&res->pair) = pair;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     // The legacy default stream cannot be captured into a graph: run on a private stream
@@ -2319,7 +2336,7 @@ int mot_server_progress(mot_server S, int* n_active, int* n_pending) {
             if (rc == MOT_OK && !a->solve.done) {
                 rc = a->solve.launch();
             } else if (rc == MOT_OK) {
-                rc = a->solve.finish(&a->res, a->req.u.empty() ? nullptr : a->req.u.data());
+                rc = a->solve.finish(&a->res, a->req.u.empty() ? nullptr : a->req.u.data(), nullptr);
                 if (rc == MOT_OK && cudaEventRecord(a->solve.ev, a->solve.st) != cudaSuccess) rc = MOT_ECUDA;
                 a->finishing = true;
             }

@@ -39,6 +39,7 @@ class Problem(C.Structure):
         ("free_nodes", C.POINTER(C.c_ubyte)),
         ("eta", C.c_double),
         ("root", C.c_int),
+        ("x_close", C.c_void_p),
     ]
 
 
@@ -72,6 +73,7 @@ class Result(C.Structure):
         ("n_grid", C.c_int), ("M", C.c_int),
         ("kernel_ms", C.c_double * MOT_NKCLASS),
         ("kernel_launches", C.c_longlong * MOT_NKCLASS),
+        ("pair", C.POINTER(C.c_void_p)),
     ]
 
 
@@ -227,7 +229,7 @@ class _ProblemHolder:
     """Keeps the ctypes arrays referenced by a Problem alive."""
 
     def __init__(self, x: Sequence, mu: Sequence, eta: float, topology: int, edges=None, edge_w=None,
-                 free_nodes=None, root: int = 0):
+                 free_nodes=None, root: int = 0, x_close=None):
         import torch
         K = len(x)
         if len(mu) != K:
@@ -259,20 +261,27 @@ class _ProblemHolder:
             p.free_nodes = self.f_arr
         p.eta = float(eta)
         p.root = int(root)
+        if x_close is not None:
+            _check_tensor(x_close, torch.float32, "x_close")
+            if tuple(x_close.shape) != tuple(x[0].shape):
+                raise ValueError("x_close must have the shape of x[0]")
+            self.x_close = x_close
+            p.x_close = x_close.data_ptr()
         self.p = p
 
 
 def mot_workspace_bytes(x, mu, eta, topology=MOT_TREE, edges=None, edge_w=None, free_nodes=None, root=0,
-                        opt: Optional[Options] = None) -> int:
-    h = _ProblemHolder(x, mu, eta, topology, edges, edge_w, free_nodes, root)
+                        opt: Optional[Options] = None, x_close=None) -> int:
+    h = _ProblemHolder(x, mu, eta, topology, edges, edge_w, free_nodes, root, x_close)
     nb = C.c_size_t(0)
     _check(lib().mot_workspace_bytes(C.byref(h.p), C.byref(opt or options()), C.byref(nb)), "mot_workspace_bytes")
     return nb.value
 
 
 class SolveOutput:
-    def __init__(self, u: List, res: Result):
+    def __init__(self, u: List, res: Result, pair: Optional[List] = None):
         self.u = u
+        self.pair = pair
         self.violation = res.violation
         self.cost_dual = res.cost_dual
         self.cost_primal = res.cost_primal
@@ -293,11 +302,15 @@ class SolveOutput:
 
 def mot_solve(x, mu, eta, topology=MOT_TREE, edges=None, edge_w=None, free_nodes=None, root=0,
               opt: Optional[Options] = None, u_warm=None, workspace=None, stream=None, u_out=None,
-              allow_noconv: bool = True) -> SolveOutput:
-    """Sinkhorn for a tree (Algorithm 2) or circle (Algorithm 3); returns u^k = eta log phi^k (FP64)."""
+              allow_noconv: bool = True, x_close=None, pair: bool = False) -> SolveOutput:
+    """Sinkhorn for a tree (Algorithm 2) or circle (Algorithm 3); returns u^k = eta log phi^k (FP64).
+
+    Circle only: ``x_close`` = sigma(x^1) for the closing edge of a generalised Euler flow, and
+    ``pair=True`` also returns the pair marginals Pi_{1,k} (Section 6.3) as ``out.pair[k]``,
+    FP64 (n_1, n_k) tensors for k = 1..K-1 (``out.pair[0]`` is None)."""
     import torch
     opt = opt or options()
-    h = _ProblemHolder(x, mu, eta, topology, edges, edge_w, free_nodes, root)
+    h = _ProblemHolder(x, mu, eta, topology, edges, edge_w, free_nodes, root, x_close)
     dev = x[0].device
     if workspace is None:
         nb = C.c_size_t(0)
@@ -308,13 +321,19 @@ def mot_solve(x, mu, eta, topology=MOT_TREE, edges=None, edge_w=None, free_nodes
     u_arr = (C.c_void_p * K)(*[t.data_ptr() for t in u])
     res = Result()
     res.u = u_arr
+    pairs = None
+    if pair:
+        n0 = int(x[0].shape[0])
+        pairs = [None] + [torch.empty((n0, int(t.shape[0])), dtype=torch.float64, device=dev) for t in x[1:]]
+        pair_arr = (C.c_void_p * K)(None, *[t.data_ptr() for t in pairs[1:]])
+        res.pair = pair_arr
     warm = None
     if u_warm is not None:
         warm = (C.c_void_p * K)(*[t.data_ptr() for t in u_warm])
     allow = (MOT_OK, MOT_ENOCONV) if allow_noconv else (MOT_OK,)
     _check(lib().mot_solve(C.byref(h.p), C.byref(opt), workspace.data_ptr(), workspace.numel(), warm, C.byref(res),
                            _stream_ptr(stream)), "mot_solve", allow)
-    return SolveOutput(u, res)
+    return SolveOutput(u, res, pairs)
 
 
 # ----------------------------------------------------------------------------------------
@@ -335,9 +354,9 @@ class Server:
         self._keep = {}
 
     def submit(self, x, mu, eta, topology=MOT_TREE, edges=None, edge_w=None, free_nodes=None, root=0,
-               opt: Optional[Options] = None, u_out=None, tag: int = 0):
+               opt: Optional[Options] = None, u_out=None, tag: int = 0, x_close=None):
         import torch
-        holder = _ProblemHolder(x, mu, eta, topology, edges, edge_w, free_nodes, root)
+        holder = _ProblemHolder(x, mu, eta, topology, edges, edge_w, free_nodes, root, x_close)
         u = u_out if u_out is not None else [torch.empty(int(t.shape[0]), dtype=torch.float64, device=t.device)
                                              for t in x]
         u_arr = (C.c_void_p * len(u))(*[t.data_ptr() for t in u])

@@ -35,7 +35,7 @@ def test_header_declarations_exported(M):
 
 def test_abi_version_and_strerror(M):
     lib = M.lib()
-    assert lib.mot_abi_version() == 2
+    assert lib.mot_abi_version() == 3
     assert M.strerror(0) == "ok"
     assert "tree" in M.strerror(M.MOT_ENOTTREE)
     assert M.strerror(12345) == "unknown status"
@@ -132,6 +132,25 @@ def test_circle_workspace_query(M):
     assert st == M.MOT_OK and nb > 4 * 200 * 210 * 2        # beta and gamma matrices
     p2, k2 = _fake_problem(M, 2, 1, [20, 20], None, topology=1)
     assert _ws(M, p2)[0] == M.MOT_EUNSUPPORTED              # a circle needs K >= 3
+
+
+def test_euler_closing_points_validation(M):
+    """Section 6.3 closing points: accepted for a circle (the workspace grows by the sorted
+    copy, d x n_1 floats), rejected for a tree; pair-marginal outputs are circle-only and a
+    tree asking for them is rejected before any CUDA call."""
+    p, keep = _fake_problem(M, 5, 2, [200, 210, 220, 230, 240], None, topology=1)
+    st0, nb0 = _ws(M, p)
+    p.x_close = 0x7000
+    st1, nb1 = _ws(M, p)
+    assert st0 == st1 == M.MOT_OK and nb1 >= nb0 + 2 * 200 * 4
+    t, k2 = _fake_problem(M, 3, 1, [5] * 3, [(0, 1), (1, 2)])
+    t.x_close = 0x7000
+    assert _ws(M, t)[0] == M.MOT_EINVAL
+    t.x_close = None
+    res = M.Result()
+    pairs = (C.c_void_p * 3)(None, 0x8000, 0x8100)
+    res.pair = pairs
+    assert M.lib().mot_solve(C.byref(t), None, C.c_void_p(0x10000), 1 << 20, None, C.byref(res), None) == M.MOT_EINVAL
 
 
 def test_server_argument_validation(M):
