@@ -460,19 +460,16 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
 // Batched 1-D fast summation of the circle (Algorithm 3, N right-hand sides, d = 1).
 //
 // In one dimension the oversampled grid (n <= 128) is far smaller than the point sets, so a
-// batch Y[c] = K (phi (.) X[c]), c < n0, is three small dense steps per column:
+// batch Y[c] = K (phi (.) X[c]), c < n0, is three small dense steps per column, all done by one
+// CTA for C1_Q columns without leaving shared memory:
 //   spread : G[c] = sum_j X[c][j] phi_j psi(u_j - .)               (Algorithm 4 step 6)
 //   conv   : H[c] = C G[c], the circulant c(m) = sum_{q<=M} D_q cos(2 pi q m / n) of Eq.
 //            (fastsum_mat) (the real part of IFFT(D FFT(.)))        (steps 7 - 8, pruned)
 //   gather : Y[c][i] = sum_a H[c][l0_i + a] psi_a(u_i), then the message epilogue (step 9)
-// One thread-block cluster of C1_CS CTAs takes C1_Q columns: rank r spreads and gathers 1/C1_CS
-// of the points, the partial grids are summed through distributed shared memory, and rank r
-// convolves n / C1_CS cells.  Each column's message is read once and written once; no grid
-// leaves shared memory.  The window taps and base cells of every point are computed once per
-// solve (k_c1_taps).
+// Each column's message is read once and written once.  The window taps and base cells of every
+// point are computed once per solve (k_c1_taps).
 // ------------------------------------------------------------------------------------------
-constexpr int C1_Q = 8;          // columns per cluster
-constexpr int C1_CS = 8;         // CTAs per cluster
+constexpr int C1_Q = 8;          // columns per CTA
 constexpr int C1_CH = 256;       // source points staged per step
 constexpr int C1_NG = 128;       // largest grid
 
@@ -495,44 +492,34 @@ __global__ void k_c1_circulant(const float* __restrict__ D, int M, int n, float*
     }
 }
 
-// Cluster (columns [c0, c0 + C1_Q)), rank r:
-//   1. spread sources [r ns / CS, (r+1) ns / CS): staged C1_CH at a time (coalesced over the
-//      columns' rows); warp w takes the chunk's points [32 w, 32 w + 32), lane (q, s) =
-//      (lane % 8, lane / 8) the points 32 w + 4 k + s for column q, keeping the window sums of
-//      one base cell in registers and adding them to the rank's grid when the cell changes
-//      (points are sorted by cell);
-//   2. sum the CS partial grids (distributed shared memory) and convolve cells
-//      [r n / CS, (r+1) n / CS) with the circulant;
-//   3. copy all of H from the owning ranks and interpolate targets [r nt / CS, (r+1) nt / CS),
-//      with the message epilogue.
-// Grids are stored cell-major, [x][q], so the C1_Q columns of a cell are two 16-byte loads.
-__global__ void __cluster_dims__(C1_CS, 1, 1) __launch_bounds__(256)
-    k_c1_batch(const float* __restrict__ X, const VecScale* sX, const float* __restrict__ phi, const VecScale* sP,
-               const int* __restrict__ l0s, const float* __restrict__ ws, int ns, const int* __restrict__ l0t,
-               const float* __restrict__ wt, int nt, int n0, int ng, const float* __restrict__ cvec,
-               float* __restrict__ Y, float floor_, VecScale* out_sc) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cluster = cg::this_cluster();
+// One CTA per group of C1_Q columns [c0, c0 + C1_Q).  Spread: the sources are staged C1_CH at a
+// time (coalesced over the columns' rows); warp w takes the chunk's points [32 w, 32 w + 32),
+// lane (q, s) = (lane % 8, lane / 8) the points 32 w + 4 k + s for column q, keeping the window
+// sums of one base cell in registers and adding them to the shared grid when the cell changes
+// (points are sorted by cell).  Grids are stored cell-major, [x][q], so the convolution and the
+// interpolation read the C1_Q columns of a cell with two 16-byte loads.
+__global__ void __launch_bounds__(256) k_c1_batch(const float* __restrict__ X, const VecScale* sX,
+                                                  const float* __restrict__ phi, const VecScale* sP,
+                                                  const int* __restrict__ l0s, const float* __restrict__ ws, int ns,
+                                                  const int* __restrict__ l0t, const float* __restrict__ wt, int nt,
+                                                  int n0, int ng, const float* __restrict__ cvec,
+                                                  float* __restrict__ Y, float floor_, VecScale* out_sc) {
     __shared__ __align__(16) float sV[C1_CH][C1_Q];
     __shared__ __align__(16) float sW[C1_CH][12];
     __shared__ int sL[C1_CH];
-    __shared__ __align__(16) float sG[C1_NG][C1_Q];              // this rank's partial grids
-    __shared__ __align__(16) float sGs[C1_NG][C1_Q];             // summed grids
-    __shared__ __align__(16) float sHp[C1_NG / C1_CS][C1_Q];     // this rank's cells of H
+    __shared__ __align__(16) float sG[C1_NG][C1_Q];
     __shared__ __align__(16) float sH[C1_NG][C1_Q];
     __shared__ float sC[C1_NG];
     __shared__ float s_mx[8];
     __shared__ unsigned int s_cl[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int r = (int)cluster.block_rank();
-    const int c0 = (int)(blockIdx.x / C1_CS) * C1_Q, ncol = min(C1_Q, n0 - c0);
-    const int mask = ng - 1, cpr = ng / C1_CS;
+    const int c0 = blockIdx.x * C1_Q, ncol = min(C1_Q, n0 - c0);
+    const int mask = ng - 1;
     const float sx = 1.f / mx_of(sX, 0), sp = 1.f / mx_of(sP, 0);
     for (int i = tid; i < C1_NG * C1_Q; i += blockDim.x) (&sG[0][0])[i] = 0.f;
     for (int i = tid; i < ng; i += blockDim.x) sC[i] = cvec[i];
 
-    // ---- 1. spread ------------------------------------------------------------------------------
-    const int pb = (int)((long long)r * ns / C1_CS), pe = (int)((long long)(r + 1) * ns / C1_CS);
+    // ---- spread ---------------------------------------------------------------------------
     const int q = lane & 7, sidx = lane >> 3;
     float acc[MOT_W];
 #pragma unroll
@@ -546,21 +533,21 @@ __global__ void __cluster_dims__(C1_CS, 1, 1) __launch_bounds__(256)
             acc[a] = 0.f;
         }
     };
-    for (int jb = pb; jb < pe; jb += C1_CH) {
-        const int cnt = min(C1_CH, pe - jb);
+    for (int jb = 0; jb < ns; jb += C1_CH) {
+        const int cnt = min(C1_CH, ns - jb);
         __syncthreads();                                     // the previous chunk is consumed
         {   // all loads of the chunk in flight at once, then the transposed stores
             constexpr int PER = C1_Q * C1_CH / 256;
             float v[PER];
 #pragma unroll
-            for (int k = 0; k < PER; ++k) {
-                const int idx = tid + 256 * k, qq = idx / C1_CH, jj = idx - qq * C1_CH;
-                v[k] = (jj < cnt && qq < ncol) ? __ldg(X + (size_t)(c0 + qq) * ns + jb + jj) : 0.f;
+            for (int r = 0; r < PER; ++r) {
+                const int idx = tid + 256 * r, qq = idx / C1_CH, jj = idx - qq * C1_CH;
+                v[r] = (jj < cnt && qq < ncol) ? __ldg(X + (size_t)(c0 + qq) * ns + jb + jj) : 0.f;
             }
 #pragma unroll
-            for (int k = 0; k < PER; ++k) {
-                const int idx = tid + 256 * k, qq = idx / C1_CH, jj = idx - qq * C1_CH;
-                sV[jj][qq] = v[k] * sx;
+            for (int r = 0; r < PER; ++r) {
+                const int idx = tid + 256 * r, qq = idx / C1_CH, jj = idx - qq * C1_CH;
+                sV[jj][qq] = v[r] * sx;
             }
         }
         for (int jj = tid; jj < cnt; jj += blockDim.x) {
@@ -600,59 +587,27 @@ __global__ void __cluster_dims__(C1_CS, 1, 1) __launch_bounds__(256)
         }
     }
     __syncthreads();
-    cluster.sync();                                          // every rank's partial grid is complete
 
-    // ---- 2. sum the partial grids, convolve this rank's cells -------------------------------------
-    for (int i = tid; i < ng * (C1_Q / 4); i += blockDim.x) {
-        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int k = 0; k < C1_CS; ++k) {
-            const float4 g = reinterpret_cast<const float4*>(cluster.map_shared_rank(&sG[0][0], k))[i];
-            t.x += g.x;
-            t.y += g.y;
-            t.z += g.z;
-            t.w += g.w;
+    // ---- circulant: H[x][q] = sum_x' c((x - x') mod n) G[x'][q] -------------------------------
+    for (int o = tid; o < 2 * ng; o += blockDim.x) {
+        const int x = o % ng, q0 = 4 * (o / ng);
+        float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int xp = 0; xp < ng; ++xp) {
+            const float c = sC[(x - xp) & mask];
+            const float4 g = *reinterpret_cast<const float4*>(&sG[xp][q0]);
+            h.x = fmaf(c, g.x, h.x);
+            h.y = fmaf(c, g.y, h.y);
+            h.z = fmaf(c, g.z, h.z);
+            h.w = fmaf(c, g.w, h.w);
         }
-        reinterpret_cast<float4*>(&sGs[0][0])[i] = t;
+        *reinterpret_cast<float4*>(&sH[x][q0]) = h;
     }
     __syncthreads();
-    {   // output (cell x, columns q0..q0+3) summed by S consecutive lanes over x' = sub (mod S)
-        const int ngroups = 2 * cpr, S = min(32, 256 / ngroups);
-        const int g = tid / S, sub = tid - g * S;
-        if (g < ngroups) {
-            const int xl = g >> 1, x = r * cpr + xl, q0 = 4 * (g & 1);
-            float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int xp = sub; xp < ng; xp += S) {
-                const float c = sC[(x - xp) & mask];
-                const float4 gv = *reinterpret_cast<const float4*>(&sGs[xp][q0]);
-                h.x = fmaf(c, gv.x, h.x);
-                h.y = fmaf(c, gv.y, h.y);
-                h.z = fmaf(c, gv.z, h.z);
-                h.w = fmaf(c, gv.w, h.w);
-            }
-            for (int o = S / 2; o > 0; o >>= 1) {
-                h.x += __shfl_xor_sync(0xffffffffu, h.x, o);
-                h.y += __shfl_xor_sync(0xffffffffu, h.y, o);
-                h.z += __shfl_xor_sync(0xffffffffu, h.z, o);
-                h.w += __shfl_xor_sync(0xffffffffu, h.w, o);
-            }
-            if (sub == 0) *reinterpret_cast<float4*>(&sHp[xl][q0]) = h;
-        }
-    }
-    __syncthreads();
-    cluster.sync();                                          // every rank's cells of H are complete
 
-    // ---- 3. all of H, then interpolation + message epilogue ----------------------------------------
-    for (int i = tid; i < 2 * ng; i += blockDim.x) {
-        const int x = i >> 1, owner = x / cpr;
-        const float4* src = reinterpret_cast<const float4*>(cluster.map_shared_rank(&sHp[0][0], owner));
-        reinterpret_cast<float4*>(&sH[0][0])[i] = src[(x - owner * cpr) * 2 + (i & 1)];
-    }
-    __syncthreads();
+    // ---- interpolation + message epilogue -------------------------------------------------------
     float mx = 0.f;
     unsigned int clamps = 0u;
-    const int tb = (int)((long long)r * nt / C1_CS), te = (int)((long long)(r + 1) * nt / C1_CS);
-    for (int i = tb + tid; i < te; i += blockDim.x) {
+    for (int i = tid; i < nt; i += blockDim.x) {
         const int b = l0t[i];
         float y[C1_Q];
 #pragma unroll
@@ -704,7 +659,6 @@ __global__ void __cluster_dims__(C1_CS, 1, 1) __launch_bounds__(256)
         atomic_max_pos(&out_sc->mx_bits, m);
         if (c) atomicAdd(&out_sc->clamped, c);
     }
-    cluster.sync();                                          // peers have copied this rank's H
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1579,8 +1533,8 @@ cudaError_t launch_c1_circulant(const float* D, int M, int n, float* c, cudaStre
 cudaError_t launch_c1_batch(const float* X, const VecScale* sX, const float* phi, const VecScale* sP, const int* l0s,
                             const float* ws, int ns, const int* l0t, const float* wt, int nt, int n0, int ng,
                             const float* cvec, float* Y, float floor_, VecScale* out_sc, cudaStream_t st) {
-    if (ng > C1_NG || ng < 2 * C1_CS || (ng & (ng - 1)) != 0) return cudaErrorInvalidValue;
-    k_c1_batch<<<((n0 + C1_Q - 1) / C1_Q) * C1_CS, 256, 0, st>>>(X, sX, phi, sP, l0s, ws, ns, l0t, wt, nt, n0, ng,
-                                                                cvec, Y, floor_, out_sc);
+    if (ng > C1_NG || (ng & (ng - 1)) != 0) return cudaErrorInvalidValue;
+    k_c1_batch<<<(n0 + C1_Q - 1) / C1_Q, 256, 0, st>>>(X, sX, phi, sP, l0s, ws, ns, l0t, wt, nt, n0, ng, cvec, Y,
+                                                      floor_, out_sc);
     return cudaGetLastError();
 }
