@@ -61,7 +61,7 @@ extern "C" {
 #define MOT_K_NODE     4    /* element-wise sweep updates and FP64 reductions                  */
 #define MOT_K_SETUP    5    /* normalisation, binning, kernel Fourier coefficients             */
 #define MOT_K_CIRCLE   6    /* circle row-dot / column-sum scaling updates                     */
-#define MOT_K_FUSED    7    /* fused fast summation: 2-D cluster kernel, 1-D circle batches     */
+#define MOT_K_FUSED    7    /* fused 2-D fast summation (spread, DFTs, gather in one cluster)  */
 #define MOT_K_TCGEMM   8    /* split-BF16 kernel product on the tensor cores (tcgen05)         */
 #define MOT_K_SPLIT    9    /* scaled source matrix split into BF16 hi / lo                    */
 #define MOT_NKCLASS    10

@@ -49,7 +49,8 @@ cudaError_t launch_c1_taps(const float* u, int n, int* l0, float* w, cudaStream_
 cudaError_t launch_c1_circulant(const float* D, int M, int n, float* c, cudaStream_t st);
 cudaError_t launch_c1_batch(const float* X, const VecScale* sX, const float* phi, const VecScale* sP, const int* l0s,
                             const float* ws, int ns, const int* l0t, const float* wt, int nt, int n0, int ng,
-                            const float* cvec, float* Y, float floor_, VecScale* out_sc, cudaStream_t st);
+                            const float* cvec, float* G, float* Y, float floor_, VecScale* out_sc, cudaStream_t st,
+                            int stage);
 // One-block iteration prologue (resets, iteration counter, accumulators).
 cudaError_t launch_prologue(VecScale* const* list, int nlist, int save_prev, int bump, double* zero_d, int zero_n,
                             const Globals& G, cudaStream_t st);

@@ -460,18 +460,17 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
 // Batched 1-D fast summation of the circle (Algorithm 3, N right-hand sides, d = 1).
 //
 // In one dimension the oversampled grid (n <= 128) is far smaller than the point sets, so a
-// batch Y[c] = K (phi (.) X[c]), c < n0, is three small dense steps per column, all done by one
-// CTA for C1_Q columns without leaving shared memory:
-//   spread : G[c] = sum_j X[c][j] phi_j psi(u_j - .)               (Algorithm 4 step 6)
-//   conv   : H[c] = C G[c], the circulant c(m) = sum_{q<=M} D_q cos(2 pi q m / n) of Eq.
-//            (fastsum_mat) (the real part of IFFT(D FFT(.)))        (steps 7 - 8, pruned)
-//   gather : Y[c][i] = sum_a H[c][l0_i + a] psi_a(u_i), then the message epilogue (step 9)
-// Each column's message is read once and written once.  The window taps and base cells of every
-// point are computed once per solve (k_c1_taps).
+// batch Y[c] = K (phi (.) X[c]), c < n0, runs as two passes over the message matrices:
+//   k_c1_spread : G[c] = sum_j X[c][j] phi_j psi(u_j - .)   (32 columns per CTA, lane = column;
+//                 the point's taps are the same for every column and are broadcast)
+//   k_c1_gather : H[c] = C G[c] with the circulant C of Eq. (fastsum_mat) (c(m) = sum_{q<=M}
+//                 D_q cos(2 pi q m / n), the real part of IFFT(D FFT(.))), then
+//                 Y[c][i] = sum_a H[c][l0_i + a] psi_a(u_i) and the message epilogue
+// The window taps and base cells of every point are computed once per solve (k_c1_taps).
 // ------------------------------------------------------------------------------------------
-constexpr int C1_Q = 8;          // columns per CTA
-constexpr int C1_CH = 256;       // source points staged per step
-constexpr int C1_NG = 128;       // largest grid
+constexpr int C1_COLS = 32;      // columns per CTA
+constexpr int C1_CHUNK = 128;    // source points staged per step
+constexpr int C1_TGT = 512;      // targets per gather CTA (2 per thread)
 
 __global__ void k_c1_taps(const float* __restrict__ u, int n, int* __restrict__ l0, float* __restrict__ w) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
@@ -492,35 +491,25 @@ __global__ void k_c1_circulant(const float* __restrict__ D, int M, int n, float*
     }
 }
 
-// One CTA per group of C1_Q columns [c0, c0 + C1_Q).  Spread: the sources are staged C1_CH at a
-// time (coalesced over the columns' rows); warp w takes the chunk's points [32 w, 32 w + 32),
-// lane (q, s) = (lane % 8, lane / 8) the points 32 w + 4 k + s for column q, keeping the window
-// sums of one base cell in registers and adding them to the shared grid when the cell changes
-// (points are sorted by cell).  Grids are stored cell-major, [x][q], so the convolution and the
-// interpolation read the C1_Q columns of a cell with two 16-byte loads.
-__global__ void __launch_bounds__(256) k_c1_batch(const float* __restrict__ X, const VecScale* sX,
-                                                  const float* __restrict__ phi, const VecScale* sP,
-                                                  const int* __restrict__ l0s, const float* __restrict__ ws, int ns,
-                                                  const int* __restrict__ l0t, const float* __restrict__ wt, int nt,
-                                                  int n0, int ng, const float* __restrict__ cvec,
-                                                  float* __restrict__ Y, float floor_, VecScale* out_sc) {
-    __shared__ __align__(16) float sV[C1_CH][C1_Q];
-    __shared__ __align__(16) float sW[C1_CH][12];
-    __shared__ int sL[C1_CH];
-    __shared__ __align__(16) float sG[C1_NG][C1_Q];
-    __shared__ __align__(16) float sH[C1_NG][C1_Q];
-    __shared__ float sC[C1_NG];
-    __shared__ float s_mx[8];
-    __shared__ unsigned int s_cl[8];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int c0 = blockIdx.x * C1_Q, ncol = min(C1_Q, n0 - c0);
+// grid (ceil(n0 / 32), splits): CTA (b, p) spreads points [p ns / splits, (p+1) ns / splits) of
+// columns [32 b, 32 b + 32) and adds its partial grids to G (zeroed by the caller).
+__global__ void __launch_bounds__(256) k_c1_spread(const float* __restrict__ X, const VecScale* sX,
+                                                   const float* __restrict__ phi, const VecScale* sP,
+                                                   const int* __restrict__ l0, const float* __restrict__ w, int ns,
+                                                   int n0, int ng, int splits, float* __restrict__ G) {
+    __shared__ float sV[C1_CHUNK][C1_COLS + 1];
+    __shared__ __align__(16) float sW[C1_CHUNK][12];
+    __shared__ int sL[C1_CHUNK];
+    __shared__ float sG[C1_COLS][128 + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int mask = ng - 1;
     const float sx = 1.f / mx_of(sX, 0), sp = 1.f / mx_of(sP, 0);
-    for (int i = tid; i < C1_NG * C1_Q; i += blockDim.x) (&sG[0][0])[i] = 0.f;
-    for (int i = tid; i < ng; i += blockDim.x) sC[i] = cvec[i];
-
-    // ---- spread ---------------------------------------------------------------------------
-    const int q = lane & 7, sidx = lane >> 3;
+    const int nitems = ((n0 + C1_COLS - 1) / C1_COLS) * splits;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {   // (column group, point split)
+    const int c0 = (item / splits) * C1_COLS, sidx = item % splits;
+    const int pb = (int)((long long)sidx * ns / splits), pe = (int)((long long)(sidx + 1) * ns / splits);
+    __syncthreads();                                        // the previous item's grid is written out
+    for (int i = tid; i < C1_COLS * ng; i += blockDim.x) sG[i / ng][i % ng] = 0.f;
     float acc[MOT_W];
 #pragma unroll
     for (int a = 0; a < MOT_W; ++a) acc[a] = 0.f;
@@ -529,44 +518,44 @@ __global__ void __launch_bounds__(256) k_c1_batch(const float* __restrict__ X, c
     auto flush = [&]() {
 #pragma unroll
         for (int a = 0; a < MOT_W; ++a) {
-            atomicAdd(&sG[(cur + a) & mask][q], acc[a]);
+            atomicAdd(&sG[lane][(cur + a) & mask], acc[a]);
             acc[a] = 0.f;
         }
     };
-    for (int jb = 0; jb < ns; jb += C1_CH) {
-        const int cnt = min(C1_CH, ns - jb);
-        __syncthreads();                                     // the previous chunk is consumed
-        {   // all loads of the chunk in flight at once, then the transposed stores
-            constexpr int PER = C1_Q * C1_CH / 256;
+    const int per_warp = C1_CHUNK / nwarps;
+    for (int jb = pb; jb < pe; jb += C1_CHUNK) {
+        const int cnt = min(C1_CHUNK, pe - jb);
+        __syncthreads();                                    // the previous chunk is consumed
+        {   // all loads of the chunk in flight at once (16 per thread), then the transposed stores
+            constexpr int PER = C1_COLS * C1_CHUNK / 256;
             float v[PER];
 #pragma unroll
             for (int r = 0; r < PER; ++r) {
-                const int idx = tid + 256 * r, qq = idx / C1_CH, jj = idx - qq * C1_CH;
-                v[r] = (jj < cnt && qq < ncol) ? __ldg(X + (size_t)(c0 + qq) * ns + jb + jj) : 0.f;
+                const int idx = tid + 256 * r, q = idx / C1_CHUNK, jj = idx - q * C1_CHUNK;
+                v[r] = (jj < cnt && c0 + q < n0) ? __ldg(X + (size_t)(c0 + q) * ns + jb + jj) : 0.f;
             }
 #pragma unroll
             for (int r = 0; r < PER; ++r) {
-                const int idx = tid + 256 * r, qq = idx / C1_CH, jj = idx - qq * C1_CH;
-                sV[jj][qq] = v[r] * sx;
+                const int idx = tid + 256 * r, q = idx / C1_CHUNK, jj = idx - q * C1_CHUNK;
+                sV[jj][q] = v[r] * sx;
             }
         }
         for (int jj = tid; jj < cnt; jj += blockDim.x) {
             const float pj = phi[jb + jj] * sp;
-            sL[jj] = l0s[jb + jj];
+            sL[jj] = l0[jb + jj];
 #pragma unroll
-            for (int a = 0; a < MOT_W; ++a) sW[jj][a] = ws[(size_t)(jb + jj) * MOT_W + a] * pj;
+            for (int a = 0; a < MOT_W; ++a) sW[jj][a] = w[(size_t)(jb + jj) * MOT_W + a] * pj;
         }
         __syncthreads();
-        for (int k = 0; k < 8; ++k) {
-            const int p = 32 * warp + 4 * k + sidx;
-            if (p >= cnt) break;
+        const int p0 = warp * per_warp, p1 = min(cnt, p0 + per_warp);
+        for (int p = p0; p < p1; ++p) {
             const int l = sL[p];
-            if (!have || l != cur) {
+            if (!have || l != cur) {                        // uniform over the warp
                 if (have) flush();
                 cur = l;
                 have = true;
             }
-            const float v = sV[p][q];
+            const float v = sV[p][lane];
             const float4 w0 = *reinterpret_cast<const float4*>(&sW[p][0]);
             const float4 w1 = *reinterpret_cast<const float4*>(&sW[p][4]);
             const float2 w2 = *reinterpret_cast<const float2*>(&sW[p][8]);
@@ -581,62 +570,76 @@ __global__ void __launch_bounds__(256) k_c1_batch(const float* __restrict__ X, c
             acc[8] = fmaf(v, w2.x, acc[8]);
             acc[9] = fmaf(v, w2.y, acc[9]);
         }
-        if (have) {                                          // the next chunk starts elsewhere
-            flush();
-            have = false;
-        }
+    }
+    if (have) flush();
+    __syncthreads();
+    for (int i = tid; i < C1_COLS * ng; i += blockDim.x) {
+        const int q = i / ng, x = i - q * ng;
+        const float val = sG[q][x];
+        if (c0 + q < n0 && val != 0.f) atomicAdd(&G[(size_t)(c0 + q) * ng + x], val);
+    }
+    }   // item
+}
+
+// grid (ceil(nt / 512), ceil(n0 / 32)): convolution of 32 columns' grids, then two targets per
+// thread for each column, message epilogue (floor, maximum, clamp count) and block reduction.
+__global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, const float* __restrict__ cvec,
+                                                   const int* __restrict__ l0, const float* __restrict__ w, int nt,
+                                                   int n0, int ng, float* __restrict__ Y, float floor_,
+                                                   VecScale* out_sc, const VecScale* sA, const VecScale* sB) {
+    __shared__ float sGc[C1_COLS][128 + 1];
+    __shared__ float sH[C1_COLS][128 + 1];
+    __shared__ float sC[128];
+    __shared__ float s_mx[8];
+    __shared__ unsigned int s_cl[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c0 = blockIdx.y * C1_COLS, mask = ng - 1;
+    const int ncol = min(C1_COLS, n0 - c0);
+    for (int i = tid; i < ng; i += blockDim.x) sC[i] = cvec[i];
+    for (int i = tid; i < ncol * ng; i += blockDim.x) sGc[i / ng][i % ng] = G[(size_t)c0 * ng + i];
+    __syncthreads();
+    for (int i = tid; i < ncol * ng; i += blockDim.x) {
+        const int q = i / ng, x = i - q * ng;
+        float s = 0.f;
+        for (int xp = 0; xp < ng; ++xp) s = fmaf(sC[(x - xp) & mask], sGc[q][xp], s);
+        sH[q][x] = s;
     }
     __syncthreads();
-
-    // ---- circulant: H[x][q] = sum_x' c((x - x') mod n) G[x'][q] -------------------------------
-    for (int o = tid; o < 2 * ng; o += blockDim.x) {
-        const int x = o % ng, q0 = 4 * (o / ng);
-        float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int xp = 0; xp < ng; ++xp) {
-            const float c = sC[(x - xp) & mask];
-            const float4 g = *reinterpret_cast<const float4*>(&sG[xp][q0]);
-            h.x = fmaf(c, g.x, h.x);
-            h.y = fmaf(c, g.y, h.y);
-            h.z = fmaf(c, g.z, h.z);
-            h.w = fmaf(c, g.w, h.w);
-        }
-        *reinterpret_cast<float4*>(&sH[x][q0]) = h;
-    }
-    __syncthreads();
-
-    // ---- interpolation + message epilogue -------------------------------------------------------
     float mx = 0.f;
     unsigned int clamps = 0u;
-    for (int i = tid; i < nt; i += blockDim.x) {
-        const int b = l0t[i];
-        float y[C1_Q];
-#pragma unroll
-        for (int qq = 0; qq < C1_Q; ++qq) y[qq] = 0.f;
+    auto emit = [&](float s, int q, int i) {
+        if (!(s >= floor_)) {
+            s = floor_;
+            clamps++;
+        }
+        mx = fmaxf(mx, s);
+        Y[(size_t)(c0 + q) * nt + i] = s;
+    };
+    for (int k = 0; k < 2; ++k) {
+        const int i = blockIdx.x * C1_TGT + k * blockDim.x + tid;
+        if (i >= nt) break;
+        float t[MOT_W];
+        const float* hp[MOT_W];                             // column 0 of each tap's grid cell
+        const int b = l0[i];
 #pragma unroll
         for (int a = 0; a < MOT_W; ++a) {
-            const float t = __ldg(wt + (size_t)i * MOT_W + a);
-            const int x = (b + a) & mask;
-            const float4 h0 = *reinterpret_cast<const float4*>(&sH[x][0]);
-            const float4 h1 = *reinterpret_cast<const float4*>(&sH[x][4]);
-            y[0] = fmaf(h0.x, t, y[0]);
-            y[1] = fmaf(h0.y, t, y[1]);
-            y[2] = fmaf(h0.z, t, y[2]);
-            y[3] = fmaf(h0.w, t, y[3]);
-            y[4] = fmaf(h1.x, t, y[4]);
-            y[5] = fmaf(h1.y, t, y[5]);
-            y[6] = fmaf(h1.z, t, y[6]);
-            y[7] = fmaf(h1.w, t, y[7]);
+            t[a] = w[(size_t)i * MOT_W + a];
+            hp[a] = &sH[0][(b + a) & mask];
         }
+        if (ncol == C1_COLS) {
 #pragma unroll
-        for (int qq = 0; qq < C1_Q; ++qq) {
-            if (qq < ncol) {
-                float v = y[qq];
-                if (!(v >= floor_)) {
-                    v = floor_;
-                    clamps++;
-                }
-                mx = fmaxf(mx, v);
-                Y[(size_t)(c0 + qq) * nt + i] = v;
+            for (int q = 0; q < C1_COLS; ++q) {             // constant offsets q * (128 + 1)
+                float s = 0.f;
+#pragma unroll
+                for (int a = 0; a < MOT_W; ++a) s = fmaf(hp[a][q * (128 + 1)], t[a], s);
+                emit(s, q, i);
+            }
+        } else {
+            for (int q = 0; q < ncol; ++q) {
+                float s = 0.f;
+#pragma unroll
+                for (int a = 0; a < MOT_W; ++a) s = fmaf(hp[a][q * (128 + 1)], t[a], s);
+                emit(s, q, i);
             }
         }
     }
@@ -655,7 +658,7 @@ __global__ void __launch_bounds__(256) k_c1_batch(const float* __restrict__ X, c
             m = fmaxf(m, s_mx[k]);
             c += s_cl[k];
         }
-        out_sc->ls = sP->ls + (double)logf(mx_of(sP, 0)) + sX->ls + (double)logf(mx_of(sX, 0));
+        out_sc->ls = sA->ls + (double)logf(mx_of(sA, 0)) + sB->ls + (double)logf(mx_of(sB, 0));
         atomic_max_pos(&out_sc->mx_bits, m);
         if (c) atomicAdd(&out_sc->clamped, c);
     }
@@ -1532,9 +1535,20 @@ cudaError_t launch_c1_circulant(const float* D, int M, int n, float* c, cudaStre
 
 cudaError_t launch_c1_batch(const float* X, const VecScale* sX, const float* phi, const VecScale* sP, const int* l0s,
                             const float* ws, int ns, const int* l0t, const float* wt, int nt, int n0, int ng,
-                            const float* cvec, float* Y, float floor_, VecScale* out_sc, cudaStream_t st) {
-    if (ng > C1_NG || (ng & (ng - 1)) != 0) return cudaErrorInvalidValue;
-    k_c1_batch<<<(n0 + C1_Q - 1) / C1_Q, 256, 0, st>>>(X, sX, phi, sP, l0s, ws, ns, l0t, wt, nt, n0, ng, cvec, Y,
-                                                      floor_, out_sc);
+                            const float* cvec, float* G, float* Y, float floor_, VecScale* out_sc, cudaStream_t st,
+                            int stage) {
+    const int nb = (n0 + C1_COLS - 1) / C1_COLS;
+    if (stage == 0) {
+        cudaError_t e = cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n0 * ng, st);
+        if (e != cudaSuccess) return e;
+        // work items (column group, point split); a grid of at most one wave of resident CTAs (two
+        // per SM) loops over them
+        const int splits = std::max(1, std::min(std::min(8, std::max(1, (2 * 152) / nb)), std::max(1, ns / C1_CHUNK)));
+        const int items = nb * splits;
+        k_c1_spread<<<std::min(items, 2 * 152), 256, 0, st>>>(X, sX, phi, sP, l0s, ws, ns, n0, ng, splits, G);
+    } else {
+        k_c1_gather<<<dim3((nt + C1_TGT - 1) / C1_TGT, nb), 256, 0, st>>>(G, cvec, l0t, wt, nt, n0, ng, Y, floor_,
+                                                                         out_sc, sP, sX);
+    }
     return cudaGetLastError();
 }

@@ -1072,6 +1072,7 @@ struct CirclePlan {
     std::vector<int*> c1_l0;        // per node: base cell of each point's window
     std::vector<float*> c1_w;       // per node: window taps [n_k][10]
     std::vector<float*> c1_c;       // per edge: circulant of D (n floats)
+    float* c1_G = nullptr;          // n0 x n spread grids of one batch
     bool has_close = false;         // closing edge against sigma(x^0) (Section 6.3)
     float* u_close = nullptr;       // [d][n0] sigma(x^0) in node 0's sorted order, grid units
     uint16_t* a_hi = nullptr;       // tensor-core path: split source matrix, n0 x ld (BF16 pairs)
@@ -1138,6 +1139,7 @@ void layout_circle(Arena& A, CirclePlan& C) {
             C.c1_w[k] = A.take<float>((size_t)C.n[k] * MOT_W);
             C.c1_c[k] = A.take<float>(128);
         }
+        C.c1_G = A.take<float>((size_t)C.n0 * 128);
     }
     C.ktf_hi.assign(K, nullptr);
     C.ktf_lo.assign(K, nullptr);
@@ -1324,11 +1326,14 @@ int c_run_batch(CirclePlan& C, CBatch& B, cudaStream_t st, Timer& tm, long long&
     cudaEvent_t e = nullptr;
     if (C.c1) {
         const int s = B.s, t = B.t;
-        RET(tm.begin(MOT_K_FUSED, &e));
-        CK(launch_c1_batch(B.X, B.sX, C.phi[s], C.phi_sc(s), C.c1_l0[s], C.c1_w[s], C.n[s], C.c1_l0[t], C.c1_w[t],
-                           C.n[t], C.n0, C.g.n, C.c1_c[B.edge], B.Y, C.G.floor_, B.out_sc, st));
-        RET(tm.end(e));
-        nl += 1;
+        for (int stage = 0; stage < 2; ++stage) {
+            RET(tm.begin(stage == 0 ? MOT_K_SPREAD : MOT_K_GATHER, &e));
+            CK(launch_c1_batch(B.X, B.sX, C.phi[s], C.phi_sc(s), C.c1_l0[s], C.c1_w[s], C.n[s], C.c1_l0[t],
+                               C.c1_w[t], C.n[t], C.n0, C.g.n, C.c1_c[B.edge], C.c1_G, B.Y, C.G.floor_, B.out_sc,
+                               st, stage));
+            RET(tm.end(e));
+        }
+        nl += 3;                // memset, spread, gather
         return MOT_OK;
     }
     for (int c0 = 0; c0 < C.n0; c0 += C.CB) {
@@ -1550,7 +1555,7 @@ int circle_setup(const mot_problem* P, const mot_options& o, CirclePlan& C, void
                 RET(make_D_for((C.eta / C.w[k]) / (g.s * g.s), g, C.d, o, C.dscr_a, C.dscr_b, C.D[k], st));
         }
         for (int c = 0; c < C.CB; ++c) CK(cudaMemsetAsync(C.grid[c], 0, gsz * sizeof(float), st));
-        C.c1 = c1_supported(C.d, g.n) && C.c1_l0[0] != nullptr;
+        C.c1 = c1_supported(C.d, g.n) && C.c1_G != nullptr;
         if (C.c1) {
             for (int k = 0; k < K; ++k) CK(launch_c1_taps(C.sets[k].u, C.n[k], C.c1_l0[k], C.c1_w[k], st));
             for (int k = 0; k < K; ++k) CK(launch_c1_circulant(C.D[k], g.M, g.n, C.c1_c[k], st));
