@@ -493,7 +493,7 @@ __global__ void k_c1_circulant(const float* __restrict__ D, int M, int n, float*
 
 // grid (ceil(n0 / 32), splits): CTA (b, p) spreads points [p ns / splits, (p+1) ns / splits) of
 // columns [32 b, 32 b + 32) and adds its partial grids to G (zeroed by the caller).
-__global__ void __launch_bounds__(256) k_c1_spread(const float* __restrict__ X, const VecScale* sX,
+__global__ void __launch_bounds__(256, 3) k_c1_spread(const float* __restrict__ X, const VecScale* sX,
                                                    const float* __restrict__ phi, const VecScale* sP,
                                                    const int* __restrict__ l0, const float* __restrict__ w, int ns,
                                                    int n0, int ng, int splits, float* __restrict__ G) {
@@ -598,8 +598,19 @@ __global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, 
     for (int i = tid; i < ng; i += blockDim.x) sC[i] = cvec[i];
     for (int i = tid; i < ncol * ng; i += blockDim.x) sGc[i / ng][i % ng] = G[(size_t)c0 * ng + i];
     __syncthreads();
-    for (int i = tid; i < ncol * ng; i += blockDim.x) {
-        const int q = i / ng, x = i - q * ng;
+    // only the cells this block's targets read (targets are sorted by cell): [l0 of the first,
+    // l0 of the last + MOT_W - 1], about a quarter of the grid per block
+    int xlo = 0, nx = ng;
+    {
+        const int i_first = blockIdx.x * C1_TGT, i_last = min(nt, i_first + C1_TGT) - 1;
+        const int lo = l0[i_first], hi = l0[i_last] + MOT_W - 1;
+        if (hi - lo + 1 < ng) {
+            xlo = lo;
+            nx = hi - lo + 1;
+        }
+    }
+    for (int i = tid; i < ncol * nx; i += blockDim.x) {
+        const int q = i / nx, x = (xlo + (i - q * nx)) & mask;
         float s = 0.f;
         for (int xp = 0; xp < ng; ++xp) s = fmaf(sC[(x - xp) & mask], sGc[q][xp], s);
         sH[q][x] = s;
@@ -1541,11 +1552,11 @@ cudaError_t launch_c1_batch(const float* X, const VecScale* sX, const float* phi
     if (stage == 0) {
         cudaError_t e = cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n0 * ng, st);
         if (e != cudaSuccess) return e;
-        // work items (column group, point split); a grid of at most one wave of resident CTAs (two
-        // per SM) loops over them
-        const int splits = std::max(1, std::min(std::min(8, std::max(1, (2 * 152) / nb)), std::max(1, ns / C1_CHUNK)));
+        // work items (column group, point split); a grid of at most one wave of resident CTAs (three
+        // per SM at 80 registers and 40 KB of shared memory) loops over them
+        const int splits = std::max(1, std::min(std::min(8, std::max(1, (3 * 152) / nb)), std::max(1, ns / C1_CHUNK)));
         const int items = nb * splits;
-        k_c1_spread<<<std::min(items, 2 * 152), 256, 0, st>>>(X, sX, phi, sP, l0s, ws, ns, n0, ng, splits, G);
+        k_c1_spread<<<std::min(items, 3 * 152), 256, 0, st>>>(X, sX, phi, sP, l0s, ws, ns, n0, ng, splits, G);
     } else {
         k_c1_gather<<<dim3((nt + C1_TGT - 1) / C1_TGT, nb), 256, 0, st>>>(G, cvec, l0t, wt, nt, n0, ng, Y, floor_,
                                                                          out_sc, sP, sX);
