@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
 // ------------------------------------------------------------------------------------------
 constexpr int C1_COLS = 32;      // columns per CTA
 constexpr int C1_CHUNK = 128;    // source points staged per step
-constexpr int C1_TGT = 512;      // targets per gather CTA (2 per thread)
+constexpr int C1_TGT = 256;      // targets per gather CTA (1 per thread)
 
 __global__ void k_c1_taps(const float* __restrict__ u, int n, int* __restrict__ l0, float* __restrict__ w) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
@@ -523,30 +523,43 @@ __global__ void __launch_bounds__(256, 3) k_c1_spread(const float* __restrict__ 
         }
     };
     const int per_warp = C1_CHUNK / nwarps;
+    // the next chunk's loads (messages, then the points' taps) are issued before the current
+    // chunk is accumulated, so their latency overlaps the arithmetic
+    constexpr int PER = C1_COLS * C1_CHUNK / 256;
+    static_assert(C1_CHUNK <= 256, "one point per thread for the taps");
+    float v[PER], tw[MOT_W], tp = 0.f;
+    int tl = 0;
+    auto load_chunk = [&](int jb0) {
+        const int cnt0 = min(C1_CHUNK, pe - jb0);
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int idx = tid + 256 * r, q = idx / C1_CHUNK, jj = idx - q * C1_CHUNK;
+            v[r] = (jj < cnt0 && c0 + q < n0) ? __ldg(X + (size_t)(c0 + q) * ns + jb0 + jj) : 0.f;
+        }
+        if (tid < cnt0) {
+            tp = phi[jb0 + tid];
+            tl = l0[jb0 + tid];
+#pragma unroll
+            for (int a = 0; a < MOT_W; ++a) tw[a] = w[(size_t)(jb0 + tid) * MOT_W + a];
+        }
+    };
+    if (pb < pe) load_chunk(pb);
     for (int jb = pb; jb < pe; jb += C1_CHUNK) {
         const int cnt = min(C1_CHUNK, pe - jb);
         __syncthreads();                                    // the previous chunk is consumed
-        {   // all loads of the chunk in flight at once (16 per thread), then the transposed stores
-            constexpr int PER = C1_COLS * C1_CHUNK / 256;
-            float v[PER];
 #pragma unroll
-            for (int r = 0; r < PER; ++r) {
-                const int idx = tid + 256 * r, q = idx / C1_CHUNK, jj = idx - q * C1_CHUNK;
-                v[r] = (jj < cnt && c0 + q < n0) ? __ldg(X + (size_t)(c0 + q) * ns + jb + jj) : 0.f;
-            }
-#pragma unroll
-            for (int r = 0; r < PER; ++r) {
-                const int idx = tid + 256 * r, q = idx / C1_CHUNK, jj = idx - q * C1_CHUNK;
-                sV[jj][q] = v[r] * sx;
-            }
+        for (int r = 0; r < PER; ++r) {
+            const int idx = tid + 256 * r, q = idx / C1_CHUNK, jj = idx - q * C1_CHUNK;
+            sV[jj][q] = v[r] * sx;
         }
-        for (int jj = tid; jj < cnt; jj += blockDim.x) {
-            const float pj = phi[jb + jj] * sp;
-            sL[jj] = l0[jb + jj];
+        if (tid < cnt) {
+            const float pj = tp * sp;
+            sL[tid] = tl;
 #pragma unroll
-            for (int a = 0; a < MOT_W; ++a) sW[jj][a] = w[(size_t)(jb + jj) * MOT_W + a] * pj;
+            for (int a = 0; a < MOT_W; ++a) sW[tid][a] = tw[a] * pj;
         }
         __syncthreads();
+        if (jb + C1_CHUNK < pe) load_chunk(jb + C1_CHUNK);
         const int p0 = warp * per_warp, p1 = min(cnt, p0 + per_warp);
         for (int p = p0; p < p1; ++p) {
             const int l = sL[p];
@@ -581,7 +594,7 @@ __global__ void __launch_bounds__(256, 3) k_c1_spread(const float* __restrict__ 
     }   // item
 }
 
-// grid (ceil(nt / 512), ceil(n0 / 32)): convolution of 32 columns' grids, then two targets per
+// grid (ceil(nt / C1_TGT), ceil(n0 / 32)): convolution of 32 columns' grids, then one target per
 // thread for each column, message epilogue (floor, maximum, clamp count) and block reduction.
 __global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, const float* __restrict__ cvec,
                                                    const int* __restrict__ l0, const float* __restrict__ w, int nt,
@@ -626,7 +639,7 @@ __global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, 
         mx = fmaxf(mx, s);
         Y[(size_t)(c0 + q) * nt + i] = s;
     };
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < C1_TGT / 256; ++k) {
         const int i = blockIdx.x * C1_TGT + k * blockDim.x + tid;
         if (i >= nt) break;
         float t[MOT_W];
