@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
 // ------------------------------------------------------------------------------------------
 constexpr int C1_COLS = 32;      // columns per CTA
 constexpr int C1_CHUNK = 128;    // source points staged per step
-constexpr int C1_TGT = 256;      // targets per gather CTA (1 per thread)
+constexpr int C1_TGT = 512;      // targets per gather CTA (2 per thread)
 
 __global__ void k_c1_taps(const float* __restrict__ u, int n, int* __restrict__ l0, float* __restrict__ w) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(256, 3) k_c1_spread(const float* __restrict__ 
     }   // item
 }
 
-// grid (ceil(nt / C1_TGT), ceil(n0 / 32)): convolution of 32 columns' grids, then one target per
+// grid (ceil(nt / C1_TGT), ceil(n0 / 32)): convolution of 32 columns' grids, then two targets per
 // thread for each column, message epilogue (floor, maximum, clamp count) and block reduction.
 __global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, const float* __restrict__ cvec,
                                                    const int* __restrict__ l0, const float* __restrict__ w, int nt,
