@@ -594,28 +594,22 @@ __global__ void __launch_bounds__(256, 3) k_c1_spread(const float* __restrict__ 
     }   // item
 }
 
-// grid (ceil(nt / C1_TGT), ceil(n0 / C1_GC)): convolution of C1_GC columns' grids over the cells
-// the block's targets read, then two targets per thread for each column, message epilogue
-// (floor, maximum, clamp count) and block reduction.  Grids are held cell-major ([x][q]), so a
-// thread convolves / interpolates four columns with one 16-byte load per cell.
-constexpr int C1_GC = 16;        // columns per gather CTA
+// grid (ceil(nt / C1_TGT), ceil(n0 / 32)): convolution of 32 columns' grids, then two targets per
+// thread for each column, message epilogue (floor, maximum, clamp count) and block reduction.
 __global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, const float* __restrict__ cvec,
                                                    const int* __restrict__ l0, const float* __restrict__ w, int nt,
                                                    int n0, int ng, float* __restrict__ Y, float floor_,
                                                    VecScale* out_sc, const VecScale* sA, const VecScale* sB) {
-    __shared__ __align__(16) float sGc[128][C1_GC];
-    __shared__ __align__(16) float sH[128][C1_GC];
+    __shared__ float sGc[C1_COLS][128 + 1];
+    __shared__ float sH[C1_COLS][128 + 1];
     __shared__ float sC[128];
     __shared__ float s_mx[8];
     __shared__ unsigned int s_cl[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int c0 = blockIdx.y * C1_GC, mask = ng - 1;
-    const int ncol = min(C1_GC, n0 - c0);
+    const int c0 = blockIdx.y * C1_COLS, mask = ng - 1;
+    const int ncol = min(C1_COLS, n0 - c0);
     for (int i = tid; i < ng; i += blockDim.x) sC[i] = cvec[i];
-    for (int i = tid; i < C1_GC * ng; i += blockDim.x) {
-        const int q = i / ng, x = i - q * ng;
-        sGc[x][q] = q < ncol ? G[(size_t)(c0 + q) * ng + x] : 0.f;
-    }
+    for (int i = tid; i < ncol * ng; i += blockDim.x) sGc[i / ng][i % ng] = G[(size_t)c0 * ng + i];
     __syncthreads();
     // only the cells this block's targets read (targets are sorted by cell): [l0 of the first,
     // l0 of the last + MOT_W - 1], about a quarter of the grid per block
@@ -628,24 +622,16 @@ __global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, 
             nx = hi - lo + 1;
         }
     }
-    for (int t = tid; t < (C1_GC / 4) * nx; t += blockDim.x) {
-        const int cg = t & (C1_GC / 4 - 1), x = (xlo + t / (C1_GC / 4)) & mask;
-        float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int xp = 0; xp < ng; ++xp) {
-            const float c = sC[(x - xp) & mask];
-            const float4 g = *reinterpret_cast<const float4*>(&sGc[xp][4 * cg]);
-            h.x = fmaf(c, g.x, h.x);
-            h.y = fmaf(c, g.y, h.y);
-            h.z = fmaf(c, g.z, h.z);
-            h.w = fmaf(c, g.w, h.w);
-        }
-        *reinterpret_cast<float4*>(&sH[x][4 * cg]) = h;
+    for (int i = tid; i < ncol * nx; i += blockDim.x) {
+        const int q = i / nx, x = (xlo + (i - q * nx)) & mask;
+        float s = 0.f;
+        for (int xp = 0; xp < ng; ++xp) s = fmaf(sC[(x - xp) & mask], sGc[q][xp], s);
+        sH[q][x] = s;
     }
     __syncthreads();
     float mx = 0.f;
     unsigned int clamps = 0u;
     auto emit = [&](float s, int q, int i) {
-        if (q >= ncol) return;
         if (!(s >= floor_)) {
             s = floor_;
             clamps++;
@@ -657,28 +643,28 @@ __global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, 
         const int i = blockIdx.x * C1_TGT + k * blockDim.x + tid;
         if (i >= nt) break;
         float t[MOT_W];
-        int cell[MOT_W];
+        const float* hp[MOT_W];                             // column 0 of each tap's grid cell
         const int b = l0[i];
 #pragma unroll
         for (int a = 0; a < MOT_W; ++a) {
             t[a] = w[(size_t)i * MOT_W + a];
-            cell[a] = (b + a) & mask;
+            hp[a] = &sH[0][(b + a) & mask];
         }
+        if (ncol == C1_COLS) {
 #pragma unroll
-        for (int cg = 0; cg < C1_GC / 4; ++cg) {
-            float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int q = 0; q < C1_COLS; ++q) {             // constant offsets q * (128 + 1)
+                float s = 0.f;
 #pragma unroll
-            for (int a = 0; a < MOT_W; ++a) {
-                const float4 h = *reinterpret_cast<const float4*>(&sH[cell[a]][4 * cg]);
-                y.x = fmaf(h.x, t[a], y.x);
-                y.y = fmaf(h.y, t[a], y.y);
-                y.z = fmaf(h.z, t[a], y.z);
-                y.w = fmaf(h.w, t[a], y.w);
+                for (int a = 0; a < MOT_W; ++a) s = fmaf(hp[a][q * (128 + 1)], t[a], s);
+                emit(s, q, i);
             }
-            emit(y.x, 4 * cg, i);
-            emit(y.y, 4 * cg + 1, i);
-            emit(y.z, 4 * cg + 2, i);
-            emit(y.w, 4 * cg + 3, i);
+        } else {
+            for (int q = 0; q < ncol; ++q) {
+                float s = 0.f;
+#pragma unroll
+                for (int a = 0; a < MOT_W; ++a) s = fmaf(hp[a][q * (128 + 1)], t[a], s);
+                emit(s, q, i);
+            }
         }
     }
     mx = warp_max(mx);
@@ -1585,8 +1571,8 @@ cudaError_t launch_c1_batch(const float* X, const VecScale* sX, const float* phi
         const int items = nb * splits;
         k_c1_spread<<<std::min(items, 3 * 152), 256, 0, st>>>(X, sX, phi, sP, l0s, ws, ns, n0, ng, splits, G);
     } else {
-        k_c1_gather<<<dim3((nt + C1_TGT - 1) / C1_TGT, (n0 + C1_GC - 1) / C1_GC), 256, 0, st>>>(
-            G, cvec, l0t, wt, nt, n0, ng, Y, floor_, out_sc, sP, sX);
+        k_c1_gather<<<dim3((nt + C1_TGT - 1) / C1_TGT, nb), 256, 0, st>>>(G, cvec, l0t, wt, nt, n0, ng, Y, floor_,
+                                                                         out_sc, sP, sX);
     }
     return cudaGetLastError();
 }
