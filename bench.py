@@ -147,6 +147,19 @@ def algorithmic_bytes(prob, n_grid):
     return {"spread": spread, "gather": gather, "fftconv": 2 * G, "fused": spread + gather - 2 * G}
 
 
+def circle1d_launch_bytes(prob, n_grid):
+    """Bytes per launch of the batched 1-D circle kernels (one launch = the n_1 column products
+    of a batch; equal point counts; window tables excluded):
+
+    spread : the messages X (4 n_1 N) + phi (4 N) + the grid accumulation (4 n_1 n)
+    gather : the grids (4 n_1 n) + the messages Y written (4 n_1 N)
+    circle : the row dot of a scaling update reads beta_k and gamma_k (8 n_1 N) + phi^1 (4 n_1)
+    """
+    N = prob.n[0]
+    G = 4 * N * n_grid
+    return {"spread": 4 * N * N + 4 * N + G, "gather": G + 4 * N * N, "circle": 8 * N * N + 4 * N}
+
+
 def products_per_solve(prob, iters, check_every):
     """Kernel products executed by one solve: the initial backward pass, 2(K-1) per sweep and
     the K-1 forward products of each check pass."""
@@ -164,13 +177,14 @@ def kernel_source_hash(cls):
     return h.hexdigest()[:16]
 
 
-def load_traffic(cls):
-    """DRAM traffic per launch of the kernel class from the committed ncu summary, or None
-    if the kernel source changed since the counters were taken."""
+def load_traffic(cls, workload=WORKLOAD):
+    """DRAM traffic per launch of the kernel class on a workload (default sizes) from the
+    committed ncu summary, or None if there is none or the kernel source changed since the
+    counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         t = json.load(open(path))
-        e = t.get(WORKLOAD, {}).get(cls)
+        e = t.get(workload, {}).get(cls)
         if e and e.get("source_hash") == kernel_source_hash(cls):
             return e.get("dram_bytes_per_launch")
     except Exception:  # noqa: BLE001
@@ -475,12 +489,15 @@ def main():
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
     per_launch = alg.get(dom, 0.0) * prods / kls[dom]
+    if prob.topology == W.CIRCLE and prob.d == 1 and path == M.MOT_PATH_NFFT:
+        per_launch = circle1d_launch_bytes(prob, last.n_grid).get(dom, 0.0)
+        prods = kls[dom] * prob.n[0]
     achieved = per_launch / avg_s / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": load_traffic(dom),
+                "frac": achieved / peak, "traffic": load_traffic(dom, args.workload) if not args.n else None,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "avg_launch_us": avg_s * 1e6, "alg_bytes_per_launch": per_launch,
-                "alg_bytes_per_product": alg.get(dom), "products_per_launch": prods / kls[dom],
+                "alg_bytes_per_product": per_launch * kls[dom] / max(1, prods), "products_per_launch": prods / kls[dom],
                 "share": {k: round(v, 4) for k, v in share.items()}}
 
     # ---- dense comparison on the same workload -------------------------------------------

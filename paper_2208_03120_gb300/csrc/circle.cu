@@ -6,7 +6,8 @@
 // per column), done by the fast-summation or dense kernels.  The scaling updates need
 //   rowdot: raw_i = sum_c beta_k[c][i] phi^1_c gamma_k^T[c][i]      (phi^k, k >= 2)
 //   colsum: raw_c = sum_j K^{(2,1)}[c][j] phi^2_j beta_2[c][j]        (phi^1)
-// with every factor taken as its normalised mantissa (divided by its maximum).
+// with every factor taken as its normalised mantissa (divided by its maximum).  For d = 1 the
+// batched fast summation of the message matrices (k_c1_spread / k_c1_gather) is here as well.
 #include "kernels.h"
 
 namespace {
@@ -135,6 +136,228 @@ __global__ void k_pair(const float* __restrict__ phi1, const VecScale* s1, const
     }
 }
 
+
+// ------------------------------------------------------------------------------------------
+// Batched 1-D fast summation of the circle (Algorithm 3, N right-hand sides, d = 1).
+//
+// In one dimension the oversampled grid (n <= 128) is far smaller than the point sets, so a
+// batch Y[c] = K (phi (.) X[c]), c < n0, runs as two passes over the message matrices:
+//   k_c1_spread : G[c] = sum_j X[c][j] phi_j psi(u_j - .)   (32 columns per CTA, lane = column;
+//                 the point's taps are the same for every column and are broadcast)
+//   k_c1_gather : H[c] = C G[c] with the circulant C of Eq. (fastsum_mat) (c(m) = sum_{q<=M}
+//                 D_q cos(2 pi q m / n), the real part of IFFT(D FFT(.))), then
+//                 Y[c][i] = sum_a H[c][l0_i + a] psi_a(u_i) and the message epilogue
+// The window taps and base cells of every point are computed once per solve (k_c1_taps).
+// ------------------------------------------------------------------------------------------
+constexpr int C1_COLS = 32;      // columns per CTA
+constexpr int C1_CHUNK = 128;    // source points staged per step
+constexpr int C1_TGT = 512;      // targets per gather CTA (2 per thread)
+
+__global__ void k_c1_circulant(const float* __restrict__ D, int M, int n, float* __restrict__ c) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q <= M; ++q) s += (double)D[q] * cospi(2.0 * (double)((q * m) % n) / (double)n);
+        c[m] = (float)s;
+    }
+}
+
+// grid (ceil(n0 / 32), splits): CTA (b, p) spreads points [p ns / splits, (p+1) ns / splits) of
+// columns [32 b, 32 b + 32) and adds its partial grids to G (zeroed by the caller).
+__global__ void __launch_bounds__(256, 3) k_c1_spread(const float* __restrict__ X, const VecScale* sX,
+                                                   const float* __restrict__ phi, const VecScale* sP,
+                                                   const int* __restrict__ l0, const float* __restrict__ w, int ns,
+                                                   int n0, int ng, int splits, float* __restrict__ G) {
+    __shared__ float sV[C1_CHUNK][C1_COLS + 1];
+    __shared__ __align__(16) float sW[C1_CHUNK][12];
+    __shared__ int sL[C1_CHUNK];
+    __shared__ float sG[C1_COLS][128 + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int mask = ng - 1;
+    const float sx = 1.f / mx_of(sX, 0), sp = 1.f / mx_of(sP, 0);
+    const int nitems = ((n0 + C1_COLS - 1) / C1_COLS) * splits;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {   // (column group, point split)
+    const int c0 = (item / splits) * C1_COLS, sidx = item % splits;
+    const int pb = (int)((long long)sidx * ns / splits), pe = (int)((long long)(sidx + 1) * ns / splits);
+    __syncthreads();                                        // the previous item's grid is written out
+    for (int i = tid; i < C1_COLS * ng; i += blockDim.x) sG[i / ng][i % ng] = 0.f;
+    float acc[MOT_W];
+#pragma unroll
+    for (int a = 0; a < MOT_W; ++a) acc[a] = 0.f;
+    int cur = 0;
+    bool have = false;
+    auto flush = [&]() {
+#pragma unroll
+        for (int a = 0; a < MOT_W; ++a) {
+            atomicAdd(&sG[lane][(cur + a) & mask], acc[a]);
+            acc[a] = 0.f;
+        }
+    };
+    const int per_warp = C1_CHUNK / nwarps;
+    // the next chunk's loads (messages, then the points' taps) are issued before the current
+    // chunk is accumulated, so their latency overlaps the arithmetic
+    constexpr int PER = C1_COLS * C1_CHUNK / 256;
+    static_assert(C1_CHUNK <= 256, "one point per thread for the taps");
+    float v[PER], tw[MOT_W], tp = 0.f;
+    int tl = 0;
+    auto load_chunk = [&](int jb0) {
+        const int cnt0 = min(C1_CHUNK, pe - jb0);
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int idx = tid + 256 * r, q = idx / C1_CHUNK, jj = idx - q * C1_CHUNK;
+            v[r] = (jj < cnt0 && c0 + q < n0) ? __ldg(X + (size_t)(c0 + q) * ns + jb0 + jj) : 0.f;
+        }
+        if (tid < cnt0) {
+            tp = phi[jb0 + tid];
+            tl = l0[jb0 + tid];
+#pragma unroll
+            for (int a = 0; a < MOT_W; ++a) tw[a] = w[(size_t)(jb0 + tid) * MOT_W + a];
+        }
+    };
+    if (pb < pe) load_chunk(pb);
+    for (int jb = pb; jb < pe; jb += C1_CHUNK) {
+        const int cnt = min(C1_CHUNK, pe - jb);
+        __syncthreads();                                    // the previous chunk is consumed
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int idx = tid + 256 * r, q = idx / C1_CHUNK, jj = idx - q * C1_CHUNK;
+            sV[jj][q] = v[r] * sx;
+        }
+        if (tid < cnt) {
+            const float pj = tp * sp;
+            sL[tid] = tl;
+#pragma unroll
+            for (int a = 0; a < MOT_W; ++a) sW[tid][a] = tw[a] * pj;
+        }
+        __syncthreads();
+        if (jb + C1_CHUNK < pe) load_chunk(jb + C1_CHUNK);
+        const int p0 = warp * per_warp, p1 = min(cnt, p0 + per_warp);
+        for (int p = p0; p < p1; ++p) {
+            const int l = sL[p];
+            if (!have || l != cur) {                        // uniform over the warp
+                if (have) flush();
+                cur = l;
+                have = true;
+            }
+            const float v = sV[p][lane];
+            const float4 w0 = *reinterpret_cast<const float4*>(&sW[p][0]);
+            const float4 w1 = *reinterpret_cast<const float4*>(&sW[p][4]);
+            const float2 w2 = *reinterpret_cast<const float2*>(&sW[p][8]);
+            acc[0] = fmaf(v, w0.x, acc[0]);
+            acc[1] = fmaf(v, w0.y, acc[1]);
+            acc[2] = fmaf(v, w0.z, acc[2]);
+            acc[3] = fmaf(v, w0.w, acc[3]);
+            acc[4] = fmaf(v, w1.x, acc[4]);
+            acc[5] = fmaf(v, w1.y, acc[5]);
+            acc[6] = fmaf(v, w1.z, acc[6]);
+            acc[7] = fmaf(v, w1.w, acc[7]);
+            acc[8] = fmaf(v, w2.x, acc[8]);
+            acc[9] = fmaf(v, w2.y, acc[9]);
+        }
+    }
+    if (have) flush();
+    __syncthreads();
+    for (int i = tid; i < C1_COLS * ng; i += blockDim.x) {
+        const int q = i / ng, x = i - q * ng;
+        const float val = sG[q][x];
+        if (c0 + q < n0 && val != 0.f) atomicAdd(&G[(size_t)(c0 + q) * ng + x], val);
+    }
+    }   // item
+}
+
+// grid (ceil(nt / C1_TGT), ceil(n0 / 32)): convolution of 32 columns' grids, then two targets per
+// thread for each column, message epilogue (floor, maximum, clamp count) and block reduction.
+__global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, const float* __restrict__ cvec,
+                                                   const int* __restrict__ l0, const float* __restrict__ w, int nt,
+                                                   int n0, int ng, float* __restrict__ Y, float floor_,
+                                                   VecScale* out_sc, const VecScale* sA, const VecScale* sB) {
+    __shared__ float sGc[C1_COLS][128 + 1];
+    __shared__ float sH[C1_COLS][128 + 1];
+    __shared__ float sC[128];
+    __shared__ float s_mx[8];
+    __shared__ unsigned int s_cl[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c0 = blockIdx.y * C1_COLS, mask = ng - 1;
+    const int ncol = min(C1_COLS, n0 - c0);
+    for (int i = tid; i < ng; i += blockDim.x) sC[i] = cvec[i];
+    for (int i = tid; i < ncol * ng; i += blockDim.x) sGc[i / ng][i % ng] = G[(size_t)c0 * ng + i];
+    __syncthreads();
+    // only the cells this block's targets read (targets are sorted by cell): [l0 of the first,
+    // l0 of the last + MOT_W - 1], about a quarter of the grid per block
+    int xlo = 0, nx = ng;
+    {
+        const int i_first = blockIdx.x * C1_TGT, i_last = min(nt, i_first + C1_TGT) - 1;
+        const int lo = l0[i_first], hi = l0[i_last] + MOT_W - 1;
+        if (hi - lo + 1 < ng) {
+            xlo = lo;
+            nx = hi - lo + 1;
+        }
+    }
+    for (int i = tid; i < ncol * nx; i += blockDim.x) {
+        const int q = i / nx, x = (xlo + (i - q * nx)) & mask;
+        float s = 0.f;
+        for (int xp = 0; xp < ng; ++xp) s = fmaf(sC[(x - xp) & mask], sGc[q][xp], s);
+        sH[q][x] = s;
+    }
+    __syncthreads();
+    float mx = 0.f;
+    unsigned int clamps = 0u;
+    auto emit = [&](float s, int q, int i) {
+        if (!(s >= floor_)) {
+            s = floor_;
+            clamps++;
+        }
+        mx = fmaxf(mx, s);
+        Y[(size_t)(c0 + q) * nt + i] = s;
+    };
+    for (int k = 0; k < C1_TGT / 256; ++k) {
+        const int i = blockIdx.x * C1_TGT + k * blockDim.x + tid;
+        if (i >= nt) break;
+        float t[MOT_W];
+        const float* hp[MOT_W];                             // column 0 of each tap's grid cell
+        const int b = l0[i];
+#pragma unroll
+        for (int a = 0; a < MOT_W; ++a) {
+            t[a] = w[(size_t)i * MOT_W + a];
+            hp[a] = &sH[0][(b + a) & mask];
+        }
+        if (ncol == C1_COLS) {
+#pragma unroll
+            for (int q = 0; q < C1_COLS; ++q) {             // constant offsets q * (128 + 1)
+                float s = 0.f;
+#pragma unroll
+                for (int a = 0; a < MOT_W; ++a) s = fmaf(hp[a][q * (128 + 1)], t[a], s);
+                emit(s, q, i);
+            }
+        } else {
+            for (int q = 0; q < ncol; ++q) {
+                float s = 0.f;
+#pragma unroll
+                for (int a = 0; a < MOT_W; ++a) s = fmaf(hp[a][q * (128 + 1)], t[a], s);
+                emit(s, q, i);
+            }
+        }
+    }
+    mx = warp_max(mx);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) clamps += __shfl_xor_sync(0xffffffffu, clamps, o);
+    if (lane == 0) {
+        s_mx[warp] = mx;
+        s_cl[warp] = clamps;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float m = 0.f;
+        unsigned int c = 0u;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            m = fmaxf(m, s_mx[k]);
+            c += s_cl[k];
+        }
+        out_sc->ls = sA->ls + (double)logf(mx_of(sA, 0)) + sB->ls + (double)logf(mx_of(sB, 0));
+        atomic_max_pos(&out_sc->mx_bits, m);
+        if (c) atomicAdd(&out_sc->clamped, c);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_close_points(const float* x, const int* perm, int n, int d, const double* c, double s, int n_grid,
@@ -174,5 +397,32 @@ cudaError_t launch_kernel_matrix(const float* ui, int ni, const float* uc, int n
     long long total = (long long)ni * nc;
     int blocks = (int)std::min<long long>((total + 255) / 256, 8192);
     k_kernel_matrix<<<blocks, 256, 0, st>>>(ui, ni, uc, nc, d, eta_u, K, sc);
+    return cudaGetLastError();
+}
+
+bool c1_supported(int d, int n) { return d == 1 && n >= 16 && n <= 128; }
+
+cudaError_t launch_c1_circulant(const float* D, int M, int n, float* c, cudaStream_t st) {
+    k_c1_circulant<<<1, 128, 0, st>>>(D, M, n, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_c1_batch(const float* X, const VecScale* sX, const float* phi, const VecScale* sP, const int* l0s,
+                            const float* ws, int ns, const int* l0t, const float* wt, int nt, int n0, int ng,
+                            const float* cvec, float* G, float* Y, float floor_, VecScale* out_sc, cudaStream_t st,
+                            int stage) {
+    const int nb = (n0 + C1_COLS - 1) / C1_COLS;
+    if (stage == 0) {
+        cudaError_t e = cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n0 * ng, st);
+        if (e != cudaSuccess) return e;
+        // work items (column group, point split); a grid of at most one wave of resident CTAs (three
+        // per SM at 80 registers and 40 KB of shared memory) loops over them
+        const int splits = std::max(1, std::min(std::min(8, std::max(1, (3 * 152) / nb)), std::max(1, ns / C1_CHUNK)));
+        const int items = nb * splits;
+        k_c1_spread<<<std::min(items, 3 * 152), 256, 0, st>>>(X, sX, phi, sP, l0s, ws, ns, n0, ng, splits, G);
+    } else {
+        k_c1_gather<<<dim3((nt + C1_TGT - 1) / C1_TGT, nb), 256, 0, st>>>(G, cvec, l0t, wt, nt, n0, ng, Y, floor_,
+                                                                         out_sc, sP, sX);
+    }
     return cudaGetLastError();
 }
