@@ -11,7 +11,7 @@ Paper passages followed (Section 5):
   * Eq. (fastsum-sum)  direct summation beta = K alpha
   * Eqs. (ndft), (ndft*), (fastsum_mat), Algorithm 4: beta ~ F_k(kappa_hat * F*_l alpha)
 
-Readings of passages that are garbled or silent (each also listed in the design doc):
+Readings of passages that are garbled or silent:
   * Hermite conditions of kappa_B: the printed rule gives p or 2p-1 conditions
     for a degree-p polynomial, which cannot hold together.  The reading that
     reproduces the printed Fig. 3 polynomial is: kappa_B has degree 2p,

@@ -20,7 +20,7 @@ problem's edge list may use any labels; :func:`tree_structure` relabels by
 breadth-first search from the root so that p(k) < k, as the paper assumes
 without loss of generality.
 
-Readings (also listed in the design doc):
+Readings of passages that are silent or ambiguous:
   * Initial scalings phi^(0) = 1 (the paper leaves the value open).
   * Algorithm 1 increments r inside the loop over k; the reading is one
     increment per sweep over all K marginals.
