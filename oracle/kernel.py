@@ -10,6 +10,9 @@ Paper passages followed (Section 5):
   * Eq. (fft)          Fourier coefficients kappa_hat(m), m in {-M..M-1}^d
   * Eq. (fastsum-sum)  direct summation beta = K alpha
   * Eqs. (ndft), (ndft*), (fastsum_mat), Algorithm 4: beta ~ F_k(kappa_hat * F*_l alpha)
+  * Section 6.1, closing remark: for very small eta the sum of Eq. (fastsum-sum)
+    may simply be truncated to nearby pairs (``truncated_sum``); the same sum
+    in log-sum-exp form (``log_kernel_sum``) serves Sinkhorn in the log domain
 
 Readings of passages that are garbled or silent:
   * Hermite conditions of kappa_B: the printed rule gives p or 2p-1 conditions
@@ -150,6 +153,53 @@ def direct_sum(x_tgt, x_src, alpha, eta: float, block: int = 2048) -> np.ndarray
         diff = xt[s:s + block, None, :] - xs[None, :, :]
         Kb = np.exp(-(diff * diff).sum(axis=-1) / eta)
         out[s:s + block] = Kb @ a
+    return out
+
+
+def truncated_sum(x_tgt, x_src, alpha, eta: float, r_cut: float, block: int = 2048) -> np.ndarray:
+    """Eq. (fastsum-sum) with every term of ||x_i - y_j|| > r_cut left out, FP64.
+
+    The truncation the paper suggests for very small eta, where the kernel is
+    concentrated near zero.  Each left-out term is at most exp(-r_cut^2/eta)
+    |alpha_j|, so |truncated - direct| <= exp(-r_cut^2/eta) sum_j |alpha_j|.
+    """
+    xt = _as2d(x_tgt)
+    xs = _as2d(x_src)
+    a = np.asarray(alpha, dtype=np.float64)
+    out = np.empty((xt.shape[0],) + a.shape[1:])
+    r2 = float(r_cut) * float(r_cut)
+    for s in range(0, xt.shape[0], block):
+        diff = xt[s:s + block, None, :] - xs[None, :, :]
+        d2 = (diff * diff).sum(axis=-1)
+        Kb = np.where(d2 <= r2, np.exp(-d2 / eta), 0.0)
+        out[s:s + block] = Kb @ a
+    return out
+
+
+def log_kernel_sum(x_tgt, x_src, log_v, eta: float, r_cut: float | None = None, block: int = 2048) -> np.ndarray:
+    """log beta_i = log sum_j exp(log_v_j - ||x_i - y_j||^2 / eta), FP64.
+
+    Eq. (fastsum-sum) with positive weights v_j = exp(log_v_j) held as their
+    logarithms: each target's exponents are shifted by their maximum before
+    summing (log-sum-exp), so no term overflows or underflows to an all-zero
+    sum.  With ``r_cut`` only the pairs with ||x_i - y_j|| <= r_cut enter
+    (``truncated_sum`` in log form).  -inf where no term is left.
+    """
+    xt = _as2d(x_tgt)
+    xs = _as2d(x_src)
+    lv = np.asarray(log_v, dtype=np.float64)
+    out = np.empty(xt.shape[0])
+    for s in range(0, xt.shape[0], block):
+        diff = xt[s:s + block, None, :] - xs[None, :, :]
+        d2 = (diff * diff).sum(axis=-1)
+        E = lv[None, :] - d2 / eta
+        if r_cut is not None:
+            E = np.where(d2 <= float(r_cut) * float(r_cut), E, -np.inf)
+        m = np.max(E, axis=1)
+        finite = np.isfinite(m)
+        shift = np.where(finite, m, 0.0)
+        with np.errstate(divide="ignore"):
+            out[s:s + block] = np.where(finite, shift + np.log(np.exp(E - shift[:, None]).sum(axis=1)), -np.inf)
     return out
 
 

@@ -14,6 +14,8 @@ Paper passages followed:
     recursions and Algorithm 3.
   * Section 6.3 (generalised Euler flows): the circle whose closing edge
     {K, 1} compares x^K with sigma(x^1), and the pair marginals Pi_{1,k}.
+  * Section 6.1, closing remark (small eta): Algorithm 2 in the log domain,
+    optionally with every kernel sum truncated to nearby pairs.
 
 Conventions: node labels are 0-based (the paper's node 1 is label 0).  A
 problem's edge list may use any labels; :func:`tree_structure` relabels by
@@ -33,13 +35,14 @@ Readings of passages that are silent or ambiguous:
 """
 from __future__ import annotations
 
+import math
 from collections import deque
 from dataclasses import dataclass, field
 from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 
-from .kernel import kernel_matrix, direct_sum
+from .kernel import kernel_matrix, direct_sum, log_kernel_sum
 
 
 # ---------------------------------------------------------------------------
@@ -278,6 +281,121 @@ def tree_marginals(x, phi, edges, eta, root: int = 0, edge_w=None) -> List[np.nd
         gamma[k] = ts.compute_gamma(ph, beta, gamma, k)
     P = [ph[k] * gamma[k] * ts.beta_prod(beta, k) for k in range(ts.K)]
     return ts.to_user(P)
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 2 in the log domain (small eta, truncated kernel sums)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class LogSolveResult:
+    logphi: List[np.ndarray]            # log phi^k in the caller's labels
+    S: List[float] = field(default_factory=list)
+    iters: int = 0
+
+
+def _logsumexp(v: np.ndarray) -> float:
+    m = float(np.max(v))
+    if not np.isfinite(m):
+        return m
+    return m + math.log(float(np.exp(v - m).sum()))
+
+
+class TreeSinkhornLog:
+    """Algorithm 2 with every scaling and message held as its logarithm, FP64.
+
+    f^k = log phi^k, b_k = log beta_k, g_k = log gamma_k.  Each kernel product
+    of Algorithm 2 becomes a log-sum-exp (``log_kernel_sum``), each
+    element-wise product a sum and each quotient a difference, in the same
+    order, so the iterates are those of ``TreeSinkhorn`` wherever both are
+    representable.  For small eta the scalings grow like exp(+-cost / eta) and
+    leave the floating-point range; their logarithms do not.  ``r_cut``
+    truncates every kernel sum to the pairs within that distance, the
+    truncation the paper suggests for very small eta.
+    """
+
+    def __init__(self, x: Sequence[np.ndarray], mu: Sequence[np.ndarray], edges, eta: float,
+                 root: int = 0, edge_w=None, r_cut: Optional[float] = None):
+        self.K = len(x)
+        self.tree = tree_structure(self.K, edges, root, edge_w)
+        t = self.tree
+        self.eta = float(eta)
+        self.x = [np.asarray(x[t.order[k]], dtype=np.float64).reshape(len(x[t.order[k]]), -1)
+                  for k in range(self.K)]
+        self.mu = [np.asarray(mu[t.order[k]], dtype=np.float64) for k in range(self.K)]
+        with np.errstate(divide="ignore"):
+            self.logmu = [np.log(m) for m in self.mu]
+        self.n = [xi.shape[0] for xi in self.x]
+        self.r_cut = r_cut
+        # kernel exp(-w ||.||^2 / eta) of edge {p(k), k} as exp(-||.||^2 / eta_e)
+        self.eta_e = [None] + [self.eta / t.weight[k] if t.weight[k] != 0 else np.inf for k in range(1, self.K)]
+
+    def _sum_b(self, b, k, exclude=None):
+        """log beta^{(.) U}, U = C_k minus ``exclude``."""
+        out = np.zeros(self.n[k])
+        for t in self.tree.children[k]:
+            if t != exclude:
+                out = out + b[t]
+        return out
+
+    def compute_b(self, f, b, k):
+        """log beta_k = log K^{(p(k),k)} exp(f^k + log beta^{(.) C_k}) (Algorithm 2, step 4)."""
+        p = self.tree.parent[k]
+        return log_kernel_sum(self.x[p], self.x[k], f[k] + self._sum_b(b, k), self.eta_e[k], self.r_cut)
+
+    def compute_g(self, f, b, g, k):
+        """log gamma_k = log (K^{(p(k),k)})^T exp(f^{p(k)} + log gamma_{p(k)} + log beta^{(.) C_{p(k)} minus k})."""
+        p = self.tree.parent[k]
+        return log_kernel_sum(self.x[k], self.x[p], f[p] + g[p] + self._sum_b(b, p, exclude=k), self.eta_e[k],
+                              self.r_cut)
+
+    def to_user(self, vecs):
+        out = [None] * self.K
+        for k in range(self.K):
+            out[self.tree.order[k]] = vecs[k]
+        return out
+
+    def from_user(self, vecs):
+        return [np.asarray(vecs[self.tree.order[k]], dtype=np.float64) for k in range(self.K)]
+
+    def init_b(self, f):
+        b = [None] * self.K
+        for k in range(self.K - 1, 0, -1):
+            b[k] = self.compute_b(f, b, k)
+        return b
+
+    def run(self, iters: int, logphi0=None, callback=None) -> LogSolveResult:
+        K = self.K
+        f = [np.zeros(n) for n in self.n] if logphi0 is None else self.from_user(logphi0)
+        b = self.init_b(f)                                            # steps 3-5
+        S_trace = []
+        for r in range(iters):
+            g = [None] * K
+            fn = [None] * K
+            for k in range(K):                                       # steps 7-13
+                g[k] = np.zeros(self.n[0]) if k == 0 else self.compute_g(fn, b, g, k)
+                fn[k] = self.logmu[k] - g[k] - self._sum_b(b, k)
+            mass = math.exp(_logsumexp(f[0] + self._sum_b(b, 0)))   # mass of K (.) Phi^(r)
+            S = self.eta * (sum(float(np.sum(np.where(m > 0, m * fk, 0.0))) for m, fk in zip(self.mu, f)) - mass)
+            for k in range(K - 1, 0, -1):                            # steps 14-15
+                b[k] = self.compute_b(fn, b, k)
+            f = fn
+            S_trace.append(S)
+            if callback is not None:
+                callback(r + 1, self.to_user(f))
+        return LogSolveResult(self.to_user(f), S_trace, iters)
+
+
+def tree_marginals_log(x, logphi, edges, eta, root: int = 0, edge_w=None, r_cut: Optional[float] = None):
+    """Theorem 4.1 in the log domain: log P_k = f^k + log gamma_k + log beta^{(.) C_k}, for any
+    f = log phi (caller labels in and out); with ``r_cut`` the marginals of the truncated kernel."""
+    ts = TreeSinkhornLog(x, [np.ones(len(a)) for a in x], edges, eta, root, edge_w, r_cut)
+    f = ts.from_user(logphi)
+    b = ts.init_b(f)
+    g = [np.zeros(ts.n[0])] + [None] * (ts.K - 1)
+    for k in range(1, ts.K):
+        g[k] = ts.compute_g(f, b, g, k)
+    return ts.to_user([f[k] + g[k] + ts._sum_b(b, k) for k in range(ts.K)])
 
 
 # ---------------------------------------------------------------------------
