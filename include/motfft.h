@@ -113,6 +113,11 @@ typedef struct {
                            period 2*tau = 1 [1/16]                                             */
     int use_graphs;     /* 1 = replay iterations as a CUDA graph, -1 = plain launches [1]      */
     int timing;         /* 1 = time every kernel class with CUDA events (slower) [0]          */
+    int wavefront;      /* trees on the fused 2-D path: 1 = pipeline the sweeps of each stop-test
+                           chunk (up to 32 sweeps) as a wavefront, each launch taking every kernel
+                           product whose inputs are ready, from several sweeps; the same
+                           products on the same inputs as the sweep-by-sweep order (Algorithm 2);
+                           -1 = sweep by sweep [1]                                              */
 } mot_options;
 
 /* Fill *o with the defaults. */

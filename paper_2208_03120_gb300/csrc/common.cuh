@@ -99,6 +99,8 @@ struct Task {
     int save_prev;               // keep ls / mx in ls_prev / mx_prev before the reset
     double* zero_d;              // doubles to zero
     int zero_n;
+    int iter_off;                // this task's sweep is the counter minus iter_off (sweeps of a
+                                 // pipelined chunk share one counter value)
 };
 
 __device__ __forceinline__ float mx_of(const VecScale* s, int use_prev) {

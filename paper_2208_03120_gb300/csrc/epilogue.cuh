@@ -163,7 +163,7 @@ __device__ __forceinline__ void load_task_consts(const Task& T, const Globals& G
         pre.ls_phi_k = ls_of(T.phi_sc, 0);
         pre.Lold = ls_of(T.phi_sc, 1) + (double)logf(mx_of(T.phi_sc, 1));
         pre.inv_mx_old = 1.f / mx_of(T.phi_sc, 1);
-        pre.iter = G.iter ? *G.iter : 0;
+        pre.iter = (G.iter ? *G.iter : 0) - T.iter_off;
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -39,6 +39,7 @@ cudaError_t prepare_fused2d();
 bool fused2d_supported(int d, int n);
 int fused2d_max_points();     // largest point set per product the fused kernel takes
 int fused2d_cluster_size();
+int fused2d_max_active_clusters();   // co-resident clusters of the fused kernel (0 before set-up)
 // msg_only: every task is a message product with a kernel sum (lean instance).
 cudaError_t launch_fused2d(const Task* tasks, int ntask, const Globals& G, cudaStream_t st, bool msg_only);
 // Batched 1-D fast summation of the circle (grids n <= 128): per-point window taps and base cells

@@ -860,14 +860,18 @@ __global__ void k_prologue(VecScale* const* __restrict__ list, int nlist, int sa
         s->clamped = 0u;
     }
     for (int i = t; i < zero_n; i += blockDim.x) zero_d[i] = 0.0;
-    if (bump && t == 0) {
-        const int it = *G.iter + 1;
-        *G.iter = it;
-        IterAcc* a = G.acc + ((it + 1) % G.R);
-        a->logphi = 0.0;
-        a->mass = 0.0;
-        a->rootviol = 0.0;
-        a->pad = 0.0;
+    // advance the sweep counter by `bump` sweeps and clear their accumulator slots: sweep s adds
+    // its scalings' logarithms to slot s + 1 and its root mass to slot s
+    if (bump > 0 && t == 0) {
+        const int old = *G.iter;
+        *G.iter = old + bump;
+        for (int s = 1; s <= bump; ++s) {
+            IterAcc* a = G.acc + ((old + s + 1) % G.R);
+            a->logphi = 0.0;
+            a->mass = 0.0;
+            a->rootviol = 0.0;
+            a->pad = 0.0;
+        }
     }
 }
 
@@ -1183,6 +1187,8 @@ cudaError_t launch_fftconv(int d, const Task* tasks, int ntask, const Globals& G
 namespace {
 // cluster size of the fused kernel per device: 0 not yet probed, -1 no cluster fits
 int g_cluster_size[kMaxDevices] = {};
+// clusters of the fused kernel that fit on the GPU at once (cudaOccupancyMaxActiveClusters)
+int g_cluster_active[kMaxDevices] = {};
 
 int current_device() {
     int dev = 0;
@@ -1192,6 +1198,7 @@ int current_device() {
 }
 
 int fused2d_cluster_size() { return g_cluster_size[current_device()]; }
+int fused2d_max_active_clusters() { return g_cluster_active[current_device()]; }
 
 bool fused2d_supported(int d, int n) {
     return d == 2 && n >= 16 && n <= F2_N && g_cluster_size[current_device()] > 0;
@@ -1225,6 +1232,7 @@ cudaError_t prepare_fused2d() {
         int nclusters = 0;
         e = cudaOccupancyMaxActiveClusters(&nclusters, k_fastsum2d<false>, &cfg);
         if (e == cudaSuccess && nclusters > 0) {
+            g_cluster_active[current_device()] = nclusters;
             csz = cs;
             return cudaSuccess;
         }

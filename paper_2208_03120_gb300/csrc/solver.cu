@@ -137,6 +137,7 @@ void fill_defaults(mot_options& o, const mot_options* in) {
     if (o.p <= 0) o.p = 3;
     if (o.eps_B <= 0.0) o.eps_B = 1.0 / 16.0;
     if (o.use_graphs == 0) o.use_graphs = 1;
+    if (o.wavefront == 0) o.wavefront = 1;
 }
 
 // =============================================================================================
@@ -295,6 +296,20 @@ struct TreePlan {
     size_t it_reset0 = 0, it_reset_n = 0;     // iteration prologue: phi (prev kept) and gamma records
     size_t ck_reset0 = 0, ck_reset_n = 0;     // check prologue: gamma-ex records (+ acc_node zeroed)
     bool fused = false;                        // 2-D grids <= 64: one cluster kernel per level
+    // wavefront schedule (fused path): beta_k alternates between two copies from sweep to sweep
+    std::vector<float*> beta2;                 // the second copy of every beta_k
+    std::vector<Level> chk1;                   // check pass reading the second copy
+    bool wave = false;
+    int par = 0;                               // copy holding the latest beta, in enqueue order
+    std::vector<Level> wlev;                   // the launches of one chunk
+    int wave_S = -1, wave_q0 = -1;             // chunk length and starting copy of wlev
+    size_t fac_base = 0, res_base = 0;         // where the chunk's factors / resets start
+    size_t fac_cap = 0, res_cap = 0;
+    Task* d_wtasks = nullptr;
+    size_t wtask_cap = 0;
+    int graph_par = -1;                        // starting copy of the captured chunk
+    size_t wave_root_reset = 0;                // reset-list entry of the root's scale record
+    long long launches_per_chunk = 0;
     Globals G;
     // graph
     cudaGraphExec_t gexec = nullptr;
@@ -305,7 +320,11 @@ struct TreePlan {
     VecScale* beta_sc(int k) const { return sc + K + k; }
     VecScale* gam_sc(int k) const { return sc + 2 * K + k; }
     VecScale* gex_sc(int k) const { return sc + 3 * K + k; }
+    VecScale* beta_sc_q(int k, int q) const { return q ? sc + 4 * K + k : sc + K + k; }
+    float* beta_q(int k, int q) const { return q ? beta2[k] : beta[k]; }
 };
+
+constexpr int kWaveMax = 32;                   // longest chunk pipelined as one wavefront
 
 int validate_problem(const mot_problem* P) {
     if (!P) return MOT_EINVAL;
@@ -420,6 +439,7 @@ void layout_tree(Arena& A, TreePlan& T) {
     for (int k = 0; k < K; ++k) layout_set(A, T.sets[k], T.n[k], d, ng, true);
     T.phi.assign(K, nullptr);
     T.beta.assign(K, nullptr);
+    T.beta2.assign(K, nullptr);
     T.gam.assign(K, nullptr);
     T.gex.assign(K, nullptr);
     T.grid.assign(K, nullptr);
@@ -433,6 +453,7 @@ void layout_tree(Arena& A, TreePlan& T) {
     for (int k = 1; k < K; ++k) {
         const int p = T.parent[k];
         T.beta[k] = A.take<float>(T.n[p]);
+        T.beta2[k] = A.take<float>(T.n[p]);
         T.gam[k] = A.take<float>(T.n[k]);
         T.gex[k] = A.take<float>(T.n[k]);
         if (nfft) {
@@ -446,8 +467,8 @@ void layout_tree(Arena& A, TreePlan& T) {
             T.rawc[k] = A.take<float>(T.n[k]);
         }
     }
-    // readback region
-    size_t stats = sizeof(IterAcc) * kRing + sizeof(double) * 3 * K + sizeof(VecScale) * 4 * K + 16;
+    // readback region (scale records: phi, beta, gamma, gamma-ex, second beta copy)
+    size_t stats = sizeof(IterAcc) * kRing + sizeof(double) * 3 * K + sizeof(VecScale) * 5 * K + 16;
     T.stats_begin = A.take<char>(stats);
     T.stats_bytes = stats;
     if (!A.measure) {
@@ -465,11 +486,16 @@ void layout_tree(Arena& A, TreePlan& T) {
         T.dscr_a = A.take<double>(s);
         T.dscr_b = A.take<double>(s);
     }
-    // factor, reset and task arrays: generous upper bounds
-    const size_t maxfac = (size_t)16 * K + 8 * (size_t)K * 4;
-    T.d_fac = A.take<Factor>(maxfac + 64 * (size_t)K);
-    T.d_resets = A.take<VecScale*>(8 * (size_t)K + 8);
-    T.d_tasks = A.take<Task>(16 * (size_t)K + 16);
+    // factor, reset and task arrays: generous upper bounds for the sweep-by-sweep levels and the
+    // check passes, plus one wavefront chunk (per sweep at most 2 (K - 1) + 1 tasks, 6 K factors
+    // and 3 K + 1 resets)
+    T.fac_cap = (size_t)16 * K + 8 * (size_t)K * 4 + 64 * (size_t)K + (size_t)kWaveMax * 6 * K;
+    T.res_cap = 8 * (size_t)K + 8 + (size_t)kWaveMax * (3 * (size_t)K + 1);
+    T.d_fac = A.take<Factor>(T.fac_cap);
+    T.d_resets = A.take<VecScale*>(T.res_cap);
+    T.d_tasks = A.take<Task>(24 * (size_t)K + 16);
+    T.wtask_cap = (size_t)kWaveMax * (2 * (size_t)K + 1);
+    T.d_wtasks = A.take<Task>(T.wtask_cap);
 }
 
 // ---- task construction ------------------------------------------------------------------
@@ -493,21 +519,22 @@ PointSet ps_of(const TreePlan& T, int k) { return pointset_of(T.sets[k]); }
 
 // Source side of the message from node `src` towards neighbour `dst`, built from the current
 // scalings: phi^src (.) [gamma-ex_src] (.) prod of the children's beta except dst.
-void src_general(TreePlan& T, Task& t, int src, int exclude_child, bool with_phi, int gamma_kind) {
+// `q` selects the copy of the children's beta (the wavefront alternates two copies).
+void src_general(TreePlan& T, Task& t, int src, int exclude_child, bool with_phi, int gamma_kind, int q = 0) {
     t.src = ps_of(T, src);
     t.sf0 = (int)T.fac.size();
     if (with_phi && !T.free_[src]) add_factor(T, T.phi[src], T.phi_sc(src), 0);
     if (gamma_kind == 1 && src != 0) add_factor(T, T.gam[src], T.gam_sc(src), 0);
     if (gamma_kind == 2 && src != 0) add_factor(T, T.gex[src], T.gex_sc(src), 0);
     for (int c : T.children[src])
-        if (c != exclude_child) add_factor(T, T.beta[c], T.beta_sc(c), 0);
+        if (c != exclude_child) add_factor(T, T.beta_q(c, q), T.beta_sc_q(c, q), 0);
     t.snf = (int)T.fac.size() - t.sf0;
 }
 
-void tgt_children(TreePlan& T, Task& t, int k, bool with_phi) {
+void tgt_children(TreePlan& T, Task& t, int k, bool with_phi, int q = 0) {
     t.tf0 = (int)T.fac.size();
     if (with_phi && !T.free_[k]) add_factor(T, T.phi[k], T.phi_sc(k), 0);
-    for (int c : T.children[k]) add_factor(T, T.beta[c], T.beta_sc(c), 0);
+    for (int c : T.children[k]) add_factor(T, T.beta_q(c, q), T.beta_sc_q(c, q), 0);
     t.tnf = (int)T.fac.size() - t.tf0;
 }
 
@@ -605,44 +632,50 @@ void build_tasks(TreePlan& T) {
         T.bwd[lev].tgt.push_back(t);
     }
 
-    // ---- check pass: exact marginals at the current scalings (Theorem 4.1) ----------------
-    T.chk.assign(std::max(maxdepth, 1), Level());
-    for (int k = 1; k < K; ++k) {
-        const int p = T.parent[k];
-        Task t = blank_task();
-        src_general(T, t, p, k, true, 2);
-        edge_grids(T, t, k, T.rawc[k]);
-        t.tgt = ps_of(T, k);
-        t.mode = EPI_MARG;
-        tgt_children(T, t, k, true);
-        t.mu_d = T.free_[k] ? nullptr : T.sets[k].mu_d;
-        t.out = T.gex[k];
-        t.out_sc = T.gex_sc(k);
-        t.phi = T.phi[k];
-        t.phi_sc = T.phi_sc(k);
-        t.acc_node = T.acc_node + 3 * k;
-        T.chk[T.depth[k] - 1].src.push_back(t);
-        T.chk[T.depth[k] - 1].tgt.push_back(t);
-    }
-    {
+    // ---- check pass: exact marginals at the current scalings (Theorem 4.1), for either copy
+    // of beta ----------------------------------------------------------------------------------
+    for (int q = 0; q < 2; ++q) {
+        std::vector<Level>& chk = q ? T.chk1 : T.chk;
+        chk.assign(std::max(maxdepth, 1), Level());
+        for (int k = 1; k < K; ++k) {
+            const int p = T.parent[k];
+            Task t = blank_task();
+            src_general(T, t, p, k, true, 2, q);
+            edge_grids(T, t, k, T.rawc[k]);
+            t.tgt = ps_of(T, k);
+            t.mode = EPI_MARG;
+            tgt_children(T, t, k, true, q);
+            t.mu_d = T.free_[k] ? nullptr : T.sets[k].mu_d;
+            t.out = T.gex[k];
+            t.out_sc = T.gex_sc(k);
+            t.phi = T.phi[k];
+            t.phi_sc = T.phi_sc(k);
+            t.acc_node = T.acc_node + 3 * k;
+            chk[T.depth[k] - 1].src.push_back(t);
+            chk[T.depth[k] - 1].tgt.push_back(t);
+        }
         Task t = blank_task();
         t.tgt = ps_of(T, 0);
         t.mode = EPI_MARG;
-        tgt_children(T, t, 0, true);
+        tgt_children(T, t, 0, true, q);
         t.mu_d = T.free_[0] ? nullptr : T.sets[0].mu_d;
         t.phi = T.phi[0];
         t.phi_sc = T.phi_sc(0);
         t.acc_node = T.acc_node;
-        T.chk[0].tgt.push_back(t);
-        T.ck_reset0 = T.resets.size();
-        for (int k = 1; k < K; ++k) T.resets.push_back(T.gex_sc(k));
-        T.ck_reset_n = T.resets.size() - T.ck_reset0;
+        chk[0].tgt.push_back(t);
     }
+    T.ck_reset0 = T.resets.size();
+    for (int k = 1; k < K; ++k) T.resets.push_back(T.gex_sc(k));
+    T.ck_reset_n = T.resets.size() - T.ck_reset0;
 }
 
 // Copy task arrays to the device, resolving reset-list offsets to device pointers.
 int upload_tasks(TreePlan& T, cudaStream_t st) {
-    if (T.fac.size() > (size_t)16 * T.K + 8 * (size_t)T.K * 4 + 64 * (size_t)T.K) return MOT_EUNSUPPORTED;
+    if (T.fac.size() > T.fac_cap - (size_t)kWaveMax * 6 * T.K) return MOT_EUNSUPPORTED;
+    if (T.resets.size() > T.res_cap - (size_t)kWaveMax * (3 * (size_t)T.K + 1)) return MOT_EUNSUPPORTED;
+    T.fac_base = T.fac.size();
+    T.res_base = T.resets.size();
+    T.wave_S = T.wave_q0 = -1;
     CK(cudaMemcpyAsync(T.d_fac, T.fac.data(), sizeof(Factor) * T.fac.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(T.d_resets, T.resets.data(), sizeof(VecScale*) * T.resets.size(), cudaMemcpyHostToDevice, st));
     std::vector<Task> all;
@@ -659,18 +692,16 @@ int upload_tasks(TreePlan& T, cudaStream_t st) {
     place(T.fwd);
     place(T.bwd);
     place(T.chk);
-    std::vector<std::pair<Level*, int>> slots;
-    for (auto* lv : {&T.fwd, &T.bwd, &T.chk})
+    place(T.chk1);
+    for (auto* lv : {&T.fwd, &T.bwd, &T.chk, &T.chk1})
         for (auto& L : *lv) {
-            slots.push_back({&L, 0});
             for (auto& t : L.src) all.push_back(t);
-            slots.push_back({&L, 1});
             for (auto& t : L.tgt) all.push_back(t);
         }
-    if (all.size() > 16 * (size_t)T.K + 16) return MOT_EUNSUPPORTED;
+    if (all.size() > 24 * (size_t)T.K + 16) return MOT_EUNSUPPORTED;
     CK(cudaMemcpyAsync(T.d_tasks, all.data(), sizeof(Task) * all.size(), cudaMemcpyHostToDevice, st));
     size_t off = 0;
-    for (auto* lv : {&T.fwd, &T.bwd, &T.chk})
+    for (auto* lv : {&T.fwd, &T.bwd, &T.chk, &T.chk1})
         for (auto& L : *lv) {
             L.d_src = T.d_tasks + off;
             off += L.src.size();
@@ -700,6 +731,160 @@ int upload_tasks(TreePlan& T, cudaStream_t st) {
     T.G.n_grid = T.g.n;
     T.G.M = T.g.M;
     T.G.fac = T.d_fac;
+    return MOT_OK;
+}
+
+// ---- wavefront chunk --------------------------------------------------------------------------
+// Sweep s of a chunk (s = 0..S-1) reads the copy q_s = (q0 + s) mod 2 of every beta and writes the
+// other copy.  With the forward identity above, the products of Algorithm 2 depend on
+//   F_k(s) (gamma_k, then phi^k)  <- B_k(s-1) and B_c(s-1) for the children c of k
+//   R(s)   (root update)          <- B_c(s-1) for the children of the root
+//   B_k(s) (beta_k)               <- F_k(s) and B_c(s)
+// and, as a copy is rewritten every second sweep, B_k(s) also waits for the readers of the copy it
+// overwrites in sweep s-1: F_k(s-1) and F_{p(k)}(s-1), or R(s-1) when p(k) is the root.  Every
+// product goes into the first launch after its inputs that has room.  The scale record of the root
+// scaling is saved and reset (R(s) reads the previous one) by a product that runs between R(s-1)
+// and R(s), and by the chunk prologue for s = 0.
+int build_wave(TreePlan& T, int S, int q0, cudaStream_t st) {
+    const int K = T.K;
+    T.fac.resize(T.fac_base);
+    T.resets.resize(T.res_base);
+    std::vector<std::vector<int>> tB(S, std::vector<int>(K, -1)), tF(S, std::vector<int>(K, -1));
+    std::vector<int> tR(S, -1);
+    auto prevB = [&](int s, int k) { return s > 0 ? tB[s - 1][k] : -1; };
+    // a launch takes at most as many products as clusters fit on the GPU at once (one more would
+    // run as a second wave); a product that finds its first possible launch full takes the next
+    const int cap = std::max(1, fused2d_max_active_clusters() > 0 ? fused2d_max_active_clusters() : 8);
+    std::vector<int> load;
+    auto place = [&](int ready) {
+        int t = ready;
+        while (t < (int)load.size() && load[t] >= cap) ++t;
+        if (t >= (int)load.size()) load.resize(t + 1, 0);
+        load[t] += 1;
+        return t;
+    };
+    for (int s = 0; s < S; ++s) {
+        int r = -1;
+        for (int c : T.children[0]) r = std::max(r, prevB(s, c));
+        tR[s] = place(r + 1);
+        for (int k = 1; k < K; ++k) {
+            int t = prevB(s, k);
+            for (int c : T.children[k]) t = std::max(t, prevB(s, c));
+            tF[s][k] = place(t + 1);
+        }
+        for (int k = K - 1; k >= 1; --k) {      // labels are in BFS order: children after parents
+            int t = tF[s][k];
+            for (int c : T.children[k]) t = std::max(t, tB[s][c]);
+            if (s > 0) {
+                const int p = T.parent[k];
+                t = std::max(t, p == 0 ? tR[s - 1] : tF[s - 1][p]);
+                t = std::max(t, tF[s - 1][k]);
+            }
+            if (T.parent[k] == 0) t = std::max(t, tR[s]);   // so that it can carry R(s+1)'s record
+            tB[s][k] = place(t + 1);
+        }
+    }
+    const int nlaunch = (int)load.size();
+    // the root scaling's record is saved and reset by the last product B_c(s-1) of a child c of the
+    // root: it runs after R(s-1) (placed so) and before R(s) (which waits for it)
+    std::vector<int> carrier(S, -1);
+    for (int s = 1; s < S; ++s) {
+        int best = -1;
+        for (int c : T.children[0])
+            if (best < 0 || tB[s - 1][c] > tB[s - 1][best]) best = c;
+        if (best < 0 || !(tB[s - 1][best] > tR[s - 1] && tB[s - 1][best] < tR[s])) return MOT_EUNSUPPORTED;
+        carrier[s] = best;
+    }
+    T.wlev.assign(nlaunch, Level());
+    T.wave_root_reset = T.resets.size();
+    T.resets.push_back(T.phi_sc(0));
+    for (int s = 0; s < S; ++s) {
+        const int q = (q0 + s) & 1, qn = q ^ 1;
+        const int off = S - 1 - s;
+        for (int k = 1; k < K; ++k) {         // F_k(s): gamma_k = K^T (mu^p / beta_k), then phi^k
+            const int p = T.parent[k];
+            Task t = blank_task();
+            t.src = ps_of(T, p);
+            t.sf0 = (int)T.fac.size();
+            add_factor(T, T.sets[p].mu_f, nullptr, 0);
+            add_factor(T, T.beta_q(k, q), T.beta_sc_q(k, q), 1);
+            t.snf = 2;
+            edge_grids(T, t, k, T.rawf[k]);
+            t.tgt = ps_of(T, k);
+            t.mode = EPI_PHI;
+            tgt_children(T, t, k, false, q);
+            t.mu_f = T.sets[k].mu_f;
+            t.mu_d = T.sets[k].mu_d;
+            t.out = T.gam[k];
+            t.out_sc = T.gam_sc(k);
+            t.phi = T.phi[k];
+            t.phi_sc = T.phi_sc(k);
+            const size_t r0 = T.resets.size();
+            T.resets.push_back(T.phi_sc(k));
+            T.resets.push_back(T.gam_sc(k));
+            t.reset_n = 2;
+            t.reset_list = (VecScale* const*)(uintptr_t)r0;
+            t.iter_off = off;
+            T.wlev[tF[s][k]].tgt.push_back(t);
+        }
+        {                                      // R(s): mass of the last iterate, then phi^1
+            Task t = blank_task();
+            t.tgt = ps_of(T, 0);
+            t.mode = EPI_ROOT;
+            tgt_children(T, t, 0, false, q);
+            t.mu_f = T.sets[0].mu_f;
+            t.mu_d = T.sets[0].mu_d;
+            t.phi = T.phi[0];
+            t.phi_sc = T.phi_sc(0);
+            t.iter_off = off;
+            T.wlev[tR[s]].tgt.push_back(t);
+        }
+        for (int k = K - 1; k >= 1; --k) {    // B_k(s) into the other copy
+            Task t = blank_task();
+            src_general(T, t, k, -1, true, 0, qn);
+            edge_grids(T, t, k, T.rawb[k]);
+            t.tgt = ps_of(T, T.parent[k]);
+            t.mode = EPI_MSG;
+            t.out = T.beta_q(k, qn);
+            t.out_sc = T.beta_sc_q(k, qn);
+            const size_t r0 = T.resets.size();
+            T.resets.push_back(T.beta_sc_q(k, qn));
+            t.reset_n = 1;
+            if (s + 1 < S && carrier[s + 1] == k) {
+                T.resets.push_back(T.phi_sc(0));
+                t.reset_n = 2;
+                t.save_prev = 1;
+            }
+            t.reset_list = (VecScale* const*)(uintptr_t)r0;
+            T.wlev[tB[s][k]].tgt.push_back(t);
+        }
+    }
+    // upload the chunk's factors, resets and tasks
+    if (T.fac.size() > T.fac_cap || T.resets.size() > T.res_cap) return MOT_EUNSUPPORTED;
+    std::vector<Task> all;
+    for (auto& L : T.wlev) {
+        L.src.clear();
+        L.msg_only = !L.tgt.empty();
+        for (auto& t : L.tgt) {
+            if (t.reset_n > 0) t.reset_list = T.d_resets + (uintptr_t)t.reset_list;
+            L.msg_only = L.msg_only && t.mode == EPI_MSG && t.hgrid != nullptr;
+        }
+        for (auto& t : L.tgt) all.push_back(t);
+    }
+    if (all.size() > T.wtask_cap) return MOT_EUNSUPPORTED;
+    CK(cudaMemcpyAsync(T.d_fac + T.fac_base, T.fac.data() + T.fac_base, sizeof(Factor) * (T.fac.size() - T.fac_base),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(T.d_resets + T.res_base, T.resets.data() + T.res_base,
+                       sizeof(VecScale*) * (T.resets.size() - T.res_base), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(T.d_wtasks, all.data(), sizeof(Task) * all.size(), cudaMemcpyHostToDevice, st));
+    size_t o = 0;
+    for (auto& L : T.wlev) {
+        L.d_src = nullptr;
+        L.d_tgt = T.d_wtasks + o;
+        o += L.tgt.size();
+    }
+    T.wave_S = S;
+    T.wave_q0 = q0;
     return MOT_OK;
 }
 
@@ -847,12 +1032,87 @@ int run_check(TreePlan& T, cudaStream_t st, Timer& tm, long long& nl) {
     CK(launch_prologue(T.d_resets + T.ck_reset0, (int)T.ck_reset_n, 0, 0, T.acc_node, 3 * T.K, T.G, st));
     RET(tm.end(e));
     nl += 1;
-    for (auto& L : T.chk) RET(run_level(T, L, st, tm, nl));
+    for (auto& L : (T.par ? T.chk1 : T.chk)) RET(run_level(T, L, st, tm, nl));
+    return MOT_OK;
+}
+
+// One wavefront chunk of S sweeps: prologue (the root's scale of the last iterate kept, the sweep
+// counter advanced by S, their accumulator slots cleared), then the chunk's launches.
+int run_wave(TreePlan& T, int S, cudaStream_t st, Timer& tm, long long& nl) {
+    cudaEvent_t e = nullptr;
+    RET(tm.begin(MOT_K_NODE, &e));
+    CK(launch_prologue(T.d_resets + T.wave_root_reset, 1, 1, S, nullptr, 0, T.G, st));
+    RET(tm.end(e));
+    nl += 1;
+    for (auto& L : T.wlev) RET(run_level(T, L, st, tm, nl));
+    return MOT_OK;
+}
+
+// One chunk with the schedule in T.wlev (built for this length and starting copy).
+int run_wave_chunk(TreePlan& T, int count, cudaStream_t st, Timer& tm, long long& nl, bool graphs) {
+    if (graphs && tm.on && st != nullptr) {
+        long long per = 0;
+        RET(tm.timed_graph(1, 2 * (T.wlev.size() + 2), [&](long long& d) {
+            const long long before = d;
+            const int rc = run_wave(T, count, st, tm, d);
+            per = d - before;
+            return rc;
+        }));
+        nl += per;
+    } else if (graphs && st != nullptr) {
+        if (T.gexec == nullptr || T.graph_iters != count || T.graph_par != T.par) {
+            if (T.gexec) {
+                cudaGraphExecDestroy(T.gexec);
+                T.gexec = nullptr;
+            }
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            long long d = 0;
+            const int rc = run_wave(T, count, st, tm, d);
+            cudaError_t ce = cudaStreamEndCapture(st, &graph);
+            if (rc != MOT_OK) return rc;
+            CK(ce);
+            CK(cudaGraphInstantiate(&T.gexec, graph, 0));
+            cudaGraphDestroy(graph);
+            T.graph_iters = count;
+            T.graph_par = T.par;
+            T.launches_per_chunk = d;
+        }
+        CK(cudaGraphLaunch(T.gexec, st));
+        nl += T.launches_per_chunk;
+    } else {
+        RET(run_wave(T, count, st, tm, nl));
+    }
+    T.par = (T.par + count) & 1;
     return MOT_OK;
 }
 
 int run_iterations(TreePlan& T, int count, cudaStream_t st, Timer& tm, long long& nl, bool graphs) {
     if (count <= 0) return MOT_OK;
+    if (T.wave) {
+        // chunks longer than kWaveMax run as equal parts (the parts reuse one schedule)
+        const int parts = (count + kWaveMax - 1) / kWaveMax;
+        for (int i = 0; i < parts; ++i) {
+            const int c = count / parts + (i < count % parts ? 1 : 0);
+            if (T.wave_S != c || T.wave_q0 != T.par) {
+                const int rc = build_wave(T, c, T.par, st);
+                if (rc != MOT_OK) {
+                    // no valid wavefront (never expected): sweep by sweep, which reads the first
+                    // beta copy, so only from a point where that copy is the latest
+                    if (rc != MOT_EUNSUPPORTED || T.par != 0) return rc;
+                    T.wave = false;
+                    return run_iterations(T, count - (count / parts) * i - std::min(i, count % parts), st, tm, nl,
+                                          graphs);
+                }
+                if (T.gexec) {
+                    cudaGraphExecDestroy(T.gexec);
+                    T.gexec = nullptr;
+                }
+            }
+            RET(run_wave_chunk(T, c, st, tm, nl, graphs));
+        }
+        return MOT_OK;
+    }
     if (graphs && tm.on && st != nullptr) {
         long long per = 0;
         RET(tm.timed_graph(count, 2 * (size_t)(4 * T.K + 8), [&](long long& d) {
@@ -865,11 +1125,12 @@ int run_iterations(TreePlan& T, int count, cudaStream_t st, Timer& tm, long long
         return MOT_OK;
     }
     if (graphs && !tm.on && st != nullptr) {
-        if (T.gexec == nullptr || T.graph_iters != count) {
+        if (T.gexec == nullptr || T.graph_iters != count || T.graph_par != -1) {
             if (T.gexec) {
                 cudaGraphExecDestroy(T.gexec);
                 T.gexec = nullptr;
             }
+            T.graph_par = -1;
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             long long dummy = 0;
@@ -980,6 +1241,9 @@ int tree_plan_setup(const mot_problem* P, const mot_options& o, TreePlan& T, voi
         int nmax = 0;
         for (int k = 0; k < T.K; ++k) nmax = std::max(nmax, T.n[k]);
         T.fused = fused2d_supported(T.d, g.n) && nmax <= fused2d_max_points();
+        bool any_free = false;
+        for (int k = 0; k < T.K; ++k) any_free = any_free || T.free_[k];
+        T.wave = T.fused && !any_free && o.wavefront > 0;
         size_t gsz = 1;
         for (int t = 0; t < T.d; ++t) gsz *= g.n;
         for (int k = 1; k < T.K; ++k) {
@@ -1610,6 +1874,7 @@ struct PlanOps {
     virtual char* stats_dev() = 0;
     virtual size_t stats_bytes() const = 0;
     virtual int K() const = 0;
+    virtual int n_scales() const = 0;          // scale records in the stats region
     virtual bool constrained(int k) const = 0;
     virtual double eta() const = 0;
     virtual int output(double* const* u, double* const* pair, cudaStream_t st, long long& nl) = 0;
@@ -1627,6 +1892,7 @@ struct TreeOps : PlanOps {
                                &T.acc[0].logphi, T.box_scratch, st));
             nl += uw ? 2 : 1;
         }
+        T.par = 0;                                                 // the first beta copy
         for (auto& L : T.bwd) RET(run_level(T, L, st, tm, nl));   // Algorithm 2, steps 3-5
         return MOT_OK;
     }
@@ -1637,6 +1903,7 @@ struct TreeOps : PlanOps {
     char* stats_dev() override { return T.stats_begin; }
     size_t stats_bytes() const override { return T.stats_bytes; }
     int K() const override { return T.K; }
+    int n_scales() const override { return 5 * T.K; }
     bool constrained(int k) const override { return !T.free_[k]; }
     double eta() const override { return T.eta; }
     int output(double* const* u, double* const*, cudaStream_t st, long long& nl) override {
@@ -1682,6 +1949,7 @@ struct CircleOps : PlanOps {
     char* stats_dev() override { return C.stats_begin; }
     size_t stats_bytes() const override { return C.stats_bytes; }
     int K() const override { return C.K; }
+    int n_scales() const override { return 4 * C.K; }
     bool constrained(int) const override { return true; }
     double eta() const override { return C.eta; }
     int output(double* const* u, double* const* pair, cudaStream_t st, long long& nl) override {
@@ -1806,7 +2074,7 @@ struct Solve {
             res->S_prev = S_prev;
             res->iters = iters;
             long long cl = 0;
-            for (int i = 0; i < 4 * K; ++i) cl += scs[i].clamped;
+            for (int i = 0; i < ops->n_scales(); ++i) cl += scs[i].clamped;
             res->clamped = cl;
             ops->geometry(res);
             res->launches = nl;

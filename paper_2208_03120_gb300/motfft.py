@@ -58,7 +58,7 @@ class Options(C.Structure):
         ("check_every", C.c_int), ("min_iter", C.c_int),
         ("n_grid", C.c_int), ("m", C.c_int), ("p", C.c_int),
         ("eps_B", C.c_double),
-        ("use_graphs", C.c_int), ("timing", C.c_int),
+        ("use_graphs", C.c_int), ("timing", C.c_int), ("wavefront", C.c_int),
     ]
 
 

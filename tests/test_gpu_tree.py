@@ -248,3 +248,35 @@ def test_timing_mode_same_result(M):
     for va, vb in zip(a, b):
         assert np.max(np.abs(va - vb)) <= 1e-5 * (np.max(np.abs(vb)) + prob.eta)
     assert o2.kernel_launches["fused"] >= 30 * 6 and sum(o2.kernel_ms.values()) > 0
+
+
+@pytest.mark.parametrize("check_every,max_iter", [(10, 40), (7, 23), (40, 80), (1, 5)])
+@pytest.mark.parametrize("shape", ["path10", "tree-random"])
+def test_wavefront_equals_sweep_by_sweep(M, shape, check_every, max_iter):
+    """The wavefront schedule (several sweeps in flight, two copies of every beta) runs the same
+    products on the same inputs as the sweep-by-sweep order of Algorithm 2: after a fixed number
+    of sweeps the scalings, S and the violation agree (up to the order of atomic sums), for stop-test
+    chunks that are even, odd (the copies swap between chunks), longer than one wavefront (run in
+    equal parts) and single sweeps."""
+    if shape == "path10":
+        prob = W.path10_d2(n=2000)
+        prob.root = -1
+    else:
+        rng = np.random.default_rng(77)
+        prob = W.random_problem(rng, W.TREE, 9, 2, 700, 0.03, shape="tree-random")
+        prob.root = 3
+    runs = []
+    for wave in (1, -1):
+        out, u = gpu_solve(M, prob, max_iter=max_iter, tol_viol=-1.0, check_every=check_every, wavefront=wave)
+        assert out.iters == max_iter
+        runs.append((out, u))
+    (a, ua), (b, ub) = runs
+    fa, fb = OS.gauge_fix(ua, prob.mu), OS.gauge_fix(ub, prob.mu)
+    scale = max(float(np.max(np.abs(v))) for v in fb) + prob.eta
+    for va, vb in zip(fa, fb):
+        assert np.max(np.abs(va - vb)) <= 1e-5 * scale
+    assert abs(a.S_last - b.S_last) <= 1e-6 * abs(b.S_last)
+    assert abs(a.cost_dual - b.cost_dual) <= 1e-6 * abs(b.cost_dual)
+    assert abs(a.violation - b.violation) <= 1e-6 + 1e-3 * b.violation
+    if check_every >= 7:                    # fewer launches: products of several sweeps share them
+        assert a.launches < b.launches
