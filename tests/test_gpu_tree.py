@@ -247,7 +247,8 @@ def test_timing_mode_same_result(M):
     a, b = OS.gauge_fix(u1, prob.mu), OS.gauge_fix(u2, prob.mu)
     for va, vb in zip(a, b):
         assert np.max(np.abs(va - vb)) <= 1e-5 * (np.max(np.abs(vb)) + prob.eta)
-    assert o2.kernel_launches["fused"] >= 30 * 6 and sum(o2.kernel_ms.values()) > 0
+    # the wavefront takes at least two launches per sweep (sweep by sweep: six)
+    assert o2.kernel_launches["fused"] >= 30 * 2 and sum(o2.kernel_ms.values()) > 0
 
 
 @pytest.mark.parametrize("check_every,max_iter", [(10, 40), (7, 23), (40, 80), (1, 5)])
