@@ -162,6 +162,24 @@ const char* mot_last_cuda_error(void);
 int mot_abi_version(void);
 
 /*
+ * Host-only helper (no GPU): the launch schedule that options.wavefront uses for a chunk of S
+ * sweeps of Algorithm 2 on a tree, exposed so that it can be inspected and tested.
+ *   parent:  host [K], the tree in breadth-first labels (parent[0] = -1, parent[k] < k).
+ *   cap:     most products per launch (the solver uses the fused kernel's co-resident clusters).
+ *   tF, tB:  host [S*K] out, entry s*K + k (k >= 1): launch of sweep s's forward product of node k
+ *            (gamma_k and the update of phi^k) and of its backward product (beta_k).
+ *   tR:      host [S] out, launch of sweep s's root update.
+ *   carrier: host [S] out, the child c of the root whose backward product of sweep s-1 saves the
+ *            root scaling's scale record for the root update of sweep s (-1 for s = 0).
+ *   nlaunch: out, launches of the chunk.
+ * Every product is in a later launch than the products whose results it reads and than the
+ * previous sweep's readers of the beta copy it overwrites (two copies, alternating by sweep).
+ * Returns MOT_OK, MOT_EINVAL (bad tree or sizes, NULL pointers) or MOT_EUNSUPPORTED.
+ */
+int mot_wave_schedule(int K, const int* parent, int S, int cap, int* tF, int* tB, int* tR, int* carrier,
+                      int* nlaunch);
+
+/*
  * Workspace bytes needed by mot_solve for this problem and these options (depends on the
  * sizes only, not on the data).  Returns MOT_EINVAL / MOT_ENOTTREE for a malformed problem.
  */

@@ -745,16 +745,21 @@ int upload_tasks(TreePlan& T, cudaStream_t st) {
 // product goes into the first launch after its inputs that has room.  The scale record of the root
 // scaling is saved and reset (R(s) reads the previous one) by a product that runs between R(s-1)
 // and R(s), and by the chunk prologue for s = 0.
-int build_wave(TreePlan& T, int S, int q0, cudaStream_t st) {
-    const int K = T.K;
-    T.fac.resize(T.fac_base);
-    T.resets.resize(T.res_base);
-    std::vector<std::vector<int>> tB(S, std::vector<int>(K, -1)), tF(S, std::vector<int>(K, -1));
-    std::vector<int> tR(S, -1);
-    auto prevB = [&](int s, int k) { return s > 0 ? tB[s - 1][k] : -1; };
-    // a launch takes at most as many products as clusters fit on the GPU at once (one more would
-    // run as a second wave); a product that finds its first possible launch full takes the next
-    const int cap = std::max(1, fused2d_max_active_clusters() > 0 ? fused2d_max_active_clusters() : 8);
+// The launch of every product of an S-sweep chunk on a tree given by parent[] (BFS labels:
+// parent[0] = -1, parent[k] < k), at most `cap` products per launch.  Fills tF / tB [S][K]
+// (entries k >= 1), tR [S], the carrier child of each R(s) (s >= 1, -1 for s = 0) and the number
+// of launches.  MOT_EUNSUPPORTED if no child of the root can carry the root's record.
+int wave_times(int K, const int* parent, int S, int cap, int* tF, int* tB, int* tR, int* carrier, int* nlaunch) {
+    if (K < 2 || S < 1 || cap < 1 || !parent || parent[0] != -1) return MOT_EINVAL;
+    std::vector<std::vector<int>> children(K);
+    for (int k = 1; k < K; ++k) {
+        if (parent[k] < 0 || parent[k] >= k) return MOT_EINVAL;
+        children[parent[k]].push_back(k);
+    }
+    auto F = [&](int s, int k) -> int& { return tF[(size_t)s * K + k]; };
+    auto B = [&](int s, int k) -> int& { return tB[(size_t)s * K + k]; };
+    for (int i = 0; i < S * K; ++i) tF[i] = tB[i] = -1;
+    auto prevB = [&](int s, int k) { return s > 0 ? B(s - 1, k) : -1; };
     std::vector<int> load;
     auto place = [&](int ready) {
         int t = ready;
@@ -765,36 +770,51 @@ int build_wave(TreePlan& T, int S, int q0, cudaStream_t st) {
     };
     for (int s = 0; s < S; ++s) {
         int r = -1;
-        for (int c : T.children[0]) r = std::max(r, prevB(s, c));
+        for (int c : children[0]) r = std::max(r, prevB(s, c));
         tR[s] = place(r + 1);
         for (int k = 1; k < K; ++k) {
             int t = prevB(s, k);
-            for (int c : T.children[k]) t = std::max(t, prevB(s, c));
-            tF[s][k] = place(t + 1);
+            for (int c : children[k]) t = std::max(t, prevB(s, c));
+            F(s, k) = place(t + 1);
         }
-        for (int k = K - 1; k >= 1; --k) {      // labels are in BFS order: children after parents
-            int t = tF[s][k];
-            for (int c : T.children[k]) t = std::max(t, tB[s][c]);
+        for (int k = K - 1; k >= 1; --k) {      // children after parents in BFS labels
+            int t = F(s, k);
+            for (int c : children[k]) t = std::max(t, B(s, c));
             if (s > 0) {
-                const int p = T.parent[k];
-                t = std::max(t, p == 0 ? tR[s - 1] : tF[s - 1][p]);
-                t = std::max(t, tF[s - 1][k]);
+                const int p = parent[k];
+                t = std::max(t, p == 0 ? tR[s - 1] : F(s - 1, p));
+                t = std::max(t, F(s - 1, k));
             }
-            if (T.parent[k] == 0) t = std::max(t, tR[s]);   // so that it can carry R(s+1)'s record
-            tB[s][k] = place(t + 1);
+            if (parent[k] == 0) t = std::max(t, tR[s]);   // so that it can carry R(s+1)'s record
+            B(s, k) = place(t + 1);
         }
     }
-    const int nlaunch = (int)load.size();
+    *nlaunch = (int)load.size();
     // the root scaling's record is saved and reset by the last product B_c(s-1) of a child c of the
     // root: it runs after R(s-1) (placed so) and before R(s) (which waits for it)
-    std::vector<int> carrier(S, -1);
+    carrier[0] = -1;
     for (int s = 1; s < S; ++s) {
         int best = -1;
-        for (int c : T.children[0])
-            if (best < 0 || tB[s - 1][c] > tB[s - 1][best]) best = c;
-        if (best < 0 || !(tB[s - 1][best] > tR[s - 1] && tB[s - 1][best] < tR[s])) return MOT_EUNSUPPORTED;
+        for (int c : children[0])
+            if (best < 0 || B(s - 1, c) > B(s - 1, best)) best = c;
+        if (best < 0 || !(B(s - 1, best) > tR[s - 1] && B(s - 1, best) < tR[s])) return MOT_EUNSUPPORTED;
         carrier[s] = best;
     }
+    return MOT_OK;
+}
+
+int build_wave(TreePlan& T, int S, int q0, cudaStream_t st) {
+    const int K = T.K;
+    T.fac.resize(T.fac_base);
+    T.resets.resize(T.res_base);
+    // a launch takes at most as many products as clusters fit on the GPU at once (one more would
+    // run as a second wave); a product that finds its first possible launch full takes the next
+    const int cap = std::max(1, fused2d_max_active_clusters() > 0 ? fused2d_max_active_clusters() : 8);
+    std::vector<int> tFf((size_t)S * K), tBf((size_t)S * K), tR(S), carrier(S);
+    int nlaunch = 0;
+    RET(wave_times(K, T.parent.data(), S, cap, tFf.data(), tBf.data(), tR.data(), carrier.data(), &nlaunch));
+    auto tF = [&](int s, int k) { return tFf[(size_t)s * K + k]; };
+    auto tB = [&](int s, int k) { return tBf[(size_t)s * K + k]; };
     T.wlev.assign(nlaunch, Level());
     T.wave_root_reset = T.resets.size();
     T.resets.push_back(T.phi_sc(0));
@@ -825,7 +845,7 @@ int build_wave(TreePlan& T, int S, int q0, cudaStream_t st) {
             t.reset_n = 2;
             t.reset_list = (VecScale* const*)(uintptr_t)r0;
             t.iter_off = off;
-            T.wlev[tF[s][k]].tgt.push_back(t);
+            T.wlev[tF(s, k)].tgt.push_back(t);
         }
         {                                      // R(s): mass of the last iterate, then phi^1
             Task t = blank_task();
@@ -856,7 +876,7 @@ int build_wave(TreePlan& T, int S, int q0, cudaStream_t st) {
                 t.save_prev = 1;
             }
             t.reset_list = (VecScale* const*)(uintptr_t)r0;
-            T.wlev[tB[s][k]].tgt.push_back(t);
+            T.wlev[tB(s, k)].tgt.push_back(t);
         }
     }
     // upload the chunk's factors, resets and tasks
@@ -2442,6 +2462,12 @@ const char* mot_strerror(int s) {
 const char* mot_last_cuda_error(void) { return g_cuda_err.c_str(); }
 
 int mot_abi_version(void) { return MOT_ABI_VERSION; }
+
+int mot_wave_schedule(int K, const int* parent, int S, int cap, int* tF, int* tB, int* tR, int* carrier,
+                      int* nlaunch) {
+    if (!tF || !tB || !tR || !carrier || !nlaunch) return MOT_EINVAL;
+    return wave_times(K, parent, S, cap, tF, tB, tR, carrier, nlaunch);
+}
 
 int mot_workspace_bytes(const mot_problem* prob, const mot_options* opt, size_t* bytes) {
     if (!bytes) return MOT_EINVAL;

@@ -109,6 +109,9 @@ def lib() -> C.CDLL:
         h.mot_server_progress.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         h.mot_server_poll.argtypes = [C.c_void_p, C.POINTER(ServerResult), C.c_int, C.POINTER(C.c_int)]
         h.mot_server_destroy.argtypes = [C.c_void_p]
+        h.mot_wave_schedule.argtypes = [C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int)]
         _lib_handle = h
     return _lib_handle
 
@@ -393,4 +396,21 @@ class Server:
 EXPORTED = ["mot_options_default", "mot_strerror", "mot_last_cuda_error", "mot_abi_version",
             "mot_workspace_bytes", "mot_solve", "mot_fastsum_workspace_bytes", "mot_fastsum",
             "mot_fastsum_static", "mot_server_create", "mot_server_submit", "mot_server_progress",
-            "mot_server_poll", "mot_server_destroy"]
+            "mot_server_poll", "mot_server_destroy", "mot_wave_schedule"]
+
+
+def wave_schedule(parent: Sequence[int], S: int, cap: int):
+    """mot_wave_schedule (host only): launches of the forward / backward products and root updates
+    of an S-sweep wavefront chunk on a tree in breadth-first labels.  Returns
+    (tF [S][K], tB [S][K], tR [S], carrier [S], nlaunch)."""
+    K = len(parent)
+    par = (C.c_int * K)(*[int(v) for v in parent])
+    tF = (C.c_int * (S * K))()
+    tB = (C.c_int * (S * K))()
+    tR = (C.c_int * S)()
+    car = (C.c_int * S)()
+    n = C.c_int(0)
+    _check(lib().mot_wave_schedule(K, par, S, cap, tF, tB, tR, car, C.byref(n)), "mot_wave_schedule")
+    F = [[tF[s * K + k] for k in range(K)] for s in range(S)]
+    B = [[tB[s * K + k] for k in range(K)] for s in range(S)]
+    return F, B, list(tR), list(car), n.value
