@@ -679,6 +679,7 @@ def main():
                    "eta": prob.eta, "tol_viol": TOL, "n_grid": last.n_grid, "M": last.M,
                    "iters_per_solve": last.iters, "parallelism": f"replicas{world}",
                    "root": "centre of the path (library choice, MOT_ROOT_CENTRE)",
+                   "schedule": "wavefront across sweeps (library default, options.wavefront)",
                    "l2": "flushed between steps (256 MB write)"},
         "latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "dense": dense,
