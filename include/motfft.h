@@ -180,6 +180,28 @@ int mot_wave_schedule(int K, const int* parent, int S, int cap, int* tF, int* tB
                       int* nlaunch);
 
 /*
+ * Host-only helper (no GPU): the boundary polynomial kappa_B of the regularised kernel, Eq.
+ * (Ker-reg) (Section 5, worked example in Fig. 3), as the solver builds it: degree 2p with
+ * kappa_B^(r) = kappa^(r) at a = tau - eps_B for r = 0..p and kappa_B^(r)(tau) = 0 for r = 1..p,
+ * kappa(x) = exp(-x^2 / eta).  coef: host [2p+1] out, coefficients of kappa_B(a + t) in powers of
+ * t.  Returns MOT_OK, MOT_EINVAL (eta <= 0, p outside 1..8, eps_B outside (0, tau)) or
+ * MOT_ENUMERIC (singular system).
+ */
+int mot_boundary_poly(double eta, double tau, double eps_B, int p, double* coef);
+
+/*
+ * Host-only helper (no GPU): the normalisation and grid the solver picks (Section 5): points
+ * within `radius` of their centre are scaled by 1/scale onto the unit torus (tau = 1/2) so that
+ * every pairwise distance stays below tau - eps_B, and the grid length n (M = n/4 Fourier
+ * half-degree) is the smallest power of two (16 .. the dimension's maximum, or exactly n_grid if
+ * > 0) for which both neglected terms -- the kernel of width eta_max at tau - eps_B and the Fourier
+ * tail of width eta_min beyond M -- are below exp(-18); err_exp receives the smaller of the two
+ * exponents reached.  Returns MOT_OK or MOT_EINVAL.
+ */
+int mot_plan_grid(int d, double radius, double eta_min, double eta_max, int n_grid, double eps_B, int* n_out,
+                  double* scale_out, double* err_exp_out);
+
+/*
  * Workspace bytes needed by mot_solve for this problem and these options (depends on the
  * sizes only, not on the data).  Returns MOT_EINVAL / MOT_ENOTTREE for a malformed problem.
  */

@@ -2469,6 +2469,24 @@ int mot_wave_schedule(int K, const int* parent, int S, int cap, int* tF, int* tB
     return wave_times(K, parent, S, cap, tF, tB, tR, carrier, nlaunch);
 }
 
+int mot_boundary_poly(double eta, double tau, double eps_B, int p, double* coef) {
+    if (!coef || !(eta > 0.0) || p < 1 || p > 8 || !(eps_B > 0.0) || !(eps_B < tau)) return MOT_EINVAL;
+    return boundary_poly(eta, tau, eps_B, p, coef) ? MOT_OK : MOT_ENUMERIC;
+}
+
+int mot_plan_grid(int d, double radius, double eta_min, double eta_max, int n_grid, double eps_B, int* n_out,
+                  double* scale_out, double* err_exp_out) {
+    if (d < 1 || d > 3 || !(radius >= 0.0) || !(eta_min > 0.0) || !(eta_max >= eta_min) || !(eps_B > 0.0) ||
+        !(eps_B < kTau) || !n_out || !scale_out || !err_exp_out)
+        return MOT_EINVAL;
+    if (n_grid && (n_grid < 16 || n_grid > max_grid(d) || (n_grid & (n_grid - 1)))) return MOT_EINVAL;
+    const GridChoice g = choose_grid(d, radius, eta_min, eta_max, n_grid, eps_B);
+    *n_out = g.n;
+    *scale_out = g.s;
+    *err_exp_out = g.err_exp;
+    return MOT_OK;
+}
+
 int mot_workspace_bytes(const mot_problem* prob, const mot_options* opt, size_t* bytes) {
     if (!bytes) return MOT_EINVAL;
     RET(validate_problem(prob));

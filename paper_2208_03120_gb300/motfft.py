@@ -109,6 +109,9 @@ def lib() -> C.CDLL:
         h.mot_server_progress.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         h.mot_server_poll.argtypes = [C.c_void_p, C.POINTER(ServerResult), C.c_int, C.POINTER(C.c_int)]
         h.mot_server_destroy.argtypes = [C.c_void_p]
+        h.mot_boundary_poly.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double)]
+        h.mot_plan_grid.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double,
+                                    C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]
         h.mot_wave_schedule.argtypes = [C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(C.c_int),
                                         C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                         C.POINTER(C.c_int)]
@@ -396,7 +399,8 @@ class Server:
 EXPORTED = ["mot_options_default", "mot_strerror", "mot_last_cuda_error", "mot_abi_version",
             "mot_workspace_bytes", "mot_solve", "mot_fastsum_workspace_bytes", "mot_fastsum",
             "mot_fastsum_static", "mot_server_create", "mot_server_submit", "mot_server_progress",
-            "mot_server_poll", "mot_server_destroy", "mot_wave_schedule"]
+            "mot_server_poll", "mot_server_destroy", "mot_wave_schedule", "mot_boundary_poly",
+            "mot_plan_grid"]
 
 
 def wave_schedule(parent: Sequence[int], S: int, cap: int):
@@ -414,3 +418,18 @@ def wave_schedule(parent: Sequence[int], S: int, cap: int):
     F = [[tF[s * K + k] for k in range(K)] for s in range(S)]
     B = [[tB[s * K + k] for k in range(K)] for s in range(S)]
     return F, B, list(tR), list(car), n.value
+
+
+def boundary_poly(eta: float, tau: float, eps_B: float, p: int):
+    """mot_boundary_poly (host only): coefficients of kappa_B(tau - eps_B + t) in powers of t."""
+    c = (C.c_double * (2 * p + 1))()
+    _check(lib().mot_boundary_poly(float(eta), float(tau), float(eps_B), int(p), c), "mot_boundary_poly")
+    return list(c)
+
+
+def plan_grid(d: int, radius: float, eta_min: float, eta_max: float, n_grid: int = 0, eps_B: float = 1.0 / 16):
+    """mot_plan_grid (host only): (n, scale, err_exp) of the normalisation and grid choice."""
+    n, s, e = C.c_int(0), C.c_double(0.0), C.c_double(0.0)
+    _check(lib().mot_plan_grid(int(d), float(radius), float(eta_min), float(eta_max), int(n_grid), float(eps_B),
+                               C.byref(n), C.byref(s), C.byref(e)), "mot_plan_grid")
+    return n.value, s.value, e.value
