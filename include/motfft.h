@@ -161,6 +161,10 @@ const char* mot_last_cuda_error(void);
 /* MOT_ABI_VERSION of the loaded library. */
 int mot_abi_version(void);
 
+/* sizeof of the ABI structs as compiled into the library (bindings check their mirrors):
+   out[0] mot_problem, out[1] mot_options, out[2] mot_result, out[3] mot_server_result. */
+void mot_struct_sizes(size_t out[4]);
+
 /*
  * Host-only helper (no GPU): the launch schedule that options.wavefront uses for a chunk of S
  * sweeps of Algorithm 2 on a tree, exposed so that it can be inspected and tested.

@@ -2463,6 +2463,14 @@ const char* mot_last_cuda_error(void) { return g_cuda_err.c_str(); }
 
 int mot_abi_version(void) { return MOT_ABI_VERSION; }
 
+void mot_struct_sizes(size_t out[4]) {
+    if (!out) return;
+    out[0] = sizeof(mot_problem);
+    out[1] = sizeof(mot_options);
+    out[2] = sizeof(mot_result);
+    out[3] = sizeof(mot_server_result);
+}
+
 int mot_wave_schedule(int K, const int* parent, int S, int cap, int* tF, int* tB, int* tR, int* carrier,
                       int* nlaunch) {
     if (!tF || !tB || !tR || !carrier || !nlaunch) return MOT_EINVAL;

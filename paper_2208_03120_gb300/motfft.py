@@ -109,6 +109,8 @@ def lib() -> C.CDLL:
         h.mot_server_progress.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         h.mot_server_poll.argtypes = [C.c_void_p, C.POINTER(ServerResult), C.c_int, C.POINTER(C.c_int)]
         h.mot_server_destroy.argtypes = [C.c_void_p]
+        h.mot_struct_sizes.argtypes = [C.POINTER(C.c_size_t)]
+        h.mot_struct_sizes.restype = None
         h.mot_boundary_poly.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double)]
         h.mot_plan_grid.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double,
                                     C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -400,7 +402,7 @@ EXPORTED = ["mot_options_default", "mot_strerror", "mot_last_cuda_error", "mot_a
             "mot_workspace_bytes", "mot_solve", "mot_fastsum_workspace_bytes", "mot_fastsum",
             "mot_fastsum_static", "mot_server_create", "mot_server_submit", "mot_server_progress",
             "mot_server_poll", "mot_server_destroy", "mot_wave_schedule", "mot_boundary_poly",
-            "mot_plan_grid"]
+            "mot_plan_grid", "mot_struct_sizes"]
 
 
 def wave_schedule(parent: Sequence[int], S: int, cap: int):

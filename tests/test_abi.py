@@ -41,6 +41,14 @@ def test_abi_version_and_strerror(M):
     assert M.strerror(12345) == "unknown status"
 
 
+def test_struct_layouts_match_the_library(M):
+    """The ctypes mirrors of mot_problem / mot_options / mot_result / mot_server_result have the
+    sizes the library was compiled with (a field added on one side only shows here)."""
+    out = (C.c_size_t * 4)()
+    M.lib().mot_struct_sizes(out)
+    assert list(out) == [C.sizeof(M.Problem), C.sizeof(M.Options), C.sizeof(M.Result), C.sizeof(M.ServerResult)]
+
+
 def test_options_defaults(M):
     o = M.options()
     assert o.max_iter == 1000 and o.check_every == 10 and o.m == 4 and o.p == 3
