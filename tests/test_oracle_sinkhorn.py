@@ -369,3 +369,46 @@ def test_euler_pair_marginals_at_convergence_carry_the_measures():
     for k in range(1, prob.K):
         np.testing.assert_allclose(pairs[k].sum(axis=1), prob.mu[0], atol=1e-8)
         np.testing.assert_allclose(pairs[k].sum(axis=0), prob.mu[k], atol=1e-8)
+
+
+def test_bruteforce_update_reproduces_the_measure():
+    """Algorithm 1 on the full tensor: right after the update of phi^k the marginal P_k of the
+    plan equals mu^k (P_k is linear in phi^k), and the total mass equals sum mu^k = 1 then."""
+    rng = np.random.default_rng(51)
+    prob = W.random_problem(rng, W.TREE, 4, 2, [3, 4, 2, 5], eta=0.3, shape="tree-random")
+    Kt = OS.full_kernel_tensor(prob.x64(), _tree_graph_edges(prob.edges), prob.eta)
+    phi = _rand_phi(rng, prob.n)
+    for k in range(4):
+        Pk = OS.tensor_marginals(OS.plan_tensor(Kt, phi))[k]
+        phi[k] = prob.mu[k] * phi[k] / Pk
+        P = OS.tensor_marginals(OS.plan_tensor(Kt, phi))
+        np.testing.assert_allclose(P[k], prob.mu[k], rtol=1e-12)
+        np.testing.assert_allclose([p.sum() for p in P], 1.0, rtol=1e-12)
+
+
+def test_euler_closing_edge_in_two_dimensions():
+    """The sigma-closing circle of Section 6.3 in d = 2 (sigma a rotation by 90 degrees about the
+    centre of the unit square): message-passing marginals and pair marginals equal brute force
+    over the tensor of the printed cost."""
+    rng = np.random.default_rng(52)
+    n = [3, 4, 3, 2]
+    x = [rng.uniform(0, 1, (m, 2)).astype(np.float32) for m in n]
+    mu = [np.full(m, 1.0 / m) for m in n]
+    x1 = x[0].astype(np.float64)
+    x_close = np.stack([1.0 - x1[:, 1], x1[:, 0]], axis=1)
+    phi = _rand_phi(rng, n)
+    xs = [a.astype(np.float64) for a in x]
+    import itertools
+    Kt = np.empty(tuple(n))
+    for idx in itertools.product(*[range(m) for m in n]):
+        c = float(((xs[-1][idx[-1]] - x_close[idx[0]]) ** 2).sum())
+        for k in range(3):
+            c += float(((xs[k + 1][idx[k + 1]] - xs[k][idx[k]]) ** 2).sum())
+        Kt[idx] = math.exp(-c / 0.3)
+    Pi = OS.plan_tensor(Kt, phi)
+    P = OS.circle_marginals(xs, phi, 0.3, x_close=x_close)
+    for a, b in zip(P, OS.tensor_marginals(Pi)):
+        np.testing.assert_allclose(a, b, rtol=1e-12)
+    pairs = OS.circle_pair_marginals(xs, phi, 0.3, x_close=x_close)
+    for k in range(1, 4):
+        np.testing.assert_allclose(pairs[k], OS.tensor_pair_marginal(Pi, 0, k), rtol=1e-12)
