@@ -756,48 +756,96 @@ int wave_times(int K, const int* parent, int S, int cap, int* tF, int* tB, int* 
         if (parent[k] < 0 || parent[k] >= k) return MOT_EINVAL;
         children[parent[k]].push_back(k);
     }
-    auto F = [&](int s, int k) -> int& { return tF[(size_t)s * K + k]; };
-    auto B = [&](int s, int k) -> int& { return tB[(size_t)s * K + k]; };
-    for (int i = 0; i < S * K; ++i) tF[i] = tB[i] = -1;
-    auto prevB = [&](int s, int k) { return s > 0 ? B(s - 1, k) : -1; };
-    std::vector<int> load;
-    auto place = [&](int ready) {
-        int t = ready;
-        while (t < (int)load.size() && load[t] >= cap) ++t;
-        if (t >= (int)load.size()) load.resize(t + 1, 0);
-        load[t] += 1;
-        return t;
+    // tasks of sweep s: R(s) = s W, F(s, k) = s W + k, B(s, k) = s W + K - 1 + k (W = 2K - 1); the
+    // order R(s), F(s, 1..K-1), B(s, K-1..1), s = 0..S-1, is topological
+    const int W = 2 * K - 1, N = S * W;
+    auto R_ = [&](int s) { return s * W; };
+    auto F_ = [&](int s, int k) { return s * W + k; };
+    auto B_ = [&](int s, int k) { return s * W + K - 1 + k; };
+    std::vector<std::vector<int>> pred(N), succ(N);
+    auto edge = [&](int u, int v) {
+        pred[v].push_back(u);
+        succ[u].push_back(v);
     };
     for (int s = 0; s < S; ++s) {
-        int r = -1;
-        for (int c : children[0]) r = std::max(r, prevB(s, c));
-        tR[s] = place(r + 1);
+        if (s > 0)
+            for (int c : children[0]) edge(B_(s - 1, c), R_(s));            // R(s) <- B_c(s-1)
         for (int k = 1; k < K; ++k) {
-            int t = prevB(s, k);
-            for (int c : children[k]) t = std::max(t, prevB(s, c));
-            F(s, k) = place(t + 1);
-        }
-        for (int k = K - 1; k >= 1; --k) {      // children after parents in BFS labels
-            int t = F(s, k);
-            for (int c : children[k]) t = std::max(t, B(s, c));
             if (s > 0) {
-                const int p = parent[k];
-                t = std::max(t, p == 0 ? tR[s - 1] : F(s - 1, p));
-                t = std::max(t, F(s - 1, k));
+                edge(B_(s - 1, k), F_(s, k));                                // F_k(s) <- B_k(s-1)
+                for (int c : children[k]) edge(B_(s - 1, c), F_(s, k));      //         <- B_c(s-1)
             }
-            if (parent[k] == 0) t = std::max(t, tR[s]);   // so that it can carry R(s+1)'s record
-            B(s, k) = place(t + 1);
+            edge(F_(s, k), B_(s, k));                                        // B_k(s) <- F_k(s)
+            for (int c : children[k]) edge(B_(s, c), B_(s, k));              //         <- B_c(s)
+            if (s > 0) {                                                     // readers of the copy
+                edge(F_(s - 1, k), B_(s, k));                                // B_k(s) overwrites
+                edge(parent[k] == 0 ? R_(s - 1) : F_(s - 1, parent[k]), B_(s, k));
+            }
+            if (parent[k] == 0) edge(R_(s), B_(s, k));   // so that it can carry R(s+1)'s record
         }
     }
-    *nlaunch = (int)load.size();
+    // topological order and the longest remaining chain of every task (its priority)
+    std::vector<int> order;
+    order.reserve(N);
+    for (int s = 0; s < S; ++s) {
+        order.push_back(R_(s));
+        for (int k = 1; k < K; ++k) order.push_back(F_(s, k));
+        for (int k = K - 1; k >= 1; --k) order.push_back(B_(s, k));
+    }
+    std::vector<int> chain(N, 1);
+    for (int i = N - 1; i >= 0; --i) {
+        const int u = order[i];
+        for (int v : succ[u]) chain[u] = std::max(chain[u], chain[v] + 1);
+    }
+    // list scheduling: each launch takes up to `cap` of the tasks whose predecessors all ran in
+    // earlier launches, longest remaining chain first (then earlier sweep, then task order)
+    std::vector<int> when(N, -1), waiting(N), ready_at(N, 0), rank(N);
+    for (int i = 0; i < N; ++i) rank[order[i]] = i;
+    std::vector<int> pool;
+    for (int u = 0; u < N; ++u) {
+        waiting[u] = (int)pred[u].size();
+        if (waiting[u] == 0) pool.push_back(u);
+    }
+    int placed = 0, t = 0;
+    while (placed < N) {
+        std::vector<int> cand;
+        for (int u : pool)
+            if (ready_at[u] <= t) cand.push_back(u);
+        if (cand.empty()) return MOT_EUNSUPPORTED;   // (never: the graph is acyclic)
+        std::sort(cand.begin(), cand.end(), [&](int x, int y) {
+            if (chain[x] != chain[y]) return chain[x] > chain[y];
+            return rank[x] < rank[y];
+        });
+        const int take = std::min<int>(cap, (int)cand.size());
+        for (int i = 0; i < take; ++i) {
+            const int u = cand[i];
+            when[u] = t;
+            ++placed;
+            pool.erase(std::find(pool.begin(), pool.end(), u));
+            for (int v : succ[u]) {
+                ready_at[v] = std::max(ready_at[v], t + 1);
+                if (--waiting[v] == 0) pool.push_back(v);
+            }
+        }
+        ++t;
+    }
+    *nlaunch = t;
+    for (int s = 0; s < S; ++s) {
+        tR[s] = when[R_(s)];
+        tF[(size_t)s * K] = tB[(size_t)s * K] = -1;
+        for (int k = 1; k < K; ++k) {
+            tF[(size_t)s * K + k] = when[F_(s, k)];
+            tB[(size_t)s * K + k] = when[B_(s, k)];
+        }
+    }
     // the root scaling's record is saved and reset by the last product B_c(s-1) of a child c of the
-    // root: it runs after R(s-1) (placed so) and before R(s) (which waits for it)
+    // root: it runs after R(s-1) (an edge above) and before R(s) (which waits for it)
     carrier[0] = -1;
     for (int s = 1; s < S; ++s) {
         int best = -1;
         for (int c : children[0])
-            if (best < 0 || B(s - 1, c) > B(s - 1, best)) best = c;
-        if (best < 0 || !(B(s - 1, best) > tR[s - 1] && B(s - 1, best) < tR[s])) return MOT_EUNSUPPORTED;
+            if (best < 0 || when[B_(s - 1, c)] > when[B_(s - 1, best)]) best = c;
+        if (best < 0 || !(when[B_(s - 1, best)] > tR[s - 1] && when[B_(s - 1, best)] < tR[s])) return MOT_EUNSUPPORTED;
         carrier[s] = best;
     }
     return MOT_OK;

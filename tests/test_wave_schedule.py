@@ -149,10 +149,10 @@ def test_schedule_reproduces_sweep_by_sweep_iterates(M, S, chunks, cap):
 
 def test_schedule_shortens_the_headline_chunk(M):
     """The 10-node path rooted at a centre, 10 sweeps, seven products per launch (the clusters
-    that fit on a GB300): 32 launches where the sweep-by-sweep order takes 60."""
+    that fit on a GB300): 30 launches where the sweep-by-sweep order takes 60."""
     parent = _trees()["path10_centre"]
     F, B, R, carrier, n = M.wave_schedule(parent, 10, 7)
-    assert n <= 32
+    assert n <= 30
 
 
 def test_schedule_rejects_bad_trees(M):
