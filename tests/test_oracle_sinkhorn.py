@@ -412,3 +412,52 @@ def test_euler_closing_edge_in_two_dimensions():
     pairs = OS.circle_pair_marginals(xs, phi, 0.3, x_close=x_close)
     for k in range(1, 4):
         np.testing.assert_allclose(pairs[k], OS.tensor_pair_marginal(Pi, 0, k), rtol=1e-12)
+
+
+@pytest.mark.parametrize("topology", ["tree", "circle"])
+def test_gauge_fix_keeps_the_plan_and_removes_only_the_gauge(topology):
+    """``gauge_fix`` (the map every potential comparison goes through) against the plan built
+    entry by entry over the full tensor: (a) the fixed potentials give the same K (.) Phi, hence
+    the same marginals, mass and dual / primal values (Theorem 3.1: only sum_k u^k_{i_k} enters);
+    (b) for k >= 1 the fixed u^k have zero mu^k-weighted mean; (c) it is idempotent; (d) two
+    gauges of one solution (u^k + c_k with sum_k c_k = 0) map to the same output, while a shift
+    that changes the plan (sum_k c_k != 0) does not."""
+    rng = np.random.default_rng(61 if topology == "tree" else 62)
+    K, n, eta = 4, [3, 4, 2, 5], 0.3
+    if topology == "tree":
+        prob = W.random_problem(rng, W.TREE, K, 2, n, eta=eta, shape="tree-random")
+        graph = _tree_graph_edges(prob.edges)
+    else:
+        prob = W.random_problem(rng, W.CIRCLE, K, 2, n, eta=eta)
+        graph = _circle_graph_edges(K)
+    Kt = OS.full_kernel_tensor(prob.x64(), graph, eta)
+    u = [eta * np.log(p) for p in _rand_phi(rng, n)]
+
+    def plan(v):
+        return OS.plan_tensor(Kt, [np.exp(a / eta) for a in v])
+
+    g = OS.gauge_fix(u, prob.mu)
+    # (a) same plan entry by entry, so the same marginals and values
+    np.testing.assert_allclose(plan(g), plan(u), rtol=1e-12)
+    Pu, Pg = OS.tensor_marginals(plan(u)), OS.tensor_marginals(plan(g))
+    for a, b in zip(Pu, Pg):
+        np.testing.assert_allclose(a, b, rtol=1e-12)
+    phi_u, phi_g = [np.exp(a / eta) for a in u], [np.exp(a / eta) for a in g]
+    mass = OS.total_mass(Pu)
+    assert abs(OS.dual_value(prob.mu, phi_g, mass, eta) - OS.dual_value(prob.mu, phi_u, mass, eta)) <= 1e-12
+    assert abs(OS.primal_value(Pg, phi_g, mass, eta) - OS.primal_value(Pu, phi_u, mass, eta)) <= 1e-12
+    # (b) the normalisation it states
+    for k in range(1, K):
+        assert abs(float(np.dot(prob.mu[k], g[k]))) <= 1e-14
+    assert not np.allclose(g[0], u[0])            # the total shift went to u^0
+    # (c) idempotent
+    for a, b in zip(OS.gauge_fix(g, prob.mu), g):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-14)
+    # (d) every gauge of the same plan maps to one output; a plan-changing shift does not
+    c = rng.normal(size=K)
+    c -= c.mean()
+    g2 = OS.gauge_fix([a + ck for a, ck in zip(u, c)], prob.mu)
+    for a, b in zip(g2, g):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-13)
+    g3 = OS.gauge_fix([a + 0.1 for a in u], prob.mu)
+    assert max(float(np.max(np.abs(a - b))) for a, b in zip(g3, g)) > 0.1
