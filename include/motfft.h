@@ -278,9 +278,9 @@ int mot_server_poll(mot_server s, mot_server_result* out, int max, int* n_out);
 int mot_server_destroy(mot_server s);
 
 /*
- * Allocation-free variant of mot_fastsum (the paper has no counterpart: this serves callers
- * that cannot allocate GPU memory or pass a workspace, e.g. code that must not allocate while
- * a CUDA graph is being captured, or plug-ins whose host application owns all device memory).
+ * Allocation-free variant of mot_fastsum (the paper has no counterpart).  It serves callers that
+ * cannot allocate GPU memory or lend a workspace: plug-ins whose host application owns all
+ * device memory through its own pool, and real-time loops where an allocation could block.
  * Same arguments and result as mot_fastsum, without ws / ws_bytes: the scratch is a static
  * device array of MOT_STATIC_SCRATCH_BYTES per GPU, held from library load until exit.
  *   - A request whose mot_fastsum_workspace_bytes exceeds MOT_STATIC_SCRATCH_BYTES returns
@@ -289,12 +289,27 @@ int mot_server_destroy(mot_server s);
  *     make it before any stream capture.
  *   - All calls on a device share the array: calls that overlap on the GPU race and must be
  *     serialised by the caller.  What must start at zero is cleared by every call.
- *   - Calls no cudaMalloc / cudaFree or any allocating routine.
+ *   - Calls no cudaMalloc / cudaFree or any allocating routine.  Like mot_fastsum, the call ends
+ *     by reading a few scalars back on its stream and synchronising that stream.
  */
 #define MOT_STATIC_SCRATCH_BYTES (32u << 20)
 int mot_fastsum_static(int d, double eta, const float* x_src, int64_t n_src, const float* x_tgt,
                        int64_t n_tgt, const float* alpha, int nrhs, float* beta,
                        const mot_options* opt, double* scale_out, void* stream);
+
+/* ---- test hook ------------------------------------------------------------------------ */
+/*
+ * Error-path testing of the tensor-core kernel (MOT_PATH_DENSE_BF16X3) without a GPU fault (the
+ * paper has no counterpart).  Every wait of that kernel on its own mbarriers is bounded by
+ * wait_ns (default 10^9, i.e. 1 s); on expiry the kernel records the failure, waits (bounded) for
+ * its own copies in flight, frees its tensor memory and returns, and the call returns
+ * MOT_ETIMEOUT.  stall_loads = 1 makes the kernel's load thread issue no copies at all, so that
+ * the first wait for operands runs out after wait_ns while nothing is in flight; the context stays
+ * usable.  Process-wide; applies to launches made after the call (a captured graph keeps the
+ * values it was captured with).  Restore with mot_test_tc_wait(1000000000, 0).
+ * Returns MOT_OK or MOT_EINVAL (wait_ns outside [10^3, 10^10]).
+ */
+int mot_test_tc_wait(long long wait_ns, int stall_loads);
 
 #ifdef __cplusplus
 }

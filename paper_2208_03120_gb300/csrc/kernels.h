@@ -141,7 +141,9 @@ struct TcEpi {
     VecScale* out_sc;         // mode 1: scale record of the output (mx reset by the caller)
     const VecScale* s_a;      // mode 1: scale records whose log-scales sum to that of the output
     const VecScale* s_b;
-    int* err;                 // bit 4 set when a bounded wait expired
+    int* err;                 // bit 2 (value 4) set when a bounded wait expired
+    unsigned long long wait_ns;  // limit of every bounded wait (filled by the launcher)
+    int stall_loads;          // test hook: the producer issues no loads (filled by the launcher)
 };
 int tc_ld(int k);             // padded row stride (elements) of a split operand with k columns
 cudaError_t prepare_tc_gemm();

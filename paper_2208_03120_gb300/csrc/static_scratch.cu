@@ -1,19 +1,21 @@
 // mot_fastsum_static: the kernel matrix-vector product for callers that cannot allocate GPU memory.
 //
-// Some callers cannot call cudaMalloc or hand the library a workspace: code running inside a
-// CUDA-graph capture that must not allocate, plugins of a host application that owns all
-// device memory through its own pool, or real-time loops where an allocation could block.
-// For them this entry point keeps its scratch in one file-scope __device__ array that is
-// created when the library's device code is loaded on a GPU and lives until the process
-// exits (every GPU that loads the library holds MOT_STATIC_SCRATCH_BYTES of it).
+// Some callers cannot call cudaMalloc or hand the library a workspace: plug-ins of a host
+// application that owns all device memory through its own pool (they get no allocator and no
+// spare buffer to lend), and real-time loops where an allocation could block or fail at the
+// wrong moment.  For them this entry point keeps its scratch in one file-scope __device__
+// array that is created when the library's device code is loaded on a GPU and lives until the
+// process exits (every GPU that loads the library holds MOT_STATIC_SCRATCH_BYTES of it).
 //
 // Set-up: the first call on each device (with that device current) looks up the array's
-// device address with cudaGetSymbolAddress and caches it; make that first call before any
-// stream capture.  The host-side name of the array is only a stand-in and is never passed
-// to a kernel.  All calls share the array and it keeps the previous call's contents; the
-// fast summation clears everything that must start at zero (grids, bin counts) on the
-// stream before use.  Calls whose work overlaps on the GPU (different streams or threads,
-// same device) race on the array and must be serialised by the caller.
+// device address with cudaGetSymbolAddress, checks the return code and caches it per device;
+// make that first call before any stream capture.  The host-side name of the array is only a
+// stand-in and is never passed to a kernel.  All calls share the array and it keeps the
+// previous call's contents; the fast summation clears everything that must start at zero
+// (grids, bin counts) on the stream before use.  Calls whose work overlaps on the GPU
+// (different streams or threads, same device) race on the array and must be serialised by the
+// caller.  Like mot_fastsum, a call ends by reading a few scalars back on its stream and
+// synchronising that stream.
 #include <mutex>
 
 #include "motfft.h"

@@ -21,11 +21,13 @@
 //   warps 0..3        epilogue: tcgen05.ld of their 32 TMEM lanes (= 32 output rows), floor /
 //                     maximum / clamp count of a message (Algorithm 3 normalisation), staged
 //                     through shared memory so each warp stores whole 128-byte row segments.
-// Every mbarrier wait is bounded (globaltimer); on expiry the CTA sets bit 4 of the error word,
-// drains its own outstanding copies (bounded), frees TMEM and returns.
+// Every mbarrier wait is bounded (globaltimer, 1 s unless a test shortens it through
+// mot_test_tc_wait); on expiry the CTA sets bit 2 (value 4) of the error word, drains its own
+// outstanding copies (bounded), frees TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "kernels.h"
@@ -34,7 +36,11 @@ namespace {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 32;                       // 32 BF16 = one 64-byte swizzle row per stage
-constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s per wait
+constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s per wait (default)
+// test hook (mot_test_tc_wait): the wait limit, and a switch that makes the producer issue no
+// loads, so that the MMA thread's first wait runs out
+std::atomic<long long> g_wait_ns{(long long)kWaitNs};
+std::atomic<int> g_stall_loads{0};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -67,13 +73,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0u;
 }
 
-// Wait for the phase of the given parity to complete; false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for the phase of the given parity to complete; false after `limit` ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit) {
     const uint32_t a = smem_u32(bar);
     if (mbar_try_wait(a, parity)) return true;
     const unsigned long long t0 = globaltimer();
     while (!mbar_try_wait(a, parity))
-        if (globaltimer() - t0 > kWaitNs) return false;
+        if (globaltimer() - t0 > limit) return false;
     return true;
 }
 
@@ -179,6 +185,7 @@ __global__ void __launch_bounds__(128, 1)
     const int gm = min(num_m - first_m, 8), in_group = (int)blockIdx.x - group * 8 * num_n;
     const int m0 = (first_m + in_group % gm) * TC_BM, n0 = (in_group / gm) * BN;
     const int nkb = (E.K + TC_BK - 1) / TC_BK;
+    const unsigned long long lim = E.wait_ns;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -205,10 +212,11 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0 && lane == 0) {
         // ---- producer ----
         int kb = 0;
-        for (; kb < nkb; ++kb) {
+        const int nkb_load = E.stall_loads ? 0 : nkb;   // test hook: no loads, nothing in flight
+        for (; kb < nkb_load; ++kb) {
             const int s = kb % STAGES;
             const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-            if (!mbar_wait(empty + s, ph ^ 1u)) {
+            if (!mbar_wait(empty + s, ph ^ 1u, lim)) {
                 atomicOr(s_fail, 1);
                 break;
             }
@@ -228,7 +236,7 @@ __global__ void __launch_bounds__(128, 1)
         for (; kb < nkb; ++kb) {
             const int s = kb % STAGES;
             const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-            if (!mbar_wait(full + s, ph)) {
+            if (!mbar_wait(full + s, ph, lim)) {
                 atomicOr(s_fail, 2);
                 break;
             }
@@ -252,7 +260,7 @@ __global__ void __launch_bounds__(128, 1)
     __syncwarp();
 
     // ---- epilogue: all four warps ----
-    const bool acc_ok = mbar_wait(accb, 0u);
+    const bool acc_ok = mbar_wait(accb, 0u, lim);
     if (!acc_ok && lane == 0) atomicOr(s_fail, 4);
     tc_fence_after();
     float mx = 0.f;
@@ -306,7 +314,7 @@ __global__ void __launch_bounds__(128, 1)
         if (*s_fail) {
             // drain the copies still in flight into this CTA's shared memory (bounded)
             for (int kb = *s_consumed; kb < *s_issued; ++kb)
-                mbar_wait(full + (kb % STAGES), (uint32_t)(kb / STAGES) & 1u);
+                mbar_wait(full + (kb % STAGES), (uint32_t)(kb / STAGES) & 1u, lim);
             if (E.err) atomicOr(E.err, 4);
         } else if (E.mode == 1) {
             float m = fmaxf(fmaxf(s_mx[0], s_mx[1]), fmaxf(s_mx[2], s_mx[3]));
@@ -488,6 +496,8 @@ cudaError_t launch_tc_gemm(const TcGemm& g, TcEpi e, cudaStream_t st) {
     e.M = g.M;
     e.N = g.N;
     e.K = g.K;
+    e.wait_ns = (unsigned long long)g_wait_ns.load();
+    e.stall_loads = g_stall_loads.load();
     switch (g.bn) {
     case 256: return launch_cfg<256>(g, e, st);
     case 224: return launch_cfg<224>(g, e, st);
@@ -513,4 +523,12 @@ cudaError_t launch_kernel_split(const float* ut, int nt, const float* us, int ns
     k_kernel_split<<<dim3(bx, std::min(nt, 65535)), 256, 0, st>>>(ut, nt, us, ns, d, eta_u, ld, static_cast<__nv_bfloat16*>(hi),
                                                  static_cast<__nv_bfloat16*>(lo));
     return cudaGetLastError();
+}
+
+// Test hook of the bounded waits (declared in motfft.h).
+extern "C" int mot_test_tc_wait(long long wait_ns, int stall_loads) {
+    if (wait_ns < 1000 || wait_ns > 10000000000ll) return MOT_EINVAL;
+    g_wait_ns.store(wait_ns);
+    g_stall_loads.store(stall_loads ? 1 : 0);
+    return MOT_OK;
 }

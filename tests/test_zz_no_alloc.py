@@ -1,17 +1,19 @@
 """mot_fastsum_static: the allocation-free kernel matrix-vector product, through the C ABI.
 
-For callers that cannot allocate GPU memory (for example code that must not allocate while
-a CUDA graph is captured, or plug-ins whose host application owns all device memory), the
-library keeps the scratch of this entry point in a static device array.  The test compares
-it with mot_fastsum (the workspace entry point) on two calls in a row with different inputs,
-within the matvec tolerance of the other GPU tests, and checks that a request larger than
-the static scratch is refused before any GPU work.  This file is collected last.
+Some callers cannot allocate GPU memory or lend the library a workspace: plug-ins whose host
+application owns all device memory through its own pool, or real-time loops where an allocation
+could block.  For them the library keeps the scratch of this entry point in a static device
+array.  The test compares it with mot_fastsum (the workspace entry point) on two calls in a row
+with different inputs, within the matvec tolerance of the other GPU tests, checks both against
+the oracle's FP64 direct summation (Eq. fastsum-sum), and checks that a request larger than the
+static scratch is refused before any GPU work.  This file is collected last.
 """
 import ctypes as C
 
 import numpy as np
 import pytest
 
+from oracle import kernel as OK
 from paper_2208_03120_gb300 import workloads as W
 from tests.gpu_helpers import inf_rel_err, to_dev_points
 
@@ -34,15 +36,19 @@ def test_static_scratch_matches_workspace_entry_point(M):
     import torch
     rng = np.random.default_rng(2024)
     for call, (d, ns, nt, eta) in enumerate([(2, 4000, 3001, 0.02), (3, 2500, 1999, 0.05)]):
-        xs = to_dev_points(W.uniform_ball(rng, ns, d, 0.24))
-        xt = to_dev_points(W.uniform_ball(rng, nt, d, 0.24))
-        a = torch.from_numpy(rng.uniform(0, 1, size=ns).astype(np.float32)).cuda()
+        ps = W.uniform_ball(rng, ns, d, 0.24).astype(np.float32)
+        pt = W.uniform_ball(rng, nt, d, 0.24).astype(np.float32)
+        an = rng.uniform(0, 1, size=ns).astype(np.float32)
+        xs, xt = to_dev_points(ps), to_dev_points(pt)
+        a = torch.from_numpy(an).cuda()
         b_ref, s_ref = M.mot_fastsum(xs, xt, a, eta)
         b_st, s_st = M.mot_fastsum_static(xs, xt, a, eta)
         torch.cuda.synchronize()
         assert s_st == s_ref
         err = inf_rel_err(b_st.cpu().numpy(), b_ref.cpu().numpy())
         assert err <= TOL, (call, err)
+        exact = OK.direct_sum(pt.astype(np.float64), ps.astype(np.float64), an.astype(np.float64), eta)
+        assert inf_rel_err(b_st.cpu().numpy(), exact) <= TOL, call
 
 
 def test_static_scratch_rejects_oversized_request(M):
