@@ -113,11 +113,13 @@ typedef struct {
                            period 2*tau = 1 [1/16]                                             */
     int use_graphs;     /* 1 = replay iterations as a CUDA graph, -1 = plain launches [1]      */
     int timing;         /* 1 = time every kernel class with CUDA events (slower) [0]          */
-    int wavefront;      /* trees on the fused 2-D path: 1 = pipeline the sweeps of each stop-test
-                           chunk (up to 32 sweeps) as a wavefront, each launch taking every kernel
-                           product whose inputs are ready, from several sweeps; the same
-                           products on the same inputs as the sweep-by-sweep order (Algorithm 2);
-                           -1 = sweep by sweep [1]                                              */
+    int wavefront;      /* trees on the fused 2-D path: pipeline the sweeps of each stop-test chunk
+                           (up to 32 sweeps) as a wavefront -- the same products on the same inputs
+                           as the sweep-by-sweep order of Algorithm 2, products of several sweeps
+                           in flight at once.  1 = one persistent launch per chunk whose clusters
+                           take the products in a topological order and start each one as soon as
+                           the products it reads have completed; 2 = one launch per step of the
+                           host's list schedule; -1 = sweep by sweep [1]                         */
 } mot_options;
 
 /* Fill *o with the defaults. */
@@ -310,6 +312,17 @@ int mot_fastsum_static(int d, double eta, const float* x_src, int64_t n_src, con
  * Returns MOT_OK or MOT_EINVAL (wait_ns outside [10^3, 10^10]).
  */
 int mot_test_tc_wait(long long wait_ns, int stall_loads);
+
+/*
+ * Test hook of the persistent wavefront kernel (options.wavefront = 1; the paper has no
+ * counterpart): launch it with `nclusters` thread-block clusters instead of as many as fit on the
+ * GPU at once (0 restores that default).  Its products are claimed in a topological order and each
+ * waits only for products claimed before it, so the result does not depend on how many clusters
+ * run, nor on how many are resident together (1 runs the chunk's products one after another; more
+ * than fit run in later waves).  Process-wide; applies to solves set up after the call.
+ * Returns MOT_OK or MOT_EINVAL (nclusters outside [0, 1024]).
+ */
+int mot_test_wave_clusters(int nclusters);
 
 #ifdef __cplusplus
 }

@@ -101,6 +101,8 @@ struct Task {
     int zero_n;
     int iter_off;                // this task's sweep is the counter minus iter_off (sweeps of a
                                  // pipelined chunk share one counter value)
+    int dep0, ndep;              // persistent wavefront kernel: indices (into its dependency
+                                 // array) of the products that must complete before this one
 };
 
 __device__ __forceinline__ float mx_of(const VecScale* s, int use_prev) {

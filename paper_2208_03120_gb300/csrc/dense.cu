@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256) k_epi(const Task* __restrict__ tasks, Glo
         }
         epilogue_point(T, tf, C, G.floor_, i, raw, ep);
     }
-    epi_block_finish(T, G, tf, Lsrc, ep, sP.iter);
+    epi_block_finish(T, G, tf, Lsrc, ep, sP.iter, C);
 }
 
 }  // namespace

@@ -49,6 +49,7 @@ __device__ __forceinline__ void load_factors(FacCache& fc, const Factor* F, int 
 struct EpiConst {
     double lsphi;      // log-scale of the scalings written (EPI_PHI / EPI_ROOT)
     double E;          // exp(total log-scale) of P_i = raw_i T_i e^{L} (EPI_MARG / EPI_ROOT)
+    double invEs;      // 1 / max(E, 1): |P_i - mu_i| is summed in FP32 scaled by it
     double ls_phi_k;   // log-scale of the node's current scaling (EPI_MARG)
     float inv_mx_old;  // 1 / mx of the previous root scaling (EPI_ROOT)
 };
@@ -62,15 +63,23 @@ __device__ __forceinline__ float eval_prod(const FacCache& fc, int i) {
     return v;
 }
 
-// Per-thread partial results of an epilogue, reduced once per block.
+// Per-thread partial results of an epilogue, reduced once per block.  The sums are FP32 with
+// every large scale factored out (FP64 arithmetic is slow on this part: a block's reduction in
+// FP64 took longer than its kernel sum); the block combines them with the scales in FP64:
+//   sum_i mu_i log phi_i     = lphi + lsphi * musum        (lsphi: the scalings' log-scale)
+//   mass = sum_i P_i          = E * a                        (P_i = E a_i, a_i = raw_i T_i <= N)
+//   viol = sum_i |P_i - mu_i| = max(E, 1) * dv
+//   sum_i P_i log phi^k_i     = E * alog + ls_phi_k * mass
+// Each block sums at most a few points per thread and some hundreds of threads, so the FP32
+// sums carry a relative error of about 1e-7, the size of the FP32 logarithms they add.
 struct EpiPartial {
     float mx_out, mx_phi;
-    double logphi, viol, mass, plogphi;
+    float lphi, musum, a, dv, alog;
     unsigned int clamps;
 };
 
 __device__ __forceinline__ void epi_zero(EpiPartial& e) {
-    e.mx_out = 0.f; e.mx_phi = 0.f; e.logphi = 0.0; e.viol = 0.0; e.mass = 0.0; e.plogphi = 0.0; e.clamps = 0u;
+    e.mx_out = 0.f; e.mx_phi = 0.f; e.lphi = 0.f; e.musum = 0.f; e.a = 0.f; e.dv = 0.f; e.alog = 0.f; e.clamps = 0u;
 }
 
 // Block-start duties carried by a task: reset scale records (and keep the previous values of
@@ -114,6 +123,7 @@ __device__ __forceinline__ void epi_prepare(const Task& T, const FacCache& tf, d
         C.E = exp(Lold + (T.mode == EPI_ROOT ? tf.L : Lsrc));
         C.inv_mx_old = 1.f / mx_of(T.phi_sc, 1);
     }
+    C.invEs = 1.0 / fmax(C.E, 1.0);
 }
 
 // One warp fills a factor cache: lanes stride over the factors, reading each factor and its
@@ -180,6 +190,7 @@ __device__ __forceinline__ void load_task_consts(const Task& T, const Globals& G
             C.E = exp(pre.Lold + (T.mode == EPI_ROOT ? tf.L : Lsrc));
             C.inv_mx_old = pre.inv_mx_old;
         }
+        C.invEs = 1.0 / fmax(C.E, 1.0);
     }
 }
 
@@ -202,7 +213,6 @@ __device__ __forceinline__ EpiIn epi_load(const Task& T, const FacCache& tf, int
     case EPI_PHI:
         in.t = eval_prod(tf, i);
         in.muf = T.mu_f[i];
-        in.mud = T.mu_d[i];
         break;
     case EPI_ROOT:
         in.t = eval_prod(tf, i);
@@ -248,7 +258,10 @@ __device__ __forceinline__ void epilogue_point_in(const Task& T, const EpiConst&
         const float ph = in.muf / (g * in.t);
         T.phi[i] = ph;
         ep.mx_phi = fmaxf(ep.mx_phi, ph);
-        if (in.mud > 0.0) ep.logphi += in.mud * ((double)logf(ph) + C.lsphi);
+        if (in.muf > 0.f) {
+            ep.lphi = fmaf(in.muf, logf(ph), ep.lphi);
+            ep.musum += in.muf;
+        }
         break;
     }
     case EPI_PHI_FREE:
@@ -264,31 +277,37 @@ __device__ __forceinline__ void epilogue_point_in(const Task& T, const EpiConst&
     case EPI_ROOT: {
         // mass and violation of the last iterate (scale record prev), then the update
         const float old = in.phi * C.inv_mx_old;
-        const double P = (double)(old * in.t) * C.E;
-        ep.mass += P;
+        const float a = old * in.t;
+        ep.a += a;
         if (T.free_node) {
             ep.mx_phi = 1.f;
         } else {
-            ep.viol += fabs(P - in.mud);
+            ep.dv += (float)(fabs((double)a * C.E - in.mud) * C.invEs);
             const float ph = in.muf / in.t;
             T.phi[i] = ph;
             ep.mx_phi = fmaxf(ep.mx_phi, ph);
-            if (in.mud > 0.0) ep.logphi += in.mud * ((double)logf(ph) + C.lsphi);
+            if (in.muf > 0.f) {
+                ep.lphi = fmaf(in.muf, logf(ph), ep.lphi);
+                ep.musum += in.muf;
+            }
         }
         break;
     }
     case EPI_CROOT: {
         // raw = sum over the root's column of the circle product (normalised factors)
         const float old = in.phi * C.inv_mx_old;
-        const double P = (double)(old * raw) * C.E;
-        ep.mass += P;
-        ep.viol += fabs(P - in.mud);
+        const float a = old * raw;
+        ep.a += a;
+        ep.dv += (float)(fabs((double)a * C.E - in.mud) * C.invEs);
         float g = raw;
         if (!(g >= floor_)) { g = floor_; ep.clamps++; }
         const float ph = in.muf / g;
         T.phi[i] = ph;
         ep.mx_phi = fmaxf(ep.mx_phi, ph);
-        if (in.mud > 0.0) ep.logphi += in.mud * ((double)logf(ph) + C.lsphi);
+        if (in.muf > 0.f) {
+            ep.lphi = fmaf(in.muf, logf(ph), ep.lphi);
+            ep.musum += in.muf;
+        }
         break;
     }
     case EPI_MARG: {
@@ -296,10 +315,10 @@ __device__ __forceinline__ void epilogue_point_in(const Task& T, const EpiConst&
         if (!(g >= floor_)) { g = floor_; ep.clamps++; }
         if (T.out) T.out[i] = g;
         ep.mx_out = fmaxf(ep.mx_out, g);
-        const double P = (double)(g * in.t) * C.E;
-        ep.mass += P;
-        if (T.mu_d) ep.viol += fabs(P - in.mud);
-        if (P > 0.0) ep.plogphi += P * ((double)logf(in.phi) + C.ls_phi_k);
+        const float a = g * in.t;
+        ep.a += a;
+        if (T.mu_d) ep.dv += (float)(fabs((double)a * C.E - in.mud) * C.invEs);
+        if (a > 0.f) ep.alog = fmaf(a, logf(in.phi), ep.alog);
         break;
     }
     default:
@@ -316,9 +335,8 @@ __device__ __forceinline__ void epilogue_point(const Task& T, const FacCache& tf
 // quantities the task's mode produces are reduced (the FP64 ones cost most); warp 0 combines
 // the warps' partials lane-parallel.  `iter` is the sweep counter read at the kernel's start.
 __device__ __forceinline__ void epi_block_finish(const Task& T, const Globals& G, const FacCache& tf,
-                                                 double Lsrc, EpiPartial ep, int iter) {
-    __shared__ float s_mx[2][32];
-    __shared__ double s_d[4][32];
+                                                 double Lsrc, EpiPartial ep, int iter, const EpiConst& C) {
+    __shared__ float s_f[7][32];
     __shared__ unsigned int s_c[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     const int mode = T.mode;
@@ -328,48 +346,57 @@ __device__ __forceinline__ void epi_block_finish(const Task& T, const Globals& G
     const bool d_log = mode == EPI_PHI || mode == EPI_ROOT || mode == EPI_CROOT;
     const bool d_vm = mode == EPI_MARG || mode == EPI_ROOT || mode == EPI_CROOT;
     const bool d_pl = mode == EPI_MARG;
-    float a = has_out ? warp_max(ep.mx_out) : 0.f;
-    float b = has_phi ? warp_max(ep.mx_phi) : 0.f;
-    double l = d_log ? warp_sum_d(ep.logphi) : 0.0;
-    double v = d_vm ? warp_sum_d(ep.viol) : 0.0;
-    double m = d_vm ? warp_sum_d(ep.mass) : 0.0;
-    double pl = d_pl ? warp_sum_d(ep.plogphi) : 0.0;
+    float v[7] = {has_out ? ep.mx_out : 0.f, has_phi ? ep.mx_phi : 0.f, d_log ? ep.lphi : 0.f,
+                  d_log ? ep.musum : 0.f, d_vm ? ep.a : 0.f, d_vm ? ep.dv : 0.f, d_pl ? ep.alog : 0.f};
+    v[0] = warp_max(v[0]);
+    v[1] = warp_max(v[1]);
+#pragma unroll
+    for (int q = 2; q < 7; ++q) v[q] = warp_sum(v[q]);
     unsigned int c = ep.clamps;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) { s_mx[0][w] = a; s_mx[1][w] = b; s_d[0][w] = l; s_d[1][w] = v; s_d[2][w] = m; s_d[3][w] = pl; s_c[w] = c; }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) s_f[q][w] = v[q];
+        s_c[w] = c;
+    }
     __syncthreads();
     if (w == 0) {
         const bool in = lane < nw;
-        a = has_out ? warp_max(in ? s_mx[0][lane] : 0.f) : 0.f;
-        b = has_phi ? warp_max(in ? s_mx[1][lane] : 0.f) : 0.f;
-        l = d_log ? warp_sum_d(in ? s_d[0][lane] : 0.0) : 0.0;
-        v = d_vm ? warp_sum_d(in ? s_d[1][lane] : 0.0) : 0.0;
-        m = d_vm ? warp_sum_d(in ? s_d[2][lane] : 0.0) : 0.0;
-        pl = d_pl ? warp_sum_d(in ? s_d[3][lane] : 0.0) : 0.0;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) v[q] = in ? s_f[q][lane] : 0.f;
+        v[0] = warp_max(v[0]);
+        v[1] = warp_max(v[1]);
+#pragma unroll
+        for (int q = 2; q < 7; ++q) v[q] = warp_sum(v[q]);
         c = in ? s_c[lane] : 0u;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         if (lane == 0) {
+            // FP64 only here: the block's sums combined with their scales
+            const double l = (double)v[2] + C.lsphi * (double)v[3];
+            const double m = C.E * (double)v[4];
+            const double vi = (double)v[5] / C.invEs;
+            const double pl = C.E * (double)v[6] + C.ls_phi_k * m;
             if (has_out) {
                 T.out_sc->ls = Lsrc;
-                atomic_max_pos(&T.out_sc->mx_bits, a);
+                atomic_max_pos(&T.out_sc->mx_bits, v[0]);
                 if (c) atomicAdd(&T.out_sc->clamped, c);
             }
             if (mode == EPI_MARG && T.acc_node) {
-                atomicAdd(T.acc_node + 0, v);
+                atomicAdd(T.acc_node + 0, vi);
                 atomicAdd(T.acc_node + 1, pl);
                 atomicAdd(T.acc_node + 2, m);
             }
             if (has_phi) {
                 T.phi_sc->ls = phi_logscale(T, tf, Lsrc);
-                atomic_max_pos(&T.phi_sc->mx_bits, b);
+                atomic_max_pos(&T.phi_sc->mx_bits, v[1]);
                 IterAcc* nxt = G.acc + ((iter + 1) % G.R);
-                if (l != 0.0) atomicAdd(&nxt->logphi, l);
+                if (d_log && l != 0.0) atomicAdd(&nxt->logphi, l);
                 if (mode == EPI_ROOT || mode == EPI_CROOT) {
                     IterAcc* cur = G.acc + (iter % G.R);
                     atomicAdd(&cur->mass, m);
-                    atomicAdd(&cur->rootviol, v);
+                    atomicAdd(&cur->rootviol, vi);
                 }
             }
         }

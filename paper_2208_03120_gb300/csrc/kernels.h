@@ -42,6 +42,25 @@ int fused2d_cluster_size();
 int fused2d_max_active_clusters();   // co-resident clusters of the fused kernel (0 before set-up)
 // msg_only: every task is a message product with a kernel sum (lean instance).
 cudaError_t launch_fused2d(const Task* tasks, int ntask, const Globals& G, cudaStream_t st, bool msg_only);
+// Persistent wavefront kernel: all products of a chunk in one launch of `nclusters` clusters, which
+// claim products in array order (a topological order) and wait for their dependencies' flags.
+struct WaveCtl {                 // zeroed once; the chunk prologue resets next / abort, advances epoch
+    int next;                    // claim counter
+    int epoch;                   // flags[i] == epoch: product i of the current launch completed
+    int abort;                   // set when a bounded wait ran out: no further claims
+    int pad;
+};
+struct WaveArgs {
+    const Task* tasks;
+    int ntask;
+    const int* deps;             // dependency lists (Task.dep0 / Task.ndep)
+    int* flags;                  // [ntask] completion flags
+    WaveCtl* ctl;
+    int* err;                    // bit 2 (value 4): a wait ran out
+    unsigned long long wait_ns;  // limit of every wait
+};
+int wave2d_max_active_clusters();    // co-resident clusters of the persistent kernel (0 before set-up)
+cudaError_t launch_wave2d(const WaveArgs& A, int nclusters, const Globals& G, cudaStream_t st);
 // Batched 1-D fast summation of the circle (grids n <= 128): per-point window taps and base cells
 // (once per solve), the circulant of D (once per edge), and one batch Y[c] = K (phi (.) X[c]):
 // stage 0 zeroes G and spreads, stage 1 convolves, interpolates and writes the messages.
@@ -52,9 +71,10 @@ cudaError_t launch_c1_batch(const float* X, const VecScale* sX, const float* phi
                             const float* ws, int ns, const int* l0t, const float* wt, int nt, int n0, int ng,
                             const float* cvec, float* G, float* Y, float floor_, VecScale* out_sc, cudaStream_t st,
                             int stage);
-// One-block iteration prologue (resets, iteration counter, accumulators).
+// One-block iteration prologue (resets, iteration counter, accumulators; with ctl: the persistent
+// kernel's claim counter and abort word reset and its epoch advanced).
 cudaError_t launch_prologue(VecScale* const* list, int nlist, int save_prev, int bump, double* zero_d, int zero_n,
-                            const Globals& G, cudaStream_t st);
+                            const Globals& G, cudaStream_t st, WaveCtl* ctl = nullptr);
 
 // ---- dense direct summation (dense.cu) ----------------------------------------------
 cudaError_t launch_dense(int d, const Task* tasks, int ntask, int ntb, int nsplit, const Globals& G,

@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(256) k_gather(const Task* __restrict__ tasks, 
             }
         }
     }
-    epi_block_finish(T, G, tf, Lsrc, ep, sP.iter);
+    epi_block_finish(T, G, tf, Lsrc, ep, sP.iter, C);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -504,30 +504,69 @@ __device__ __forceinline__ float group_sum(float v) {
     return v;
 }
 
-// MSG: every task of the launch is a message product (EPI_MSG, the backward levels): the
-// instance carries only that epilogue, which keeps its code (fetched cold at every launch) small.
+// Static shared memory of one fused product (one CTA of the cluster).
+struct __align__(16) F2Sh {
+    Task T;
+    FacCache fc, tf;
+    EpiConst sC;
+    EpiPre sP;
+    double sLsrc;
+    int s_ylo, s_yhi;                   // window rows of this CTA's targets
+    int s_next;                         // next spread batch of this CTA
+    float Gs[F2_N * F2_N];
+    float Grow[F2_MAXR * F2_N];
+    float2 Gx[F2_MAXR * (F2_M + 1)];
+    float2 Ycol[F2_MAXC][F2_N];
+    float2 Hk[F2_MAXC][2 * F2_M + 1];
+    float2 Acol[F2_MAXC][F2_N];
+    float2 Arow[F2_MAXR * (F2_M + 1)];
+    float Hrow[F2_MAXR * F2_N];
+    float2 tw[F2_N];
+};
+
+// Twiddles e^{-2 pi i k / n} (once per kernel: they depend on n only).
+__device__ __forceinline__ void f2_twiddles(F2Sh& S, int n) {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        float sn, cs;
+        sincospif(2.f * (float)k / (float)n, &sn, &cs);
+        S.tw[k] = make_float2(cs, -sn);
+    }
+}
+
+// Part of a product that reads only its own (static) task: the descriptor into shared memory,
+// the spread grid zeroed.  Visible to the block after the caller's next barrier.
+__device__ __forceinline__ void f2_prep(F2Sh& S, const Task* task, int n) {
+    load_task(S.T, task);
+    if (threadIdx.x == 0) {
+        S.s_ylo = 1 << 30;
+        S.s_yhi = -(1 << 30);
+        S.s_next = 0;
+    }
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) S.Gs[i] = 0.f;
+}
+
+// The product itself, after f2_prep and a block barrier, once the results of the products it
+// reads are complete.  Every CTA of the cluster calls it; it passes through the cluster barriers
+// below whatever the data.
+// MSG: the task is a message product (EPI_MSG with a kernel sum): the instance carries only that
+// epilogue, which keeps its code (fetched cold at every launch of the one-shot kernel) small.  The
+// persistent kernel runs the general instance for every product (its code stays resident, and a
+// second inlined instance would push it past the register budget of 640 threads).
 template <bool MSG>
-__global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restrict__ tasks, Globals G) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cluster = cg::this_cluster();
-    __shared__ Task T;
-    __shared__ FacCache fc, tf;
-    __shared__ double sLsrc;
-    __shared__ EpiConst sC;
-    __shared__ EpiPre sP;
-    __shared__ int s_ylo, s_yhi;                   // window rows of this CTA's targets
-    __shared__ int s_next;                         // next spread batch of this CTA
-    __shared__ float Gs[F2_N * F2_N];
-    __shared__ float Grow[F2_MAXR * F2_N];
-    __shared__ float2 Gx[F2_MAXR * (F2_M + 1)];
-    __shared__ float2 Ycol[F2_MAXC][F2_N];
-    __shared__ float2 Hk[F2_MAXC][2 * F2_M + 1];
-    __shared__ float2 Acol[F2_MAXC][F2_N];
-    __shared__ float2 Arow[F2_MAXR * (F2_M + 1)];
-    __shared__ float Hrow[F2_MAXR * F2_N];
-    __shared__ float2 tw[F2_N];
-    extern __shared__ float4 f2_dyn[];             // spread staging, SP2_WARP floats per warp
-    float* f2_stage = reinterpret_cast<float*>(f2_dyn);
+__device__ __forceinline__ void f2_run(F2Sh& S, float* f2_stage, const Globals& G,
+                                       cooperative_groups::cluster_group& cluster) {
+    const Task& T = S.T;
+    FacCache& fc = S.fc;
+    FacCache& tf = S.tf;
+    float* Gs = S.Gs;
+    float* Grow = S.Grow;
+    float2* Gx = S.Gx;
+    auto& Ycol = S.Ycol;
+    auto& Hk = S.Hk;
+    auto& Acol = S.Acol;
+    float2* Arow = S.Arow;
+    float* Hrow = S.Hrow;
+    const float2* tw = S.tw;
     float* sUx = f2_stage + (F2_THREADS / 32) * SP2_WARP;   // this rank's sources: x, y, value
     float* sUy = sUx + F2_SLOTS;
     float* sVv = sUy + F2_SLOTS;
@@ -536,33 +575,13 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
     const int lane = tid & 31, warp = tid >> 5;
     const int CS = (int)cluster.num_blocks();
     const int r = (int)cluster.block_rank();
-    load_task(T, tasks + blockIdx.y);
     const int n = G.n_grid, M = G.M, mask = n - 1;
-    if (tid == 0) {
-        s_ylo = 1 << 30;
-        s_yhi = -(1 << 30);
-        s_next = 0;
-    }
-    for (int i = tid; i < n * n; i += nt) Gs[i] = 0.f;
-    for (int k = tid; k < n; k += nt) {
-        float sn, cs;
-        sincospif(2.f * (float)k / (float)n, &sn, &cs);
-        tw[k] = make_float2(cs, -sn);                  // e^{-2 pi i k / n}
-    }
-    // Launched with programmatic stream serialisation: everything above uses only this launch's
-    // own (static) task; from here on the kernel reads what the previous launch wrote (scale
-    // records, messages, scalings), so it waits for that grid to complete and flush.  The next
-    // launch may then be scheduled: its blocks do their own set-up and wait in the same way, so
-    // at most one launch runs ahead.
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    __syncthreads();
     if (r == 0 && tid == 0) task_resets(T, G, 0);
     if constexpr (MSG) {
         if (warp == 0) fill_factors_warp(fc, G.fac, T.sf0, T.snf, lane);
         __syncthreads();
     } else {
-        load_task_consts(T, G, fc, tf, sP, sC, sLsrc);   // constants visible after the next barrier
+        load_task_consts(T, G, fc, tf, S.sP, S.sC, S.sLsrc);   // constants visible after the next barrier
     }
     const bool fast = MSG || T.hgrid != nullptr;
     EpiPartial ep;
@@ -614,7 +633,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
             };
             for (;;) {
                 int k = 0;
-                if (lane == 0) k = atomicAdd(&s_next, 1);
+                if (lane == 0) k = atomicAdd(&S.s_next, 1);
                 k = __shfl_sync(0xffffffffu, k, 0);
                 if (k >= nbr) break;
                 const int cnt = min(SP2_B, Ns - (r + CS * k) * SP2_B);
@@ -638,8 +657,8 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
                 hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
             }
             if (lane == 0 && lo <= hi) {
-                atomicMin(&s_ylo, lo);
-                atomicMax(&s_yhi, hi);
+                atomicMin(&S.s_ylo, lo);
+                atomicMax(&S.s_yhi, hi);
             }
         }
         cluster.sync();
@@ -764,7 +783,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
         cluster.sync();
         // ---- 5. copy the rows of h this CTA reads, interpolate (one thread per target) -------
         {
-            int ylo = s_ylo, nrows = s_yhi >= s_ylo ? s_yhi - s_ylo + MOT_W : 0;
+            int ylo = S.s_ylo, nrows = S.s_yhi >= S.s_ylo ? S.s_yhi - S.s_ylo + MOT_W : 0;
             if (nrows >= n) {
                 ylo = 0;
                 nrows = n;
@@ -793,7 +812,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
         }
         cluster.sync();      // peers may now leave; Hrow of this CTA is no longer read
         EpiConst C;
-        if constexpr (!MSG) C = sC;
+        if constexpr (!MSG) C = S.sC;
         const int i0 = ti0, i1 = ti1;
         for (int i = i0 + tid; i < i1; i += nt) {
             const bool first = i == i0 + tid;       // prefetched at the kernel's start
@@ -829,13 +848,123 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
     } else if constexpr (!MSG) {
         // node step without a kernel product; the cluster barrier orders the reset above
         cluster.sync();
-        const EpiConst C = sC;
+        const EpiConst C = S.sC;
         for (int i = ti0 + tid; i < ti1; i += nt) epilogue_point(T, tf, C, G.floor_, i, 1.f, ep);
     }
     if constexpr (MSG)
         epi_block_finish_msg(T, fc.L, ep);
     else
-        epi_block_finish(T, G, tf, sLsrc, ep, sP.iter);
+        epi_block_finish(T, G, tf, S.sLsrc, ep, S.sP.iter, S.sC);
+}
+
+// One product per cluster (blockIdx.y): the launch-per-level form of the fused product.
+template <bool MSG>
+__global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restrict__ tasks, Globals G) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ F2Sh S;
+    extern __shared__ float4 f2_dyn[];             // spread staging, SP2_WARP floats per warp
+    f2_prep(S, tasks + blockIdx.y, G.n_grid);
+    f2_twiddles(S, G.n_grid);
+    // Launched with programmatic stream serialisation: everything above uses only this launch's
+    // own (static) task; from here on the kernel reads what the previous launch wrote (scale
+    // records, messages, scalings), so it waits for that grid to complete and flush.  The next
+    // launch may then be scheduled: its blocks do their own set-up and wait in the same way, so
+    // at most one launch runs ahead.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    __syncthreads();
+    f2_run<MSG>(S, reinterpret_cast<float*>(f2_dyn), G, cluster);
+}
+
+// ------------------------------------------------------------------------------------------
+// Persistent wavefront kernel: every product of a chunk of tree sweeps in one launch.
+//
+// Clusters claim products from a counter in the order of the host's list schedule (a
+// topological order of the chunk's dependency graph), and a product waits until every product
+// it depends on has completed (per-product flags holding the launch's epoch).  A cluster waits
+// only for products claimed before its own, and those are held by clusters that are already
+// running, so the chunk completes whether or not all clusters are resident at once.  Claims run
+// one product ahead (the next index is taken while the current product runs, published by its
+// first cluster barrier and read by every CTA before the product's last one, so that rank 0 may
+// leave as soon as the others have passed it).  Completion: every thread fences its writes, the cluster barrier, then
+// rank 0 stores the flag with release semantics; a waiting CTA reads the flags with acquire
+// semantics before its block barrier.  Every wait is bounded (wait_ns of %globaltimer): on expiry
+// the CTA sets bit 2 (value 4) of the error word and the abort word, which stops all claims; the
+// cluster still runs its product (on whatever data) so that every CTA meets every cluster barrier.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long f2_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int wave_claim(const WaveArgs& A) {
+    if (*reinterpret_cast<volatile int*>(&A.ctl->abort)) return A.ntask;
+    return atomicAdd(&A.ctl->next, 1);
+}
+
+// Warp 0 waits: lane q polls the flags of dependencies q, q + 32, ... (one round trip to L2 for
+// all of them instead of one per dependency), each lane bounded by wait_ns.
+__device__ __forceinline__ void wave_wait_warp(const WaveArgs& A, int i, int epoch, int lane) {
+    const int d0 = A.tasks[i].dep0, nd = A.tasks[i].ndep;
+    unsigned long long t0 = 0;
+    for (int q = lane; q < nd; q += 32) {
+        const int* f = A.flags + A.deps[d0 + q];
+        while (ld_acquire_gpu(f) != epoch) {
+            if (*reinterpret_cast<volatile int*>(&A.ctl->abort)) return;
+            const unsigned long long now = f2_globaltimer();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > A.wait_ns) {
+                atomicOr(A.err, 4);
+                atomicExch(&A.ctl->abort, 1);
+                return;
+            }
+            __nanosleep(32);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(F2_THREADS, 1) k_wave2d(WaveArgs A, Globals G) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ F2Sh S;
+    __shared__ int s_claim;                         // rank 0's latest claim
+    extern __shared__ float4 f2_dyn[];
+    float* dyn = reinterpret_cast<float*>(f2_dyn);
+    const int tid = threadIdx.x;
+    const int r = (int)cluster.block_rank();
+    const int n = G.n_grid;
+    const int epoch = *reinterpret_cast<volatile int*>(&A.ctl->epoch);   // advanced by the prologue
+    f2_twiddles(S, n);
+    if (r == 0 && tid == 0) s_claim = wave_claim(A);
+    cluster.sync();
+    int i = *cluster.map_shared_rank(&s_claim, 0);
+    // A CTA may leave only once no peer reads its shared memory any more: every read of rank 0's
+    // claim is followed by a cluster barrier before the loop test can end the kernel.
+    cluster.sync();
+    while (i < A.ntask) {
+        f2_prep(S, A.tasks + i, n);
+        // the next claim, written before f2_run and published by its first cluster barrier
+        if (r == 0 && tid == 0) s_claim = wave_claim(A);
+        if (tid < 32) wave_wait_warp(A, i, epoch, tid);
+        __syncthreads();
+        f2_run<false>(S, dyn, G, cluster);   // one instance for every mode (code stays resident)
+        const int next = *cluster.map_shared_rank(&s_claim, 0);
+        __threadfence();
+        cluster.sync();                      // product complete; every read of s_claim done
+        if (r == 0 && tid == 0) st_release_gpu(A.flags + i, epoch);
+        i = next;
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -844,7 +973,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
 // iteration produces.  Runs alone, so every later kernel of the iteration sees it.
 // ------------------------------------------------------------------------------------------
 __global__ void k_prologue(VecScale* const* __restrict__ list, int nlist, int save_prev, int bump,
-                           double* zero_d, int zero_n, Globals G) {
+                           double* zero_d, int zero_n, Globals G, WaveCtl* ctl) {
     // launched with programmatic stream serialisation: wait for the previous grid, then let the
     // next launch get scheduled (it waits for this one in the same way)
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -860,6 +989,11 @@ __global__ void k_prologue(VecScale* const* __restrict__ list, int nlist, int sa
         s->clamped = 0u;
     }
     for (int i = t; i < zero_n; i += blockDim.x) zero_d[i] = 0.0;
+    if (ctl != nullptr && t == 0) {
+        ctl->next = 0;
+        ctl->abort = 0;
+        ctl->epoch = ctl->epoch + 1;
+    }
     // advance the sweep counter by `bump` sweeps and clear their accumulator slots: sweep s adds
     // its scalings' logarithms to slot s + 1 and its root mass to slot s
     if (bump > 0 && t == 0) {
@@ -1189,6 +1323,8 @@ namespace {
 int g_cluster_size[kMaxDevices] = {};
 // clusters of the fused kernel that fit on the GPU at once (cudaOccupancyMaxActiveClusters)
 int g_cluster_active[kMaxDevices] = {};
+// the same for the persistent wavefront kernel
+int g_wave_active[kMaxDevices] = {};
 
 int current_device() {
     int dev = 0;
@@ -1199,6 +1335,7 @@ int current_device() {
 
 int fused2d_cluster_size() { return g_cluster_size[current_device()]; }
 int fused2d_max_active_clusters() { return g_cluster_active[current_device()]; }
+int wave2d_max_active_clusters() { return g_wave_active[current_device()]; }
 
 bool fused2d_supported(int d, int n) {
     return d == 2 && n >= 16 && n <= F2_N && g_cluster_size[current_device()] > 0;
@@ -1217,7 +1354,11 @@ cudaError_t prepare_fused2d() {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, F2_DYN_SMEM);
         if (e != cudaSuccess) return e;
     }
-    for (int cs : {16, 8}) {
+    e = cudaFuncSetAttribute(k_wave2d, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) cudaGetLastError();
+    e = cudaFuncSetAttribute(k_wave2d, cudaFuncAttributeMaxDynamicSharedMemorySize, F2_DYN_SMEM);
+    if (e != cudaSuccess) return e;
+    auto active = [](const void* fn, int cs) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cs, 1, 1);
         cfg.blockDim = dim3(F2_THREADS, 1, 1);
@@ -1230,13 +1371,20 @@ cudaError_t prepare_fused2d() {
         cfg.attrs = &attr;
         cfg.numAttrs = 1;
         int nclusters = 0;
-        e = cudaOccupancyMaxActiveClusters(&nclusters, k_fastsum2d<false>, &cfg);
-        if (e == cudaSuccess && nclusters > 0) {
-            g_cluster_active[current_device()] = nclusters;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return nclusters;
+    };
+    for (int cs : {16, 8}) {
+        const int nc = active((const void*)k_fastsum2d<false>, cs);
+        if (nc > 0) {
+            g_cluster_active[current_device()] = nc;
+            g_wave_active[current_device()] = active((const void*)k_wave2d, cs);
             csz = cs;
             return cudaSuccess;
         }
-        cudaGetLastError();
     }
     csz = -1;
     return cudaSuccess;
@@ -1263,8 +1411,27 @@ cudaError_t launch_fused2d(const Task* tasks, int ntask, const Globals& G, cudaS
                     : cudaLaunchKernelEx(&cfg, k_fastsum2d<false>, tasks, G);
 }
 
+cudaError_t launch_wave2d(const WaveArgs& A, int nclusters, const Globals& G, cudaStream_t st) {
+    if (A.ntask <= 0) return cudaSuccess;
+    const int cs = g_cluster_size[current_device()];
+    if (cs <= 0 || nclusters <= 0) return cudaErrorInvalidConfiguration;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs * nclusters, 1, 1);
+    cfg.blockDim = dim3(F2_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = F2_DYN_SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;   // no programmatic serialisation: the kernel
+    attr.val.clusterDim.x = cs;                      // reads the prologue's epoch at its start
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_wave2d, A, G);
+}
+
 cudaError_t launch_prologue(VecScale* const* list, int nlist, int save_prev, int bump, double* zero_d, int zero_n,
-                            const Globals& G, cudaStream_t st) {
+                            const Globals& G, cudaStream_t st, WaveCtl* ctl) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(1, 1, 1);
     cfg.blockDim = dim3(256, 1, 1);
@@ -1274,7 +1441,7 @@ cudaError_t launch_prologue(VecScale* const* list, int nlist, int save_prev, int
     attr.val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_prologue, list, nlist, save_prev, bump, zero_d, zero_n, G);
+    return cudaLaunchKernelEx(&cfg, k_prologue, list, nlist, save_prev, bump, zero_d, zero_n, G, ctl);
 }
 
 // ---- window coefficients ----------------------------------------------------------------------

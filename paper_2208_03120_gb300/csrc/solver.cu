@@ -7,6 +7,7 @@
 // pass recomputes beta_k level by level from the leaves.  Every message and scaling is stored
 // as FP32 mantissas with an FP64 log-scale (VecScale); the dual value, marginal violation and
 // cost are FP64 reductions.
+#include <atomic>
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -44,6 +45,10 @@ void set_cuda_error(cudaError_t e, const char* what) {
         int _r = (x);                            \
         if (_r != MOT_OK) return _r;             \
     } while (0)
+
+// test hook (mot_test_wave_clusters): clusters of the persistent wavefront kernel, 0 = as many as
+// are co-resident on an idle GPU
+std::atomic<int> g_wave_clusters_override{0};
 
 int max_grid(int d) { return d == 1 ? 4096 : (d == 2 ? 128 : 64); }
 
@@ -249,6 +254,7 @@ int make_D_for(double eta_e_norm, const GridChoice& g, int d, const mot_options&
 // =============================================================================================
 struct Level {
     std::vector<Task> src, tgt;   // host copies
+    std::vector<int> node;        // wavefront chunk: graph node of every tgt task
     Task* d_src = nullptr;
     Task* d_tgt = nullptr;
     int grid_src = 1, grid_tgt = 1, ntb = 1, nsplit = 1;
@@ -310,6 +316,16 @@ struct TreePlan {
     int graph_par = -1;                        // starting copy of the captured chunk
     size_t wave_root_reset = 0;                // reset-list entry of the root's scale record
     long long launches_per_chunk = 0;
+    // persistent wavefront kernel (options.wavefront = 1): the whole chunk in one launch
+    bool persist = false;
+    int wave_clusters = 0;                     // clusters launched (co-resident on an idle GPU)
+    int wave_ntask = 0;
+    int* d_deps = nullptr;                     // dependency lists of the chunk's products
+    size_t deps_cap = 0;
+    int* d_flags = nullptr;                    // completion flags (epoch of the launch)
+    WaveCtl* d_ctl = nullptr;
+    bool wave_chk = false;                     // the chunk schedule ends with the check pass
+    bool check_done = false;                   // the last chunk run included the check pass
     Globals G;
     // graph
     cudaGraphExec_t gexec = nullptr;
@@ -496,6 +512,11 @@ void layout_tree(Arena& A, TreePlan& T) {
     T.d_tasks = A.take<Task>(24 * (size_t)K + 16);
     T.wtask_cap = (size_t)kWaveMax * (2 * (size_t)K + 1);
     T.d_wtasks = A.take<Task>(T.wtask_cap);
+    // dependency lists: per sweep at most about 6 K edges, and the check pass at most K (K + 2)
+    T.deps_cap = (size_t)kWaveMax * (7 * (size_t)K + 8) + (size_t)K * (K + 4);
+    T.d_deps = A.take<int>(T.deps_cap);
+    T.d_flags = A.take<int>(T.wtask_cap);
+    T.d_ctl = A.take<WaveCtl>(1);
 }
 
 // ---- task construction ------------------------------------------------------------------
@@ -547,6 +568,27 @@ void edge_grids(TreePlan& T, Task& t, int k, float* raw) {
     const double eta_e = T.eta / T.w[k];
     const double eta_n = eta_e / (T.g.s * T.g.s);
     t.eta_u = (float)(eta_n * (double)T.g.n * (double)T.g.n);
+}
+
+// Check pass task of node k (Theorem 4.1 at the current scalings, beta copy q): EPI_MARG with the
+// exact forward message gamma-ex_k = K^T (phi^p (.) gamma-ex_p (.) beta^{C_p \ k}), or for the root
+// (no kernel sum) its marginal from its children's messages.
+Task check_task(TreePlan& T, int k, int q) {
+    Task t = blank_task();
+    if (k > 0) {
+        src_general(T, t, T.parent[k], k, true, 2, q);
+        edge_grids(T, t, k, T.rawc[k]);
+        t.out = T.gex[k];
+        t.out_sc = T.gex_sc(k);
+    }
+    t.tgt = ps_of(T, k);
+    t.mode = EPI_MARG;
+    tgt_children(T, t, k, true, q);
+    t.mu_d = T.free_[k] ? nullptr : T.sets[k].mu_d;
+    t.phi = T.phi[k];
+    t.phi_sc = T.phi_sc(k);
+    t.acc_node = T.acc_node + 3 * k;
+    return t;
 }
 
 void build_tasks(TreePlan& T) {
@@ -638,31 +680,11 @@ void build_tasks(TreePlan& T) {
         std::vector<Level>& chk = q ? T.chk1 : T.chk;
         chk.assign(std::max(maxdepth, 1), Level());
         for (int k = 1; k < K; ++k) {
-            const int p = T.parent[k];
-            Task t = blank_task();
-            src_general(T, t, p, k, true, 2, q);
-            edge_grids(T, t, k, T.rawc[k]);
-            t.tgt = ps_of(T, k);
-            t.mode = EPI_MARG;
-            tgt_children(T, t, k, true, q);
-            t.mu_d = T.free_[k] ? nullptr : T.sets[k].mu_d;
-            t.out = T.gex[k];
-            t.out_sc = T.gex_sc(k);
-            t.phi = T.phi[k];
-            t.phi_sc = T.phi_sc(k);
-            t.acc_node = T.acc_node + 3 * k;
+            Task t = check_task(T, k, q);
             chk[T.depth[k] - 1].src.push_back(t);
             chk[T.depth[k] - 1].tgt.push_back(t);
         }
-        Task t = blank_task();
-        t.tgt = ps_of(T, 0);
-        t.mode = EPI_MARG;
-        tgt_children(T, t, 0, true, q);
-        t.mu_d = T.free_[0] ? nullptr : T.sets[0].mu_d;
-        t.phi = T.phi[0];
-        t.phi_sc = T.phi_sc(0);
-        t.acc_node = T.acc_node;
-        chk[0].tgt.push_back(t);
+        chk[0].tgt.push_back(check_task(T, 0, q));
     }
     T.ck_reset0 = T.resets.size();
     for (int k = 1; k < K; ++k) T.resets.push_back(T.gex_sc(k));
@@ -749,7 +771,8 @@ int upload_tasks(TreePlan& T, cudaStream_t st) {
 // parent[0] = -1, parent[k] < k), at most `cap` products per launch.  Fills tF / tB [S][K]
 // (entries k >= 1), tR [S], the carrier child of each R(s) (s >= 1, -1 for s = 0) and the number
 // of launches.  MOT_EUNSUPPORTED if no child of the root can carry the root's record.
-int wave_times(int K, const int* parent, int S, int cap, int* tF, int* tB, int* tR, int* carrier, int* nlaunch) {
+int wave_times(int K, const int* parent, int S, int cap, int* tF, int* tB, int* tR, int* carrier, int* nlaunch,
+               std::vector<std::vector<int>>* pred_out = nullptr) {
     if (K < 2 || S < 1 || cap < 1 || !parent || parent[0] != -1) return MOT_EINVAL;
     std::vector<std::vector<int>> children(K);
     for (int k = 1; k < K; ++k) {
@@ -838,6 +861,7 @@ int wave_times(int K, const int* parent, int S, int cap, int* tF, int* tB, int* 
             tB[(size_t)s * K + k] = when[B_(s, k)];
         }
     }
+    if (pred_out) *pred_out = pred;
     // the root scaling's record is saved and reset by the last product B_c(s-1) of a child c of the
     // root: it runs after R(s-1) (an edge above) and before R(s) (which waits for it)
     carrier[0] = -1;
@@ -851,16 +875,22 @@ int wave_times(int K, const int* parent, int S, int cap, int* tF, int* tB, int* 
     return MOT_OK;
 }
 
-int build_wave(TreePlan& T, int S, int q0, cudaStream_t st) {
+// with_check (persistent kernel only): the chunk ends with the check pass at its final scalings,
+// each check product waiting for exactly the products whose results it reads.
+int build_wave(TreePlan& T, int S, int q0, bool with_check, cudaStream_t st) {
     const int K = T.K;
     T.fac.resize(T.fac_base);
     T.resets.resize(T.res_base);
     // a launch takes at most as many products as clusters fit on the GPU at once (one more would
     // run as a second wave); a product that finds its first possible launch full takes the next
-    const int cap = std::max(1, fused2d_max_active_clusters() > 0 ? fused2d_max_active_clusters() : 8);
+    // (the persistent kernel: as many products as it runs clusters)
+    const int ncl = T.persist ? T.wave_clusters : fused2d_max_active_clusters();
+    const int cap = std::max(1, ncl > 0 ? ncl : 8);
     std::vector<int> tFf((size_t)S * K), tBf((size_t)S * K), tR(S), carrier(S);
     int nlaunch = 0;
-    RET(wave_times(K, T.parent.data(), S, cap, tFf.data(), tBf.data(), tR.data(), carrier.data(), &nlaunch));
+    std::vector<std::vector<int>> pred;
+    RET(wave_times(K, T.parent.data(), S, cap, tFf.data(), tBf.data(), tR.data(), carrier.data(), &nlaunch, &pred));
+    const int W = 2 * K - 1;                   // graph nodes of sweep s: R = sW, F_k = sW + k, B_k = sW + K - 1 + k
     auto tF = [&](int s, int k) { return tFf[(size_t)s * K + k]; };
     auto tB = [&](int s, int k) { return tBf[(size_t)s * K + k]; };
     T.wlev.assign(nlaunch, Level());
@@ -894,6 +924,7 @@ int build_wave(TreePlan& T, int S, int q0, cudaStream_t st) {
             t.reset_list = (VecScale* const*)(uintptr_t)r0;
             t.iter_off = off;
             T.wlev[tF(s, k)].tgt.push_back(t);
+            T.wlev[tF(s, k)].node.push_back(s * W + k);
         }
         {                                      // R(s): mass of the last iterate, then phi^1
             Task t = blank_task();
@@ -906,6 +937,7 @@ int build_wave(TreePlan& T, int S, int q0, cudaStream_t st) {
             t.phi_sc = T.phi_sc(0);
             t.iter_off = off;
             T.wlev[tR[s]].tgt.push_back(t);
+            T.wlev[tR[s]].node.push_back(s * W);
         }
         for (int k = K - 1; k >= 1; --k) {    // B_k(s) into the other copy
             Task t = blank_task();
@@ -925,11 +957,50 @@ int build_wave(TreePlan& T, int S, int q0, cudaStream_t st) {
             }
             t.reset_list = (VecScale* const*)(uintptr_t)r0;
             T.wlev[tB(s, k)].tgt.push_back(t);
+            T.wlev[tB(s, k)].node.push_back(s * W + K - 1 + k);
+        }
+    }
+    // the check pass (Theorem 4.1 at the chunk's final scalings, beta copy qf): node S W + k;
+    // BFS order puts every parent before its children.  Each check product resets the record of
+    // the message it writes and zeroes its node's accumulators (it is their only writer).
+    const int qf = (q0 + S) & 1;
+    if (with_check) {
+        T.wlev.emplace_back();
+        Level& L = T.wlev.back();
+        for (int k = 0; k < K; ++k) {
+            Task t = check_task(T, k, qf);
+            t.zero_d = T.acc_node + 3 * k;
+            t.zero_n = 3;
+            if (k > 0) {
+                const size_t r0 = T.resets.size();
+                T.resets.push_back(T.gex_sc(k));
+                t.reset_n = 1;
+                t.reset_list = (VecScale* const*)(uintptr_t)r0;
+            }
+            L.tgt.push_back(t);
+            L.node.push_back(S * W + k);
+        }
+        pred.resize((size_t)S * W + K);
+        const int s = S - 1;
+        auto Fn = [&](int k) { return k == 0 ? s * W : s * W + k; };   // producer of phi^k
+        auto Bn = [&](int k) { return s * W + K - 1 + k; };
+        for (int k = 0; k < K; ++k) {
+            std::vector<int>& pr = pred[(size_t)S * W + k];
+            pr.push_back(Fn(k));                                       // phi^k
+            for (int c : T.children[k]) pr.push_back(Bn(c));           // its children's beta
+            if (k > 0) {
+                const int p = T.parent[k];
+                pr.push_back(Fn(p));                                   // phi^p
+                if (p > 0) pr.push_back(S * W + p);                    // gamma-ex_p
+                for (int c : T.children[p])
+                    if (c != k) pr.push_back(Bn(c));                   // the siblings' beta
+            }
         }
     }
     // upload the chunk's factors, resets and tasks
     if (T.fac.size() > T.fac_cap || T.resets.size() > T.res_cap) return MOT_EUNSUPPORTED;
     std::vector<Task> all;
+    std::vector<int> flat_of((size_t)S * W + K, -1), node_of;
     for (auto& L : T.wlev) {
         L.src.clear();
         L.msg_only = !L.tgt.empty();
@@ -937,9 +1008,98 @@ int build_wave(TreePlan& T, int S, int q0, cudaStream_t st) {
             if (t.reset_n > 0) t.reset_list = T.d_resets + (uintptr_t)t.reset_list;
             L.msg_only = L.msg_only && t.mode == EPI_MSG && t.hgrid != nullptr;
         }
-        for (auto& t : L.tgt) all.push_back(t);
+        for (size_t j = 0; j < L.tgt.size(); ++j) {
+            flat_of[L.node[j]] = (int)all.size();
+            node_of.push_back(L.node[j]);
+            all.push_back(L.tgt[j]);
+        }
     }
     if (all.size() > T.wtask_cap) return MOT_EUNSUPPORTED;
+    if (T.persist) {
+        // claim order of the persistent kernel: the start order of a greedy schedule simulated on
+        // its clusters, each free cluster taking the ready product with the longest remaining
+        // chain of dependent work.  Products are weighted by their measured cost (a message
+        // product 1; a scaling update 1.1; a check product 1.25; the root updates, which have no
+        // kernel sum, 0.4).  Start times follow finish times of predecessors, so the order is
+        // topological.
+        const int n = (int)all.size();
+        std::vector<double> wgt(n);
+        for (int i = 0; i < n; ++i) {
+            const int u = node_of[i];
+            if (u >= S * W) wgt[i] = u == S * W ? 0.4 : 1.25;       // check products
+            else if (u % W == 0) wgt[i] = 0.4;                       // R(s)
+            else if (u % W < K) wgt[i] = 1.1;                        // F_k(s)
+            else wgt[i] = 1.0;                                       // B_k(s)
+        }
+        std::vector<std::vector<int>> ps(n), sc(n);
+        for (int i = 0; i < n; ++i)
+            for (int u : pred[node_of[i]]) {
+                const int j = flat_of[u];
+                if (j < 0 || j >= i) return MOT_EUNSUPPORTED;        // (never: launch order is topological)
+                ps[i].push_back(j);
+                sc[j].push_back(i);
+            }
+        std::vector<double> tail(n, 0.0), fin(n, 0.0), start(n, 0.0), ready_t(n, 0.0);
+        for (int i = n - 1; i >= 0; --i) {
+            double m = 0.0;
+            for (int v : sc[i]) m = std::max(m, tail[v]);
+            tail[i] = wgt[i] + m;
+        }
+        std::vector<int> pending(n), ready;
+        for (int i = 0; i < n; ++i) {
+            pending[i] = (int)ps[i].size();
+            if (pending[i] == 0) ready.push_back(i);
+        }
+        std::vector<double> cf(std::max(1, T.wave_clusters), 0.0);
+        for (int placed = 0; placed < n; ++placed) {
+            const int c = (int)(std::min_element(cf.begin(), cf.end()) - cf.begin());
+            double t = cf[c], tmin = 1e300;
+            for (int v : ready) tmin = std::min(tmin, ready_t[v]);
+            if (ready.empty()) return MOT_EUNSUPPORTED;                // (never: acyclic)
+            t = std::max(t, tmin);
+            int best = -1;
+            for (int v : ready)
+                if (ready_t[v] <= t && (best < 0 || tail[v] > tail[best] || (tail[v] == tail[best] && v < best))) best = v;
+            start[best] = t;
+            fin[best] = t + wgt[best];
+            cf[c] = fin[best];
+            ready.erase(std::find(ready.begin(), ready.end(), best));
+            for (int v : sc[best])
+                if (--pending[v] == 0) {
+                    double rt = 0.0;
+                    for (int u : ps[v]) rt = std::max(rt, fin[u]);
+                    ready_t[v] = rt;
+                    ready.push_back(v);
+                }
+        }
+        std::vector<int> perm(n);
+        for (int i = 0; i < n; ++i) perm[i] = i;
+        std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return start[a] < start[b]; });
+        std::vector<Task> all2(n);
+        std::vector<int> node2(n);
+        for (int i = 0; i < n; ++i) {
+            all2[i] = all[perm[i]];
+            node2[i] = node_of[perm[i]];
+            flat_of[node2[i]] = i;
+        }
+        all.swap(all2);
+        node_of.swap(node2);
+    }
+    // dependency lists of the persistent kernel: the products each one waits for (all earlier in
+    // the array, which is in a topological order)
+    std::vector<int> deps;
+    for (size_t i = 0; i < all.size(); ++i) {
+        all[i].dep0 = (int)deps.size();
+        for (int u : pred[node_of[i]]) {
+            const int j = flat_of[u];
+            if (j < 0 || j >= (int)i) return MOT_EUNSUPPORTED;   // (never: the order is topological)
+            deps.push_back(j);
+        }
+        all[i].ndep = (int)deps.size() - all[i].dep0;
+    }
+    if (deps.size() > T.deps_cap) return MOT_EUNSUPPORTED;
+    if (!deps.empty()) CK(cudaMemcpyAsync(T.d_deps, deps.data(), sizeof(int) * deps.size(), cudaMemcpyHostToDevice, st));
+    T.wave_ntask = (int)all.size();
     CK(cudaMemcpyAsync(T.d_fac + T.fac_base, T.fac.data() + T.fac_base, sizeof(Factor) * (T.fac.size() - T.fac_base),
                        cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(T.d_resets + T.res_base, T.resets.data() + T.res_base,
@@ -953,6 +1113,7 @@ int build_wave(TreePlan& T, int S, int q0, cudaStream_t st) {
     }
     T.wave_S = S;
     T.wave_q0 = q0;
+    T.wave_chk = with_check;
     return MOT_OK;
 }
 
@@ -1109,9 +1270,24 @@ int run_check(TreePlan& T, cudaStream_t st, Timer& tm, long long& nl) {
 int run_wave(TreePlan& T, int S, cudaStream_t st, Timer& tm, long long& nl) {
     cudaEvent_t e = nullptr;
     RET(tm.begin(MOT_K_NODE, &e));
-    CK(launch_prologue(T.d_resets + T.wave_root_reset, 1, 1, S, nullptr, 0, T.G, st));
+    CK(launch_prologue(T.d_resets + T.wave_root_reset, 1, 1, S, nullptr, 0, T.G, st, T.persist ? T.d_ctl : nullptr));
     RET(tm.end(e));
     nl += 1;
+    if (T.persist) {
+        WaveArgs A;
+        A.tasks = T.d_wtasks;
+        A.ntask = T.wave_ntask;
+        A.deps = T.d_deps;
+        A.flags = T.d_flags;
+        A.ctl = T.d_ctl;
+        A.err = T.err;
+        A.wait_ns = 1000000000ull;            // 1 s per wait (a chunk takes about a millisecond)
+        RET(tm.begin(MOT_K_FUSED, &e));
+        CK(launch_wave2d(A, T.wave_clusters, T.G, st));
+        RET(tm.end(e));
+        nl += 1;
+        return MOT_OK;
+    }
     for (auto& L : T.wlev) RET(run_level(T, L, st, tm, nl));
     return MOT_OK;
 }
@@ -1162,8 +1338,9 @@ int run_iterations(TreePlan& T, int count, cudaStream_t st, Timer& tm, long long
         const int parts = (count + kWaveMax - 1) / kWaveMax;
         for (int i = 0; i < parts; ++i) {
             const int c = count / parts + (i < count % parts ? 1 : 0);
-            if (T.wave_S != c || T.wave_q0 != T.par) {
-                const int rc = build_wave(T, c, T.par, st);
+            const bool chk = T.persist && i == parts - 1;   // the persistent launch ends with the check
+            if (T.wave_S != c || T.wave_q0 != T.par || T.wave_chk != chk) {
+                const int rc = build_wave(T, c, T.par, chk, st);
                 if (rc != MOT_OK) {
                     // no valid wavefront (never expected): sweep by sweep, which reads the first
                     // beta copy, so only from a point where that copy is the latest
@@ -1178,6 +1355,7 @@ int run_iterations(TreePlan& T, int count, cudaStream_t st, Timer& tm, long long
                 }
             }
             RET(run_wave_chunk(T, c, st, tm, nl, graphs));
+            if (chk) T.check_done = true;
         }
         return MOT_OK;
     }
@@ -1312,6 +1490,13 @@ int tree_plan_setup(const mot_problem* P, const mot_options& o, TreePlan& T, voi
         bool any_free = false;
         for (int k = 0; k < T.K; ++k) any_free = any_free || T.free_[k];
         T.wave = T.fused && !any_free && o.wavefront > 0;
+        T.wave_clusters = g_wave_clusters_override.load() > 0 ? g_wave_clusters_override.load()
+                                                               : wave2d_max_active_clusters();
+        T.persist = T.wave && o.wavefront == 1 && T.wave_clusters > 0;
+        if (T.wave) {
+            CK(cudaMemsetAsync(T.d_flags, 0, sizeof(int) * T.wtask_cap, st));
+            CK(cudaMemsetAsync(T.d_ctl, 0, sizeof(WaveCtl), st));
+        }
         size_t gsz = 1;
         for (int t = 0; t < T.d; ++t) gsz *= g.n;
         for (int k = 1; k < T.K; ++k) {
@@ -1967,7 +2152,13 @@ struct TreeOps : PlanOps {
     int iterations(int count, cudaStream_t st, Timer& tm, long long& nl, bool graphs) override {
         return run_iterations(T, count, st, tm, nl, graphs);
     }
-    int check(cudaStream_t st, Timer& tm, long long& nl) override { return run_check(T, st, tm, nl); }
+    int check(cudaStream_t st, Timer& tm, long long& nl) override {
+        if (T.check_done) {          // the persistent wavefront launch already ran the check pass
+            T.check_done = false;
+            return MOT_OK;
+        }
+        return run_check(T, st, tm, nl);
+    }
     char* stats_dev() override { return T.stats_begin; }
     size_t stats_bytes() const override { return T.stats_bytes; }
     int K() const override { return T.K; }
@@ -2510,6 +2701,12 @@ const char* mot_strerror(int s) {
 const char* mot_last_cuda_error(void) { return g_cuda_err.c_str(); }
 
 int mot_abi_version(void) { return MOT_ABI_VERSION; }
+
+int mot_test_wave_clusters(int nclusters) {
+    if (nclusters < 0 || nclusters > 1024) return MOT_EINVAL;
+    g_wave_clusters_override.store(nclusters);
+    return MOT_OK;
+}
 
 void mot_struct_sizes(size_t out[4]) {
     if (!out) return;

@@ -110,6 +110,7 @@ def lib() -> C.CDLL:
         h.mot_server_poll.argtypes = [C.c_void_p, C.POINTER(ServerResult), C.c_int, C.POINTER(C.c_int)]
         h.mot_server_destroy.argtypes = [C.c_void_p]
         h.mot_test_tc_wait.argtypes = [C.c_longlong, C.c_int]
+        h.mot_test_wave_clusters.argtypes = [C.c_int]
         h.mot_struct_sizes.argtypes = [C.POINTER(C.c_size_t)]
         h.mot_struct_sizes.restype = None
         h.mot_boundary_poly.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double)]
@@ -207,11 +208,17 @@ def mot_fastsum(x_src, x_tgt, alpha, eta: float, opt: Optional[Options] = None, 
 MOT_STATIC_SCRATCH_BYTES = 32 << 20
 
 
-def test_tc_wait(wait_ns: int = 1_000_000_000, stall_loads: bool = False) -> None:
+def hook_tc_wait(wait_ns: int = 1_000_000_000, stall_loads: bool = False) -> None:
     """Test hook of the tensor-core kernel's bounded waits (mot_test_tc_wait): the wait limit in
     ns and a switch that makes the kernel issue no operand loads, so that its first wait runs
-    out.  ``test_tc_wait()`` restores the defaults."""
+    out.  ``hook_tc_wait()`` restores the defaults."""
     _check(lib().mot_test_tc_wait(int(wait_ns), 1 if stall_loads else 0), "mot_test_tc_wait")
+
+
+def hook_wave_clusters(nclusters: int = 0) -> None:
+    """Test hook (mot_test_wave_clusters): clusters of the persistent wavefront kernel for solves
+    set up afterwards; 0 restores the default (as many as are co-resident)."""
+    _check(lib().mot_test_wave_clusters(int(nclusters)), "mot_test_wave_clusters")
 
 
 def mot_fastsum_static(x_src, x_tgt, alpha, eta: float, opt: Optional[Options] = None, stream=None, out=None):
@@ -410,7 +417,8 @@ EXPORTED = ["mot_options_default", "mot_strerror", "mot_last_cuda_error", "mot_a
             "mot_workspace_bytes", "mot_solve", "mot_fastsum_workspace_bytes", "mot_fastsum",
             "mot_fastsum_static", "mot_server_create", "mot_server_submit", "mot_server_progress",
             "mot_server_poll", "mot_server_destroy", "mot_wave_schedule", "mot_boundary_poly",
-            "mot_plan_grid", "mot_struct_sizes", "mot_test_tc_wait"]
+            "mot_plan_grid", "mot_struct_sizes", "mot_test_tc_wait",
+            "mot_test_wave_clusters"]
 
 
 def wave_schedule(parent: Sequence[int], S: int, cap: int):

@@ -74,14 +74,14 @@ def test_tensor_core_wait_runs_out_and_context_survives(M):
     xs, xt = to_dev_points(ps), to_dev_points(pt)
     a = torch.from_numpy(an).cuda()
     opt = M.options(path=M.MOT_PATH_DENSE_BF16X3)
-    M.test_tc_wait(2_000_000, stall_loads=True)
+    M.hook_tc_wait(2_000_000, stall_loads=True)
     try:
         with pytest.raises(M.MotError) as ei:
             M.mot_fastsum(xs, xt, a, 0.02, opt=opt)
         torch.cuda.synchronize()
         assert ei.value.status == M.MOT_ETIMEOUT
     finally:
-        M.test_tc_wait()
+        M.hook_tc_wait()
     b, _ = M.mot_fastsum(xs, xt, a, 0.02, opt=opt)
     torch.cuda.synchronize()
     exact = OK.direct_sum(pt.astype(np.float64), ps.astype(np.float64), an.T.astype(np.float64), 0.02)
@@ -97,7 +97,8 @@ def test_tc_wait_hook_validates_its_limit(M):
 def test_delta_S_stop_matches_oracle_trace(M, topology):
     """Algorithm 2 / 3 stop when |S^(r) - S^(r-1)| < delta (tested after every sweep here).
     delta is put halfway (geometrically) between two consecutive differences of the oracle's trace
-    where they differ by at least a factor 1.5, so that FP32 rounding of S cannot move the stop."""
+    that differ by at least a factor 4 and are at least 1e-6, so that delta is at least 1e-6 away
+    from both: FP32 rounding of the CUDA path's S differences (~1e-7 here) cannot move the stop."""
     import torch
     if topology == W.TREE:
         prob = W.path3_d1()
@@ -107,14 +108,13 @@ def test_delta_S_stop_matches_oracle_trace(M, topology):
         res = OS.CircleSinkhorn(prob.x64(), prob.mu, prob.eta).run(200)
     dS = np.abs(np.diff(res.S))                     # dS[r-2] = |S^(r) - S^(r-1)| after r sweeps
     stop = None
-    for i in range(4, len(dS) - 1):
-        if dS[i] < 1e-3 and dS[i] > 1e-6 and dS[i - 1] > 1.5 * dS[i] and np.all(dS[:i] > 1.5 * dS[i]):
+    for i in range(1, len(dS) - 1):
+        if dS[i] >= 1e-6 and np.all(dS[:i] >= 4.0 * dS[i]):
             stop = i
             break
     assert stop is not None
     delta = float(np.sqrt(dS[stop] * dS[stop - 1]))
     expected = stop + 2                              # sweeps run when the oracle stops
-    assert OS.TreeSinkhorn if topology == W.TREE else True
     x, mu = problem_tensors(prob)
     opt = M.options(delta_S=delta, tol_viol=-1.0, check_every=1, max_iter=500)
     if topology == W.TREE:
