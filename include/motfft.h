@@ -30,7 +30,7 @@
 extern "C" {
 #endif
 
-#define MOT_ABI_VERSION 3
+#define MOT_ABI_VERSION 4
 
 /* ---- status codes ---------------------------------------------------------------- */
 #define MOT_OK           0
@@ -52,6 +52,10 @@ extern "C" {
 #define MOT_PATH_NFFT         0  /* fast summation, Algorithm 4 (window spread, FFT, D, iFFT, gather), FP32 */
 #define MOT_PATH_DENSE        1  /* direct summation, Eq. (fastsum-sum), FP32 SIMT                          */
 #define MOT_PATH_DENSE_BF16X3 2  /* direct summation on tensor cores, split hi+lo BF16, FP32 accumulate     */
+#define MOT_PATH_LOCAL        3  /* trees, small eta (Section 6.1, closing remark): Algorithm 2 with the
+                                    logarithms of scalings and messages (FP64), every kernel sum truncated
+                                    to the pairs within options.r_cut and evaluated as a log-sum-exp over a
+                                    cell list (FP32 terms against FP64 references)                        */
 
 /* Kernel classes for the optional per-kernel timing of mot_result. */
 #define MOT_K_SPREAD   0    /* window spreading onto the oversampled grid (adjoint NFFT)       */
@@ -120,6 +124,9 @@ typedef struct {
                            take the products in a topological order and start each one as soon as
                            the products it reads have completed; 2 = one launch per step of the
                            host's list schedule; -1 = sweep by sweep [1]                         */
+    double r_cut;       /* MOT_PATH_LOCAL: pairs farther apart than r_cut leave every kernel sum
+                           [0 = sqrt(40 eta / w_e) per edge, where the kernel is below e^-40].  Every
+                           target needs a source point within r_cut (MOT_ENUMERIC otherwise)     */
 } mot_options;
 
 /* Fill *o with the defaults. */

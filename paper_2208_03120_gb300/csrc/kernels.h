@@ -145,6 +145,73 @@ cudaError_t launch_pair(const float* phi1, const VecScale* s1, const int* perm1,
                         const VecScale* sk, const int* permk, int nk, const float* G, const VecScale* sG,
                         const float* B, const VecScale* sB, double* out, cudaStream_t st);
 
+// ---- small-eta local path: truncated kernel sums in the log domain (local.cu) -------------------
+struct LGrid {                   // common grid of cells (side h >= r_cut) over all point sets
+    int d;
+    int dims[3];
+    float lo[3];                 // box corner
+    float h, inv_h;
+    int ncells;
+};
+struct LBinSet {                 // one point set to bin
+    int n;
+    const float* x;              // caller points [n][d]
+    const double* mu;            // caller weights [n]
+    int* cell;                   // [n] scratch
+    int* cstart;                 // [ncells + 1] out: first sorted point of each cell (zeroed by the caller)
+    int* cursor;                 // [ncells] scratch
+    float* u;                    // [d][n] out: sorted coordinates
+    int* perm;                   // [n] out: sorted position -> caller index
+    double* mu_s;                // [n] out: sorted mu
+    double* logmu;               // [n] out: sorted log mu (-inf where mu = 0)
+};
+struct LSet {                    // a binned point set
+    int n;
+    const float* u;
+    const int* cstart;
+    const double* logmu;
+    const double* mu;
+};
+struct LFac {                    // one term of a sum of log-vectors: +-v
+    const double* v;
+    int sign;
+};
+enum LEpi : int {
+    LEPI_MSG = 0,                // out = log of the kernel sum (a message b_k)
+    LEPI_FWD = 1,                // out = g_k; f^k = log mu^k - g_k - sum_c b_c; sum mu f into the next slot
+    LEPI_CHK = 2,                // out = g-ex_k; exact marginal of node k into acc_node
+    LEPI_ROOT = 3,               // root: mass / violation of the last iterate, then f^1 = log mu^1 - sum_c b_c
+    LEPI_CHKROOT = 4,            // root: exact marginal into acc_node
+};
+struct LTask {
+    LSet src, tgt;
+    int sf0, snf;                // source log-values l_j = sum of the factors
+    int tf0, tnf;                // target-side log-messages (children's b)
+    float* delta;                // [src.n] scratch: l_j - L_c
+    double* Lc;                  // [ncells] scratch: max l over each source cell
+    float inv_eta, r2;           // 1 / eta_e and r_cut^2
+    double inv_eta_d;
+    int mode;                    // LEpi
+    double* out;                 // [tgt.n] log kernel sum
+    double* f;                   // [tgt.n] log phi of the target node
+    double* acc_node;            // check: [3] violation, sum P f, mass
+    int iter_off;
+};
+struct LGlobals {
+    int* iter;
+    IterAcc* acc;
+    int R;
+    int* err;                    // bit 0: non-finite input; bit 1: negative weight; bit 3: a target
+};                               // has no source within r_cut
+cudaError_t launch_lbin(const LBinSet* sets_dev, int nsets, int nmax, const LGrid& g, int* err, cudaStream_t st);
+cudaError_t launch_lsrc(const LTask* tasks, int ntask, const LFac* F, int ncells, int* err, cudaStream_t st);
+cudaError_t launch_lse(const LTask* tasks, int ntask, const LFac* F, const LGrid& g, const LGlobals& G,
+                       cudaStream_t st);
+cudaError_t launch_lroot(const LTask* tasks, int ntask, const LFac* F, int nmax, const LGlobals& G, cudaStream_t st);
+cudaError_t launch_linit(double* f, const int* perm, const double* mu, int n, const double* u, double eta,
+                         double* logphi, cudaStream_t st);
+cudaError_t launch_lout(const double* f, const int* perm, int n, double eta, double* u, cudaStream_t st);
+
 // ---- dense products on the tensor cores, BF16 hi + lo split (tc_gemm.cu) ------------------
 // Y[c][i] = sum_j A[c][j] B[i][j] with A = Ahi + Alo (M x K), B = Bhi + Blo (N x K), BF16,
 // row strides lda / ldb (multiples of 8 elements); FP32 accumulation of Ahi Bhi + Ahi Blo + Alo Bhi.

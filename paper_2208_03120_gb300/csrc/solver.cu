@@ -2239,7 +2239,450 @@ struct CircleOps : PlanOps {
 };
 
 // Build the plan of a problem inside `ws` (sizes: mot_workspace_bytes) and enqueue its set-up.
+// =============================================================================================
+// small-eta local path (Section 6.1, closing remark): Algorithm 2 in the log domain with every
+// kernel sum truncated to the pairs within r_cut (local.cu)
+// =============================================================================================
+constexpr int kLocalMaxCells = 1 << 16;      // cells of the common grid (h grows until they fit)
+
+struct LocalPlan {
+    TreePlan S;                              // tree structure only (BFS labels, parents, depths)
+    int K = 0, d = 0;
+    double eta = 0.0, h = 0.0;
+    std::vector<double> r_e;                 // cutoff of edge {p(k), k}
+    LGrid grid{};
+    int nmax = 0;
+    // per node (BFS labels)
+    std::vector<LBinSet> bins;
+    std::vector<double*> f;
+    // per edge k >= 1
+    std::vector<double*> b, g, gx, Lc_f, Lc_b, Lc_c;
+    std::vector<float*> dl_f, dl_b, dl_c;
+    // tasks: forward (one launch), root, backward levels, check levels, check root
+    std::vector<LTask> fwd, root, chkroot;
+    std::vector<std::vector<LTask>> bwd, chk;
+    LTask* d_fwd = nullptr;
+    LTask* d_root = nullptr;
+    LTask* d_chkroot = nullptr;
+    std::vector<LTask*> d_bwd, d_chk;
+    LTask* d_tasks = nullptr;
+    size_t task_cap = 0;
+    std::vector<LFac> fac;
+    LFac* d_fac = nullptr;
+    size_t fac_cap = 0;
+    LBinSet* d_bins = nullptr;
+    float* box_scratch = nullptr;
+    float* box_out = nullptr;
+    PrepSet* d_sets = nullptr;
+    // stats region: the accumulator ring, per-node check accumulators, error word and counter
+    char* stats_begin = nullptr;
+    size_t stats_bytes = 0;
+    IterAcc* acc = nullptr;
+    double* acc_node = nullptr;
+    int* err = nullptr;
+    int* iter = nullptr;
+    LGlobals LG{};
+    Globals G{};
+    cudaGraphExec_t gexec = nullptr;
+    int graph_iters = 0;
+    long long launches_per_iter = 0;
+};
+
+void layout_local(Arena& A, LocalPlan& L) {
+    const int K = L.K, d = L.d;
+    const int nc = kLocalMaxCells;
+    L.bins.assign(K, LBinSet());
+    L.f.assign(K, nullptr);
+    for (int k = 0; k < K; ++k) {
+        const int n = L.S.n[k];
+        LBinSet& B = L.bins[k];
+        B.n = n;
+        B.cell = A.take<int>(n);
+        B.cstart = A.take<int>(nc + 1);
+        B.cursor = A.take<int>(nc);
+        B.u = A.take<float>((size_t)d * n);
+        B.perm = A.take<int>(n);
+        B.mu_s = A.take<double>(n);
+        B.logmu = A.take<double>(n);
+        L.f[k] = A.take<double>(n);
+    }
+    for (auto* v : {&L.b, &L.g, &L.gx, &L.Lc_f, &L.Lc_b, &L.Lc_c}) v->assign(K, nullptr);
+    for (auto* v : {&L.dl_f, &L.dl_b, &L.dl_c}) v->assign(K, nullptr);
+    for (int k = 1; k < K; ++k) {
+        const int p = L.S.parent[k], nk = L.S.n[k], np = L.S.n[p];
+        L.b[k] = A.take<double>(np);
+        L.g[k] = A.take<double>(nk);
+        L.gx[k] = A.take<double>(nk);
+        L.dl_f[k] = A.take<float>(np);
+        L.dl_b[k] = A.take<float>(nk);
+        L.dl_c[k] = A.take<float>(np);
+        L.Lc_f[k] = A.take<double>(nc);
+        L.Lc_b[k] = A.take<double>(nc);
+        L.Lc_c[k] = A.take<double>(nc);
+    }
+    L.stats_bytes = sizeof(IterAcc) * kRing + sizeof(double) * 3 * K + 16;
+    L.stats_begin = A.take<char>(L.stats_bytes);
+    if (!A.measure) {
+        L.acc = reinterpret_cast<IterAcc*>(L.stats_begin);
+        L.acc_node = reinterpret_cast<double*>(L.stats_begin + sizeof(IterAcc) * kRing);
+        L.err = reinterpret_cast<int*>(L.stats_begin + L.stats_bytes - 16);
+        L.iter = L.err + 1;
+    }
+    L.task_cap = 3 * (size_t)K + 4;
+    L.d_tasks = A.take<LTask>(L.task_cap);
+    L.fac_cap = 6 * (size_t)K + 8;
+    for (int k = 0; k < K; ++k) L.fac_cap += 2 * L.S.children[k].size();
+    L.d_fac = A.take<LFac>(L.fac_cap);
+    L.d_bins = A.take<LBinSet>(K);
+    L.d_sets = A.take<PrepSet>(K);
+    L.box_scratch = A.take<float>(8);
+    L.box_out = A.take<float>(8);
+}
+
+LSet lset_of(const LocalPlan& L, int k) {
+    LSet s;
+    s.n = L.S.n[k];
+    s.u = L.bins[k].u;
+    s.cstart = L.bins[k].cstart;
+    s.logmu = L.bins[k].logmu;
+    s.mu = L.bins[k].mu_s;
+    return s;
+}
+
+LTask ltask_blank() {
+    LTask t;
+    std::memset(&t, 0, sizeof(t));
+    return t;
+}
+
+void ltask_kernel(LocalPlan& L, LTask& t, int k) {
+    const double eta_e = L.eta / L.S.w[k];
+    t.inv_eta = (float)(1.0 / eta_e);
+    t.inv_eta_d = 1.0 / eta_e;
+    t.r2 = (float)(L.r_e[k] * L.r_e[k]);
+}
+
+void lfac(LocalPlan& L, const double* v, int sign) {
+    LFac f;
+    f.v = v;
+    f.sign = sign;
+    L.fac.push_back(f);
+}
+
+void local_build(LocalPlan& L) {
+    const int K = L.K;
+    const TreePlan& S = L.S;
+    L.fac.clear();
+    L.fwd.clear();
+    for (int k = 1; k < K; ++k) {          // gamma_k = K^T (mu^p / beta_k), then f^k (Algorithm 2, forward)
+        const int p = S.parent[k];
+        LTask t = ltask_blank();
+        t.src = lset_of(L, p);
+        t.sf0 = (int)L.fac.size();
+        lfac(L, L.bins[p].logmu, +1);
+        lfac(L, L.b[k], -1);
+        t.snf = 2;
+        t.tgt = lset_of(L, k);
+        t.tf0 = (int)L.fac.size();
+        for (int c : S.children[k]) lfac(L, L.b[c], +1);
+        t.tnf = (int)L.fac.size() - t.tf0;
+        t.delta = L.dl_f[k];
+        t.Lc = L.Lc_f[k];
+        ltask_kernel(L, t, k);
+        t.mode = LEPI_FWD;
+        t.out = L.g[k];
+        t.f = L.f[k];
+        L.fwd.push_back(t);
+    }
+    auto root_task = [&](int mode) {
+        LTask t = ltask_blank();
+        t.tgt = lset_of(L, 0);
+        t.tf0 = (int)L.fac.size();
+        for (int c : S.children[0]) lfac(L, L.b[c], +1);
+        t.tnf = (int)L.fac.size() - t.tf0;
+        t.mode = mode;
+        t.f = L.f[0];
+        t.acc_node = L.acc_node;
+        return t;
+    };
+    L.root.assign(1, root_task(LEPI_ROOT));
+    int maxdepth = 0;
+    for (int k = 0; k < K; ++k) maxdepth = std::max(maxdepth, S.depth[k]);
+    L.bwd.assign(std::max(maxdepth, 1), {});
+    for (int k = K - 1; k >= 1; --k) {     // beta_k = K (phi^k (.) beta^{C_k}), deepest level first
+        LTask t = ltask_blank();
+        t.src = lset_of(L, k);
+        t.sf0 = (int)L.fac.size();
+        lfac(L, L.f[k], +1);
+        for (int c : S.children[k]) lfac(L, L.b[c], +1);
+        t.snf = (int)L.fac.size() - t.sf0;
+        t.tgt = lset_of(L, S.parent[k]);
+        t.delta = L.dl_b[k];
+        t.Lc = L.Lc_b[k];
+        ltask_kernel(L, t, k);
+        t.mode = LEPI_MSG;
+        t.out = L.b[k];
+        L.bwd[maxdepth - S.depth[k]].push_back(t);
+    }
+    L.chk.assign(std::max(maxdepth, 1), {});
+    for (int k = 1; k < K; ++k) {          // check pass: gamma-ex_k from the root down (Theorem 4.1)
+        const int p = S.parent[k];
+        LTask t = ltask_blank();
+        t.src = lset_of(L, p);
+        t.sf0 = (int)L.fac.size();
+        lfac(L, L.f[p], +1);
+        if (p != 0) lfac(L, L.gx[p], +1);
+        for (int c : S.children[p])
+            if (c != k) lfac(L, L.b[c], +1);
+        t.snf = (int)L.fac.size() - t.sf0;
+        t.tgt = lset_of(L, k);
+        t.tf0 = (int)L.fac.size();
+        for (int c : S.children[k]) lfac(L, L.b[c], +1);
+        t.tnf = (int)L.fac.size() - t.tf0;
+        t.delta = L.dl_c[k];
+        t.Lc = L.Lc_c[k];
+        ltask_kernel(L, t, k);
+        t.mode = LEPI_CHK;
+        t.out = L.gx[k];
+        t.f = L.f[k];
+        t.acc_node = L.acc_node + 3 * k;
+        L.chk[S.depth[k] - 1].push_back(t);
+    }
+    L.chkroot.assign(1, root_task(LEPI_CHKROOT));
+}
+
+int local_upload(LocalPlan& L, cudaStream_t st) {
+    if (L.fac.size() > L.fac_cap) return MOT_EUNSUPPORTED;
+    std::vector<LTask> all;
+    auto place = [&](std::vector<LTask>& v) {
+        LTask* p = L.d_tasks + all.size();
+        for (auto& t : v) all.push_back(t);
+        return p;
+    };
+    L.d_fwd = place(L.fwd);
+    L.d_root = place(L.root);
+    L.d_chkroot = place(L.chkroot);
+    L.d_bwd.clear();
+    for (auto& v : L.bwd) L.d_bwd.push_back(place(v));
+    L.d_chk.clear();
+    for (auto& v : L.chk) L.d_chk.push_back(place(v));
+    if (all.size() > L.task_cap) return MOT_EUNSUPPORTED;
+    CK(cudaMemcpyAsync(L.d_fac, L.fac.data(), sizeof(LFac) * L.fac.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(L.d_tasks, all.data(), sizeof(LTask) * all.size(), cudaMemcpyHostToDevice, st));
+    return MOT_OK;
+}
+
+int local_setup(const mot_problem* P, const mot_options& o, LocalPlan& L, void* ws, size_t ws_bytes, bool measure,
+                size_t* need, cudaStream_t st) {
+    RET(tree_structure(P, L.S));
+    if (P->free_nodes)
+        for (int k = 0; k < P->K; ++k)
+            if (P->free_nodes[k]) return MOT_EUNSUPPORTED;
+    if (o.r_cut < 0.0 || !std::isfinite(o.r_cut)) return MOT_EINVAL;
+    L.K = P->K;
+    L.d = P->d;
+    L.eta = P->eta;
+    L.r_e.assign(L.K, 0.0);
+    L.h = 0.0;
+    for (int k = 1; k < L.K; ++k) {
+        // the kernel of edge k is below e^-40 beyond sqrt(40 eta_e) unless the caller sets r_cut
+        L.r_e[k] = o.r_cut > 0.0 ? o.r_cut : std::sqrt(40.0 * P->eta / L.S.w[k]);
+        L.h = std::max(L.h, L.r_e[k]);
+    }
+    Arena A;
+    A.measure = measure;
+    A.base = reinterpret_cast<char*>(ws);
+    A.cap = ws_bytes;
+    layout_local(A, L);
+    if (measure) {
+        *need = A.off + 256;
+        return MOT_OK;
+    }
+    if (A.off > ws_bytes) return MOT_ENOMEM;
+    // bounding box of all points (one readback), then the cell grid
+    std::vector<PrepSet> sets;
+    for (int k = 0; k < L.K; ++k) {
+        PrepSet ps;
+        std::memset(&ps, 0, sizeof(ps));
+        ps.x = P->x[L.S.order[k]];
+        ps.n = L.S.n[k];
+        sets.push_back(ps);
+    }
+    CK(cudaMemcpyAsync(L.d_sets, sets.data(), sizeof(PrepSet) * sets.size(), cudaMemcpyHostToDevice, st));
+    CK(launch_bounds(L.d_sets, L.K, L.d, L.box_scratch, L.box_out, st));
+    float hb[7] = {0, 0, 0, 0, 0, 0, 0};
+    CK(cudaMemcpyAsync(hb, L.box_out, sizeof(float) * (2 * L.d + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double h = L.h;
+    for (int t = 0; t < L.d; ++t)
+        if (!std::isfinite(hb[2 * t]) || !std::isfinite(hb[2 * t + 1])) return MOT_ENUMERIC;
+    for (;;) {
+        long long cells = 1;
+        for (int t = 0; t < L.d; ++t) cells *= std::max(1LL, (long long)std::ceil(((double)hb[2 * t + 1] - hb[2 * t]) / h + 1e-9));
+        if (cells <= kLocalMaxCells) break;
+        h *= 1.25;                            // larger cells: still every pair within r_cut is in the 3^d block
+    }
+    L.grid.d = L.d;
+    L.grid.ncells = 1;
+    for (int t = 0; t < 3; ++t) {
+        L.grid.dims[t] = 1;
+        L.grid.lo[t] = 0.f;
+    }
+    for (int t = 0; t < L.d; ++t) {
+        L.grid.lo[t] = hb[2 * t];
+        L.grid.dims[t] = std::max(1, (int)std::ceil(((double)hb[2 * t + 1] - hb[2 * t]) / h + 1e-9));
+        L.grid.ncells *= L.grid.dims[t];
+    }
+    L.grid.h = (float)h;
+    L.grid.inv_h = (float)(1.0 / h);
+    // binning
+    CK(cudaMemsetAsync(L.stats_begin, 0, L.stats_bytes, st));
+    L.nmax = 0;
+    for (int k = 0; k < L.K; ++k) {
+        L.bins[k].x = P->x[L.S.order[k]];
+        L.bins[k].mu = P->mu[L.S.order[k]];
+        L.nmax = std::max(L.nmax, L.S.n[k]);
+        CK(cudaMemsetAsync(L.bins[k].cstart, 0, sizeof(int) * (L.grid.ncells + 1), st));
+    }
+    CK(cudaMemcpyAsync(L.d_bins, L.bins.data(), sizeof(LBinSet) * L.K, cudaMemcpyHostToDevice, st));
+    CK(launch_lbin(L.d_bins, L.K, L.nmax, L.grid, L.err, st));
+    L.LG.iter = L.iter;
+    L.LG.acc = L.acc;
+    L.LG.R = kRing;
+    L.LG.err = L.err;
+    std::memset(&L.G, 0, sizeof(L.G));
+    L.G.iter = L.iter;
+    L.G.acc = L.acc;
+    L.G.R = kRing;
+    local_build(L);
+    RET(local_upload(L, st));
+    return MOT_OK;
+}
+
+int local_backward(LocalPlan& L, cudaStream_t st, long long& nl) {
+    for (size_t l = 0; l < L.bwd.size(); ++l) {
+        CK(launch_lsrc(L.d_bwd[l], (int)L.bwd[l].size(), L.d_fac, L.grid.ncells, L.err, st));
+        CK(launch_lse(L.d_bwd[l], (int)L.bwd[l].size(), L.d_fac, L.grid, L.LG, st));
+        nl += 2;
+    }
+    return MOT_OK;
+}
+
+int local_iteration(LocalPlan& L, cudaStream_t st, Timer& tm, long long& nl) {
+    cudaEvent_t e = nullptr;
+    RET(tm.begin(MOT_K_NODE, &e));
+    CK(launch_prologue(nullptr, 0, 0, 1, nullptr, 0, L.G, st));
+    RET(tm.end(e));
+    RET(tm.begin(MOT_K_DENSE, &e));
+    CK(launch_lsrc(L.d_fwd, (int)L.fwd.size(), L.d_fac, L.grid.ncells, L.err, st));
+    CK(launch_lse(L.d_fwd, (int)L.fwd.size(), L.d_fac, L.grid, L.LG, st));
+    CK(launch_lroot(L.d_root, 1, L.d_fac, L.nmax, L.LG, st));
+    nl += 4;
+    RET(local_backward(L, st, nl));
+    RET(tm.end(e));
+    return MOT_OK;
+}
+
+int local_check(LocalPlan& L, cudaStream_t st, Timer& tm, long long& nl) {
+    cudaEvent_t e = nullptr;
+    RET(tm.begin(MOT_K_NODE, &e));
+    CK(launch_prologue(nullptr, 0, 0, 0, L.acc_node, 3 * L.K, L.G, st));
+    CK(launch_lroot(L.d_chkroot, 1, L.d_fac, L.nmax, L.LG, st));
+    RET(tm.end(e));
+    nl += 2;
+    RET(tm.begin(MOT_K_DENSE, &e));
+    for (size_t l = 0; l < L.chk.size(); ++l) {
+        CK(launch_lsrc(L.d_chk[l], (int)L.chk[l].size(), L.d_fac, L.grid.ncells, L.err, st));
+        CK(launch_lse(L.d_chk[l], (int)L.chk[l].size(), L.d_fac, L.grid, L.LG, st));
+        nl += 2;
+    }
+    RET(tm.end(e));
+    return MOT_OK;
+}
+
+int local_iterations(LocalPlan& L, int count, cudaStream_t st, Timer& tm, long long& nl, bool graphs) {
+    if (count <= 0) return MOT_OK;
+    if (graphs && !tm.on && st != nullptr) {
+        if (L.gexec == nullptr || L.graph_iters != count) {
+            if (L.gexec) {
+                cudaGraphExecDestroy(L.gexec);
+                L.gexec = nullptr;
+            }
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            long long dn = 0;
+            int rc = MOT_OK;
+            for (int i = 0; i < count && rc == MOT_OK; ++i) rc = local_iteration(L, st, tm, dn);
+            cudaError_t ce = cudaStreamEndCapture(st, &graph);
+            if (rc != MOT_OK) return rc;
+            CK(ce);
+            CK(cudaGraphInstantiate(&L.gexec, graph, 0));
+            cudaGraphDestroy(graph);
+            L.graph_iters = count;
+            L.launches_per_iter = dn / count;
+        }
+        CK(cudaGraphLaunch(L.gexec, st));
+        nl += L.launches_per_iter * count;
+        return MOT_OK;
+    }
+    for (int i = 0; i < count; ++i) RET(local_iteration(L, st, tm, nl));
+    return MOT_OK;
+}
+
+struct LocalOps : PlanOps {
+    LocalPlan L;
+    int init(const double* const* u_warm, cudaStream_t st, Timer& tm, long long& nl) override {
+        (void)tm;
+        int minus1 = -1;
+        CK(cudaMemcpyAsync(L.iter, &minus1, sizeof(int), cudaMemcpyHostToDevice, st));
+        for (int k = 0; k < L.K; ++k) {
+            const double* uw = u_warm ? u_warm[L.S.order[k]] : nullptr;
+            CK(launch_linit(L.f[k], L.bins[k].perm, L.bins[k].mu_s, L.S.n[k], uw, L.eta, &L.acc[0].logphi, st));
+            nl += 1;
+        }
+        return local_backward(L, st, nl);    // Algorithm 2, steps 3-5
+    }
+    int iterations(int count, cudaStream_t st, Timer& tm, long long& nl, bool graphs) override {
+        return local_iterations(L, count, st, tm, nl, graphs);
+    }
+    int check(cudaStream_t st, Timer& tm, long long& nl) override { return local_check(L, st, tm, nl); }
+    char* stats_dev() override { return L.stats_begin; }
+    size_t stats_bytes() const override { return L.stats_bytes; }
+    int K() const override { return L.K; }
+    int n_scales() const override { return 0; }
+    bool constrained(int) const override { return true; }
+    double eta() const override { return L.eta; }
+    int output(double* const* u, double* const*, cudaStream_t st, long long& nl) override {
+        for (int k = 0; k < L.K && u; ++k) {
+            if (!u[L.S.order[k]]) continue;
+            CK(launch_lout(L.f[k], L.bins[k].perm, L.S.n[k], L.eta, u[L.S.order[k]], st));
+            nl += 1;
+        }
+        return MOT_OK;
+    }
+    void geometry(mot_result* r) const override {
+        r->scale = 1.0;
+        r->eta_norm = L.eta;
+        r->n_grid = 0;
+        r->M = 0;
+    }
+    ~LocalOps() override {
+        if (L.gexec) cudaGraphExecDestroy(L.gexec);
+    }
+};
+
 int make_ops(const mot_problem* P, const mot_options& o, void* ws, size_t ws_bytes, cudaStream_t st, PlanOps** out) {
+    if (o.path == MOT_PATH_LOCAL) {
+        if (P->topology != MOT_TREE) return MOT_EUNSUPPORTED;
+        LocalOps* l = new LocalOps();
+        int rc = local_setup(P, o, l->L, ws, ws_bytes, false, nullptr, st);
+        if (rc != MOT_OK) {
+            delete l;
+            return rc;
+        }
+        *out = l;
+        return MOT_OK;
+    }
     if (P->topology == MOT_TREE) {
         TreeOps* t = new TreeOps();
         int rc = tree_plan_setup(P, o, t->T, ws, ws_bytes, false, nullptr, st);
@@ -2747,6 +3190,11 @@ int mot_workspace_bytes(const mot_problem* prob, const mot_options* opt, size_t*
     fill_defaults(o, opt);
     if (o.n_grid && (o.n_grid < 16 || o.n_grid > max_grid(prob->d) || (o.n_grid & (o.n_grid - 1)))) return MOT_EINVAL;
     if (o.m != 4) return MOT_EUNSUPPORTED;
+    if (o.path == MOT_PATH_LOCAL) {
+        if (prob->topology != MOT_TREE) return MOT_EUNSUPPORTED;
+        LocalPlan L;
+        return local_setup(prob, o, L, nullptr, 0, true, bytes, nullptr);
+    }
     if (prob->topology == MOT_CIRCLE) {
         CirclePlan C;
         return circle_setup(prob, o, C, nullptr, 0, true, bytes, nullptr);

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmotfft.s
 
 MOT_OK, MOT_EINVAL, MOT_ENOTTREE, MOT_ENOMEM, MOT_ENUMERIC, MOT_ENOCONV, MOT_ETIMEOUT, MOT_ECUDA, MOT_EUNSUPPORTED = range(9)
 MOT_TREE, MOT_CIRCLE = 0, 1
-MOT_PATH_NFFT, MOT_PATH_DENSE, MOT_PATH_DENSE_BF16X3 = 0, 1, 2
+MOT_PATH_NFFT, MOT_PATH_DENSE, MOT_PATH_DENSE_BF16X3, MOT_PATH_LOCAL = 0, 1, 2, 3
 MOT_NKCLASS = 10
 KERNEL_CLASSES = ["spread", "fftconv", "gather", "dense", "node", "setup", "circle", "fused", "tcgemm", "split"]
 
@@ -59,6 +59,7 @@ class Options(C.Structure):
         ("n_grid", C.c_int), ("m", C.c_int), ("p", C.c_int),
         ("eps_B", C.c_double),
         ("use_graphs", C.c_int), ("timing", C.c_int), ("wavefront", C.c_int),
+        ("r_cut", C.c_double),
     ]
 
 

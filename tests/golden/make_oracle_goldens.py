@@ -19,7 +19,12 @@ Each is run in chunks of sweeps from phi = 1 until the exact violation is at mos
 ``TOL`` (or the sweep cap), far below the 1e-6 the CUDA path stops at, so that the
 golden stands for the fixed point.
 
-Usage: python tests/golden/make_oracle_goldens.py [path10_d2|star9_d3_n5000|circle5_d1 ...]
+  * local_path5_d2 -- Algorithm 2 in the log domain with every kernel sum truncated to
+                      |x - y| <= sqrt(40 eta) (Section 6.1, closing remark): path of 5, d=2,
+                      N=400, eta=2e-3 (a regime the FP32 scaling form cannot span); the
+                      potentials are stored as log phi^k.
+
+Usage: python tests/golden/make_oracle_goldens.py [path10_d2|star9_d3_n5000|circle5_d1|local_path5_d2 ...]
 """
 from __future__ import annotations
 
@@ -93,6 +98,9 @@ def solve(prob, chunk: int, cap: int):
 
 def write(name: str, prob, chunk: int, cap: int, extra: dict) -> None:
     print(f"{name}: K={prob.K} d={prob.d} n={prob.n[0]} eta={prob.eta}", flush=True)
+    # keep every edge's kernel matrix in memory (10^8 FP64 entries per edge at N = 10^4): the same
+    # products, formed once instead of block by block at every sweep
+    OS.EdgeKernel.DENSE_LIMIT = max(OS.EdgeKernel.DENSE_LIMIT, max(prob.n) ** 2)
     phi, sweeps, S, rep = solve(prob, chunk, cap)
     u = OS.gauge_fix([prob.eta * np.log(p) for p in phi], prob.mu)
     idx = [sample_indices(len(v), k) for k, v in enumerate(u)]
@@ -105,7 +113,42 @@ def write(name: str, prob, chunk: int, cap: int, extra: dict) -> None:
         f.write("\n")
 
 
+def local_problem():
+    return W.random_problem(np.random.default_rng(5), W.TREE, 5, 2, 400, 2e-3, shape="path")
+
+
+def write_local(name: str) -> None:
+    import math
+    prob = local_problem()
+    r_cut = math.sqrt(40.0 * prob.eta)
+    print(f"{name}: K={prob.K} d={prob.d} n={prob.n[0]} eta={prob.eta} r_cut={r_cut}", flush=True)
+    ts = OS.TreeSinkhornLog(prob.x64(), prob.mu, prob.edges, prob.eta, r_cut=r_cut)
+    f, sweeps, S = None, 0, []
+    t0 = time.time()
+    while True:
+        res = ts.run(50, logphi0=f)
+        f, sweeps = res.logphi, sweeps + res.iters
+        S += res.S
+        lp = OS.tree_marginals_log(prob.x64(), f, prob.edges, prob.eta, r_cut=r_cut)
+        P = [np.exp(a) for a in lp]
+        viol = OS.violation(P, prob.mu)
+        mass = float(P[0].sum())
+        dual = prob.eta * (sum(float(np.sum(np.where(m > 0, m * fk, 0.0))) for m, fk in zip(prob.mu, f)) - mass)
+        print(f"  {name}: {sweeps} sweeps, violation {viol:.3e}, S {dual:.12e} ({time.time() - t0:.0f} s)", flush=True)
+        if viol <= 1e-8 or sweeps >= 2000:
+            break
+    g = OS.gauge_fix(f, prob.mu)
+    doc = dict(workload=name, K=prob.K, d=prob.d, n=prob.n, eta=prob.eta, r_cut=r_cut, inputs_crc=inputs_crc(prob),
+               oracle_sweeps=sweeps, violation=viol, dual=dual, mass=mass, S_trace_tail=S[-5:],
+               note="TreeSinkhornLog with r_cut rooted at node 0; logphi gauge-fixed (all points stored)",
+               logphi=[v.tolist() for v in g])
+    with open(os.path.join(HERE, f"oracle_{name}.json"), "w") as fh:
+        json.dump(doc, fh, indent=0)
+        fh.write("\n")
+
+
 JOBS = {
+    "local_path5_d2": lambda: write_local("local_path5_d2"),
     "path10_d2": lambda: write("path10_d2", W.path10_d2(), 20, 400,
                                dict(note="Algorithm 2 rooted at node 0; the fixed point does not depend on the root")),
     "star9_d3_n5000": lambda: write("star9_d3_n5000", W.star9_d3(n=5000), 20, 600,

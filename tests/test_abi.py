@@ -35,7 +35,7 @@ def test_header_declarations_exported(M):
 
 def test_abi_version_and_strerror(M):
     lib = M.lib()
-    assert lib.mot_abi_version() == 3
+    assert lib.mot_abi_version() == 4
     assert M.strerror(0) == "ok"
     assert "tree" in M.strerror(M.MOT_ENOTTREE)
     assert M.strerror(12345) == "unknown status"
