@@ -68,7 +68,9 @@ extern "C" {
 #define MOT_K_FUSED    7    /* fused 2-D fast summation (spread, DFTs, gather in one cluster)  */
 #define MOT_K_TCGEMM   8    /* split-BF16 kernel product on the tensor cores (tcgen05)         */
 #define MOT_K_SPLIT    9    /* scaled source matrix split into BF16 hi / lo                    */
-#define MOT_NKCLASS    10
+#define MOT_K_WAVE     10   /* persistent wavefront kernel: a chunk of tree sweeps + check pass */
+#define MOT_K_LOCAL    11   /* truncated log-sum-exp kernel sums of the small-eta local path     */
+#define MOT_NKCLASS    12
 
 /* ---- problem --------------------------------------------------------------------- */
 /* Section 2 / Section 4: K marginals mu^k on points x^k in R^d, a tree or a circle, eta. */

@@ -196,6 +196,7 @@ struct LTask {
     double* f;                   // [tgt.n] log phi of the target node
     double* acc_node;            // check: [3] violation, sum P f, mass
     int iter_off;
+    int tchunks;                 // chunks of LSE_TARGETS targets in the fullest target cell
 };
 struct LGlobals {
     int* iter;
@@ -203,9 +204,12 @@ struct LGlobals {
     int R;
     int* err;                    // bit 0: non-finite input; bit 1: negative weight; bit 3: a target
 };                               // has no source within r_cut
-cudaError_t launch_lbin(const LBinSet* sets_dev, int nsets, int nmax, const LGrid& g, int* err, cudaStream_t st);
+cudaError_t launch_lbin(const LBinSet* sets_dev, int nsets, int nmax, const LGrid& g, int* err, int* maxcount,
+                        cudaStream_t st);
+constexpr int LSE_TARGETS = 256;   // targets per CTA of the log-sum-exp kernel
 cudaError_t launch_lsrc(const LTask* tasks, int ntask, const LFac* F, int ncells, int* err, cudaStream_t st);
-cudaError_t launch_lse(const LTask* tasks, int ntask, const LFac* F, const LGrid& g, const LGlobals& G,
+// grid (cells, tasks, tchunks): tchunks = the largest LTask.tchunks of the launch
+cudaError_t launch_lse(const LTask* tasks, int ntask, int tchunks, const LFac* F, const LGrid& g, const LGlobals& G,
                        cudaStream_t st);
 cudaError_t launch_lroot(const LTask* tasks, int ntask, const LFac* F, int nmax, const LGlobals& G, cudaStream_t st);
 cudaError_t launch_linit(double* f, const int* perm, const double* mu, int n, const double* u, double eta,

@@ -60,14 +60,18 @@ __global__ void k_lbin_count(const LBinSet* __restrict__ sets, LGrid g, int* err
     }
 }
 
-__global__ void __launch_bounds__(1024) k_lbin_scan(const LBinSet* __restrict__ sets, int ncells) {
+__global__ void __launch_bounds__(1024) k_lbin_scan(const LBinSet* __restrict__ sets, int ncells, int* maxcount) {
     const LBinSet S = sets[blockIdx.x];
     __shared__ int part[1024];
     const int t = threadIdx.x, nt = blockDim.x;
     const int chunk = (ncells + nt - 1) / nt;
     const int c0 = min(ncells, t * chunk), c1 = min(ncells, c0 + chunk);
-    int local = 0;
-    for (int c = c0; c < c1; ++c) local += S.cstart[c];
+    int local = 0, mx = 0;
+    for (int c = c0; c < c1; ++c) {
+        local += S.cstart[c];
+        mx = max(mx, S.cstart[c]);
+    }
+    atomicMax(maxcount + blockIdx.x, mx);
     part[t] = local;
     __syncthreads();
     for (int off = 1; off < nt; off <<= 1) {
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(256) k_lsrc(const LTask* __restrict__ tasks, c
 }
 
 // ---- the truncated log-sum-exp and its epilogue ---------------------------------------------
-constexpr int LSE_THREADS = 256;
+constexpr int LSE_THREADS = LSE_TARGETS;
 constexpr int LSE_CAP = 1024;           // staged source points per round (coordinates + delta)
 constexpr int LSE_MAXNB = 27;           // neighbour cells (3^d)
 
@@ -180,11 +184,21 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
     __syncthreads();
 }
 
+// The fast pass sums 2^e2 (exponents in log2 units, e2 <= 0 against the reference, so no term
+// overflows).  Its result is kept when the sum is at least 2^-LSE_MIN2: every term that underflowed
+// is then below 2^-(126 - LSE_MIN2) of the sum.  No constant is added inside exp2 (that would
+// round the argument at the constant's magnitude).
+constexpr float LSE_MIN2 = 100.f;
+constexpr float LOG2E = 1.4426950408889634f;
+
+template <int D>
 __global__ void __launch_bounds__(LSE_THREADS) k_lse(const LTask* __restrict__ tasks, const LFac* __restrict__ F,
                                                      LGrid g, LGlobals G) {
     const LTask& T = tasks[blockIdx.y];
     const int cT = blockIdx.x;
-    const int i0 = T.tgt.cstart[cT], i1 = T.tgt.cstart[cT + 1];
+    // this CTA's chunk of the target cell's points (blockIdx.z)
+    const int i0 = T.tgt.cstart[cT] + (int)blockIdx.z * LSE_THREADS;
+    const int i1 = min(T.tgt.cstart[cT + 1], i0 + LSE_THREADS);
     if (i0 >= i1) return;                       // uniform over the block
     __shared__ float sx[3][LSE_CAP];
     __shared__ float sdel[LSE_CAP];
@@ -254,37 +268,76 @@ __global__ void __launch_bounds__(LSE_THREADS) k_lse(const LTask* __restrict__ t
                 ref = fmax(ref, s_L[q] - box_d2(xi, qc, g) * ied);
             }
         }
-        float m = -INFINITY, s = 0.f;
+        // one pass with a fixed offset (branch-free: one exp2 per pair within r_cut); a target whose
+        // sum left the FP32 range is redone below with a running maximum
+        const float ie2 = ie * LOG2E;
+        float s2 = 0.f;
         for (int q = 0; q < nnb; ++q) {
             const int c = s_nb[q];
             const int j0 = T.src.cstart[c], j1 = T.src.cstart[c + 1];
-            const float off = act && ref > -INFINITY ? (float)(s_L[q] - ref) : -INFINITY;
+            const float off2 = act && ref > -INFINITY ? (float)((s_L[q] - ref) * (double)LOG2E) : -INFINITY;
             for (int jb = j0; jb < j1; jb += LSE_CAP) {
                 const int cnt = min(LSE_CAP, j1 - jb);
                 __syncthreads();
                 for (int p = tid; p < cnt; p += LSE_THREADS) {
-                    for (int t = 0; t < g.d; ++t) sx[t][p] = T.src.u[(size_t)t * T.src.n + jb + p];
-                    sdel[p] = T.delta[jb + p];
+#pragma unroll
+                    for (int t = 0; t < D; ++t) sx[t][p] = T.src.u[(size_t)t * T.src.n + jb + p];
+                    sdel[p] = T.delta[jb + p] * LOG2E;
                 }
                 __syncthreads();
-                if (act && off > -INFINITY) {
+                if (act && off2 > -INFINITY) {
+#pragma unroll 4
                     for (int p = 0; p < cnt; ++p) {
                         float d2 = 0.f;
-                        for (int t = 0; t < g.d; ++t) {
+#pragma unroll
+                        for (int t = 0; t < D; ++t) {
                             const float e = xi[t] - sx[t][p];
                             d2 = fmaf(e, e, d2);
                         }
-                        if (d2 > r2) continue;
-                        const float e = off + sdel[p] - d2 * ie;
-                        if (e > m) {
-                            s = s * __expf(m - e) + 1.f;      // rescale the running sum to the new maximum
-                            m = e;
-                        } else {
-                            s += __expf(e - m);
+                        const float v = exp2f(fmaf(-d2, ie2, off2 + sdel[p]));
+                        s2 += d2 <= r2 ? v : 0.f;
+                    }
+                }
+            }
+        }
+        float m = 0.f, s = 0.f;                          // log beta = ref + m + log s
+        if (act && s2 >= exp2f(-LSE_MIN2)) s = s2;
+        const bool redo = act && !(s > 0.f);
+        if (__syncthreads_or(redo)) {
+            m = redo ? -INFINITY : m;
+            float sr = redo ? 0.f : s;
+            for (int q = 0; q < nnb; ++q) {
+                const int c = s_nb[q];
+                const int j0 = T.src.cstart[c], j1 = T.src.cstart[c + 1];
+                const float off = redo && ref > -INFINITY ? (float)(s_L[q] - ref) : -INFINITY;
+                for (int jb = j0; jb < j1; jb += LSE_CAP) {
+                    const int cnt = min(LSE_CAP, j1 - jb);
+                    __syncthreads();
+                    for (int p = tid; p < cnt; p += LSE_THREADS) {
+                        for (int t = 0; t < D; ++t) sx[t][p] = T.src.u[(size_t)t * T.src.n + jb + p];
+                        sdel[p] = T.delta[jb + p];
+                    }
+                    __syncthreads();
+                    if (redo && off > -INFINITY) {
+                        for (int p = 0; p < cnt; ++p) {
+                            float d2 = 0.f;
+                            for (int t = 0; t < D; ++t) {
+                                const float e = xi[t] - sx[t][p];
+                                d2 = fmaf(e, e, d2);
+                            }
+                            if (d2 > r2) continue;
+                            const float e = off + sdel[p] - d2 * ie;
+                            if (e > m) {
+                                sr = sr * __expf(m - e) + 1.f;      // rescale to the new maximum
+                                m = e;
+                            } else {
+                                sr += __expf(e - m);
+                            }
                         }
                     }
                 }
             }
+            s = sr;
         }
         if (act) {
             double lb = -INFINITY;
@@ -387,10 +440,11 @@ int blocks_of(long long n, int per) { return (int)std::min<long long>((n + per -
 
 }  // namespace
 
-cudaError_t launch_lbin(const LBinSet* sets_dev, int nsets, int nmax, const LGrid& g, int* err, cudaStream_t st) {
+cudaError_t launch_lbin(const LBinSet* sets_dev, int nsets, int nmax, const LGrid& g, int* err, int* maxcount,
+                        cudaStream_t st) {
     const int bx = blocks_of(nmax, 256);
     k_lbin_count<<<dim3(bx, nsets), 256, 0, st>>>(sets_dev, g, err);
-    k_lbin_scan<<<nsets, 1024, 0, st>>>(sets_dev, g.ncells);
+    k_lbin_scan<<<nsets, 1024, 0, st>>>(sets_dev, g.ncells, maxcount);
     k_lbin_scatter<<<dim3(bx, nsets), 256, 0, st>>>(sets_dev, g.d);
     return cudaGetLastError();
 }
@@ -401,10 +455,13 @@ cudaError_t launch_lsrc(const LTask* tasks, int ntask, const LFac* F, int ncells
     return cudaGetLastError();
 }
 
-cudaError_t launch_lse(const LTask* tasks, int ntask, const LFac* F, const LGrid& g, const LGlobals& G,
+cudaError_t launch_lse(const LTask* tasks, int ntask, int tchunks, const LFac* F, const LGrid& g, const LGlobals& G,
                        cudaStream_t st) {
     if (ntask <= 0) return cudaSuccess;
-    k_lse<<<dim3(g.ncells, ntask), LSE_THREADS, 0, st>>>(tasks, F, g, G);
+    const dim3 grid(g.ncells, ntask, std::max(1, tchunks));
+    if (g.d == 1) k_lse<1><<<grid, LSE_THREADS, 0, st>>>(tasks, F, g, G);
+    else if (g.d == 2) k_lse<2><<<grid, LSE_THREADS, 0, st>>>(tasks, F, g, G);
+    else k_lse<3><<<grid, LSE_THREADS, 0, st>>>(tasks, F, g, G);
     return cudaGetLastError();
 }
 

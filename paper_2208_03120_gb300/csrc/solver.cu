@@ -1282,7 +1282,7 @@ int run_wave(TreePlan& T, int S, cudaStream_t st, Timer& tm, long long& nl) {
         A.ctl = T.d_ctl;
         A.err = T.err;
         A.wait_ns = 1000000000ull;            // 1 s per wait (a chunk takes about a millisecond)
-        RET(tm.begin(MOT_K_FUSED, &e));
+        RET(tm.begin(MOT_K_WAVE, &e));
         CK(launch_wave2d(A, T.wave_clusters, T.G, st));
         RET(tm.end(e));
         nl += 1;
@@ -2271,6 +2271,8 @@ struct LocalPlan {
     LFac* d_fac = nullptr;
     size_t fac_cap = 0;
     LBinSet* d_bins = nullptr;
+    int* d_maxcount = nullptr;               // [K] most points in one cell, per set
+    std::vector<int> maxcount;
     float* box_scratch = nullptr;
     float* box_out = nullptr;
     PrepSet* d_sets = nullptr;
@@ -2334,6 +2336,7 @@ void layout_local(Arena& A, LocalPlan& L) {
     for (int k = 0; k < K; ++k) L.fac_cap += 2 * L.S.children[k].size();
     L.d_fac = A.take<LFac>(L.fac_cap);
     L.d_bins = A.take<LBinSet>(K);
+    L.d_maxcount = A.take<int>(K);
     L.d_sets = A.take<PrepSet>(K);
     L.box_scratch = A.take<float>(8);
     L.box_out = A.take<float>(8);
@@ -2354,6 +2357,8 @@ LTask ltask_blank() {
     std::memset(&t, 0, sizeof(t));
     return t;
 }
+
+int lchunks(const LocalPlan& L, int node) { return (L.maxcount[node] + LSE_TARGETS - 1) / LSE_TARGETS; }
 
 void ltask_kernel(LocalPlan& L, LTask& t, int k) {
     const double eta_e = L.eta / L.S.w[k];
@@ -2392,6 +2397,7 @@ void local_build(LocalPlan& L) {
         t.mode = LEPI_FWD;
         t.out = L.g[k];
         t.f = L.f[k];
+        t.tchunks = lchunks(L, k);
         L.fwd.push_back(t);
     }
     auto root_task = [&](int mode) {
@@ -2422,6 +2428,7 @@ void local_build(LocalPlan& L) {
         ltask_kernel(L, t, k);
         t.mode = LEPI_MSG;
         t.out = L.b[k];
+        t.tchunks = lchunks(L, S.parent[k]);
         L.bwd[maxdepth - S.depth[k]].push_back(t);
     }
     L.chk.assign(std::max(maxdepth, 1), {});
@@ -2446,6 +2453,7 @@ void local_build(LocalPlan& L) {
         t.out = L.gx[k];
         t.f = L.f[k];
         t.acc_node = L.acc_node + 3 * k;
+        t.tchunks = lchunks(L, k);
         L.chk[S.depth[k] - 1].push_back(t);
     }
     L.chkroot.assign(1, root_task(LEPI_CHKROOT));
@@ -2545,7 +2553,12 @@ int local_setup(const mot_problem* P, const mot_options& o, LocalPlan& L, void* 
         CK(cudaMemsetAsync(L.bins[k].cstart, 0, sizeof(int) * (L.grid.ncells + 1), st));
     }
     CK(cudaMemcpyAsync(L.d_bins, L.bins.data(), sizeof(LBinSet) * L.K, cudaMemcpyHostToDevice, st));
-    CK(launch_lbin(L.d_bins, L.K, L.nmax, L.grid, L.err, st));
+    CK(cudaMemsetAsync(L.d_maxcount, 0, sizeof(int) * L.K, st));
+    CK(launch_lbin(L.d_bins, L.K, L.nmax, L.grid, L.err, L.d_maxcount, st));
+    // the fullest cell of each set sizes the log-sum-exp grid (one readback)
+    L.maxcount.assign(L.K, 0);
+    CK(cudaMemcpyAsync(L.maxcount.data(), L.d_maxcount, sizeof(int) * L.K, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     L.LG.iter = L.iter;
     L.LG.acc = L.acc;
     L.LG.R = kRing;
@@ -2559,12 +2572,26 @@ int local_setup(const mot_problem* P, const mot_options& o, LocalPlan& L, void* 
     return MOT_OK;
 }
 
-int local_backward(LocalPlan& L, cudaStream_t st, long long& nl) {
-    for (size_t l = 0; l < L.bwd.size(); ++l) {
-        CK(launch_lsrc(L.d_bwd[l], (int)L.bwd[l].size(), L.d_fac, L.grid.ncells, L.err, st));
-        CK(launch_lse(L.d_bwd[l], (int)L.bwd[l].size(), L.d_fac, L.grid, L.LG, st));
-        nl += 2;
-    }
+// One level of truncated kernel sums: per-cell source maxima, then the log-sum-exp (timed as
+// MOT_K_NODE and MOT_K_LOCAL).
+int local_level(LocalPlan& L, const LTask* d, const std::vector<LTask>& h, cudaStream_t st, Timer& tm, long long& nl) {
+    cudaEvent_t e = nullptr;
+    const int n = (int)h.size();
+    int tch = 1;
+    for (const LTask& t : h) tch = std::max(tch, t.tchunks);
+    if (tch > 65535) return MOT_EUNSUPPORTED;             // a cell of more than 2^24 points
+    RET(tm.begin(MOT_K_NODE, &e));
+    CK(launch_lsrc(d, n, L.d_fac, L.grid.ncells, L.err, st));
+    RET(tm.end(e));
+    RET(tm.begin(MOT_K_LOCAL, &e));
+    CK(launch_lse(d, n, tch, L.d_fac, L.grid, L.LG, st));
+    RET(tm.end(e));
+    nl += 2;
+    return MOT_OK;
+}
+
+int local_backward(LocalPlan& L, cudaStream_t st, Timer& tm, long long& nl) {
+    for (size_t l = 0; l < L.bwd.size(); ++l) RET(local_level(L, L.d_bwd[l], L.bwd[l], st, tm, nl));
     return MOT_OK;
 }
 
@@ -2573,14 +2600,13 @@ int local_iteration(LocalPlan& L, cudaStream_t st, Timer& tm, long long& nl) {
     RET(tm.begin(MOT_K_NODE, &e));
     CK(launch_prologue(nullptr, 0, 0, 1, nullptr, 0, L.G, st));
     RET(tm.end(e));
-    RET(tm.begin(MOT_K_DENSE, &e));
-    CK(launch_lsrc(L.d_fwd, (int)L.fwd.size(), L.d_fac, L.grid.ncells, L.err, st));
-    CK(launch_lse(L.d_fwd, (int)L.fwd.size(), L.d_fac, L.grid, L.LG, st));
+    nl += 1;
+    RET(local_level(L, L.d_fwd, L.fwd, st, tm, nl));
+    RET(tm.begin(MOT_K_NODE, &e));
     CK(launch_lroot(L.d_root, 1, L.d_fac, L.nmax, L.LG, st));
-    nl += 4;
-    RET(local_backward(L, st, nl));
     RET(tm.end(e));
-    return MOT_OK;
+    nl += 1;
+    return local_backward(L, st, tm, nl);
 }
 
 int local_check(LocalPlan& L, cudaStream_t st, Timer& tm, long long& nl) {
@@ -2590,18 +2616,23 @@ int local_check(LocalPlan& L, cudaStream_t st, Timer& tm, long long& nl) {
     CK(launch_lroot(L.d_chkroot, 1, L.d_fac, L.nmax, L.LG, st));
     RET(tm.end(e));
     nl += 2;
-    RET(tm.begin(MOT_K_DENSE, &e));
-    for (size_t l = 0; l < L.chk.size(); ++l) {
-        CK(launch_lsrc(L.d_chk[l], (int)L.chk[l].size(), L.d_fac, L.grid.ncells, L.err, st));
-        CK(launch_lse(L.d_chk[l], (int)L.chk[l].size(), L.d_fac, L.grid, L.LG, st));
-        nl += 2;
-    }
-    RET(tm.end(e));
+    for (size_t l = 0; l < L.chk.size(); ++l) RET(local_level(L, L.d_chk[l], L.chk[l], st, tm, nl));
     return MOT_OK;
 }
 
 int local_iterations(LocalPlan& L, int count, cudaStream_t st, Timer& tm, long long& nl, bool graphs) {
     if (count <= 0) return MOT_OK;
+    if (graphs && tm.on && st != nullptr) {
+        long long per = 0;
+        RET(tm.timed_graph(count, 2 * (size_t)(4 * L.K + 8), [&](long long& dn) {
+            const long long before = dn;
+            const int rc = local_iteration(L, st, tm, dn);
+            per = dn - before;
+            return rc;
+        }));
+        nl += per * count;
+        return MOT_OK;
+    }
     if (graphs && !tm.on && st != nullptr) {
         if (L.gexec == nullptr || L.graph_iters != count) {
             if (L.gexec) {
@@ -2640,7 +2671,7 @@ struct LocalOps : PlanOps {
             CK(launch_linit(L.f[k], L.bins[k].perm, L.bins[k].mu_s, L.S.n[k], uw, L.eta, &L.acc[0].logphi, st));
             nl += 1;
         }
-        return local_backward(L, st, nl);    // Algorithm 2, steps 3-5
+        return local_backward(L, st, tm, nl);    // Algorithm 2, steps 3-5
     }
     int iterations(int count, cudaStream_t st, Timer& tm, long long& nl, bool graphs) override {
         return local_iterations(L, count, st, tm, nl, graphs);

@@ -17,8 +17,9 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmotfft.s
 MOT_OK, MOT_EINVAL, MOT_ENOTTREE, MOT_ENOMEM, MOT_ENUMERIC, MOT_ENOCONV, MOT_ETIMEOUT, MOT_ECUDA, MOT_EUNSUPPORTED = range(9)
 MOT_TREE, MOT_CIRCLE = 0, 1
 MOT_PATH_NFFT, MOT_PATH_DENSE, MOT_PATH_DENSE_BF16X3, MOT_PATH_LOCAL = 0, 1, 2, 3
-MOT_NKCLASS = 10
-KERNEL_CLASSES = ["spread", "fftconv", "gather", "dense", "node", "setup", "circle", "fused", "tcgemm", "split"]
+MOT_NKCLASS = 12
+KERNEL_CLASSES = ["spread", "fftconv", "gather", "dense", "node", "setup", "circle", "fused", "tcgemm", "split",
+                  "wave", "local"]
 
 
 class MotError(RuntimeError):

@@ -192,10 +192,11 @@ class Request:
 
 def serving_stream(n_requests: int = 2000, rate_hz: float = 100.0, seed: Optional[int] = None,
                    n_range: Tuple[int, int] = (500, 20_000), k_range: Tuple[int, int] = (3, 20),
-                   circle_n_max: Optional[int] = None) -> List[Request]:
+                   circle_n_max=None) -> List[Request]:
     """Poisson arrivals; topology uniform over {path, star, circle}; K ~ U{3..20};
     d ~ U{1,2,3}; N log-uniform on [500, 20000]; eta in {0.01, 0.05, 0.1}.
-    ``circle_n_max`` caps N of circle requests (their cost grows as K N^2)."""
+    ``circle_n_max`` caps N of circle requests (their cost grows as K N^2): an int for every
+    dimension, or a dict {d: cap} (dimensions not listed are not capped)."""
     rng = _rng(4, seed)
     t = 0.0
     out = []
@@ -208,8 +209,9 @@ def serving_stream(n_requests: int = 2000, rate_hz: float = 100.0, seed: Optiona
         eta = float(rng.choice([0.01, 0.05, 0.1]))
         sub = np.random.Generator(np.random.PCG64(int(rng.integers(0, 2**63 - 1))))
         if kind == 2:
-            if circle_n_max is not None:
-                N = min(N, circle_n_max)
+            cap = circle_n_max.get(d) if isinstance(circle_n_max, dict) else circle_n_max
+            if cap is not None:
+                N = min(N, cap)
             prob = random_problem(sub, CIRCLE, K, d, N, eta)
         else:
             prob = random_problem(sub, TREE, K, d, N, eta, shape="path" if kind == 0 else "star")
