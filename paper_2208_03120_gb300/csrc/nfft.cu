@@ -148,9 +148,13 @@ struct RunSpread {
 // of one cell in registers and add them to the shared grid only when the cell changes.
 // ------------------------------------------------------------------------------------------
 constexpr int SP2_B = 16;         // points per warp batch
-constexpr int SP2_ROW = 24;       // staged floats per point: v wx [0,10), wy [12,22), cell key [23]
+constexpr int SP2_ROW = 24;       // staged floats per point: v wx [0,10), wy [12,24) in the order
+                                  // 0 3 6 9 | 1 4 7 - | 2 5 8 - (one float4 per lane row group)
 constexpr int SP2_WARP = SP2_B * SP2_ROW;
 
+// Lane (a, blk) = (lane % 10, lane / 10), lanes < 30, owns tap column a and tap rows blk, blk + 3,
+// blk + 6 (, blk + 9 for blk = 0): the rows of one flush instruction are then consecutive, and in a
+// grid whose row stride is 10 mod 32 the 30 lanes of every atomic hit 30 different banks.
 struct Spread2Acc {
     float acc[4];
     int a, b0, nb;
@@ -158,17 +162,18 @@ struct Spread2Acc {
     __device__ __forceinline__ void init(int lane) {
         on = lane < 30;
         a = on ? lane % MOT_W : 0;
-        b0 = on ? 4 * (lane / MOT_W) : 8;         // lanes 30, 31 read a valid slot and never add
-        nb = lane < 20 ? 4 : 2;
+        b0 = on ? lane / MOT_W : 2;               // lanes 30, 31 read a valid slot and never add
+        nb = b0 == 0 ? 4 : 3;
         zero();
     }
+    __device__ __forceinline__ int row(int i) const { return b0 + 3 * i; }
     __device__ __forceinline__ void zero() {
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[i] = 0.f;
     }
     __device__ __forceinline__ void step(const float* row) {
         const float xa = row[a];
-        const float4 y = *reinterpret_cast<const float4*>(row + 12 + b0);
+        const float4 y = *reinterpret_cast<const float4*>(row + 12 + 4 * b0);   // wy[b0], wy[b0+3], ...
         acc[0] = fmaf(xa, y.x, acc[0]);
         acc[1] = fmaf(xa, y.y, acc[1]);
         acc[2] = fmaf(xa, y.z, acc[2]);
@@ -205,9 +210,9 @@ __device__ __forceinline__ int spread2_stage(float* stg, int lane, int jb, int c
             *reinterpret_cast<float4*>(row + 4) = make_float4(w[4], w[5], w[6], w[7]);
             *reinterpret_cast<float2*>(row + 8) = make_float2(w[8], w[9]);
         } else {
-            *reinterpret_cast<float4*>(row + 12) = make_float4(w[0], w[1], w[2], w[3]);
-            *reinterpret_cast<float4*>(row + 16) = make_float4(w[4], w[5], w[6], w[7]);
-            *reinterpret_cast<float2*>(row + 20) = make_float2(w[8], w[9]);
+            *reinterpret_cast<float4*>(row + 12) = make_float4(w[0], w[3], w[6], w[9]);
+            *reinterpret_cast<float4*>(row + 16) = make_float4(w[1], w[4], w[7], 0.f);
+            *reinterpret_cast<float4*>(row + 20) = make_float4(w[2], w[5], w[8], 0.f);
         }
     }
     __syncwarp();
@@ -300,7 +305,7 @@ __global__ void __launch_bounds__(256) k_spread(const Task* __restrict__ tasks, 
                 if (S.on)
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
-                        if (i < S.nb) atomicAdd(&tile[key + (S.b0 + i) * P + S.a], S.acc[i]);
+                        if (i < S.nb) atomicAdd(&tile[key + S.row(i) * P + S.a], S.acc[i]);
             };
             for (int jb = j0; jb < j1; jb += SP2_B) {
                 const int cnt = min(SP2_B, j1 - jb);
@@ -494,6 +499,7 @@ __global__ void k_c1_taps(const float* __restrict__ u, int n, int* __restrict__ 
 #define F2_SLOTS (F2_MAXPTS / 8)
 // dynamic shared memory: spread staging (SP2_WARP floats per warp), then the rank's source
 // coordinates and values (3 x F2_SLOTS floats; a rank holds at most 1/8 of the sources)
+#define F2_LD 74           // row stride of the shared grid: 10 mod 32 (conflict-free spread flushes)
 #define F2_DYN_SMEM ((F2_THREADS / 32 * SP2_WARP + 3 * F2_SLOTS) * 4)
 
 // Sum of `v` over groups of G consecutive lanes (G a power of two <= 32).
@@ -513,7 +519,7 @@ struct __align__(16) F2Sh {
     double sLsrc;
     int s_ylo, s_yhi;                   // window rows of this CTA's targets
     int s_next;                         // next spread batch of this CTA
-    float Gs[F2_N * F2_N];
+    float Gs[F2_N * F2_LD];
     float Grow[F2_MAXR * F2_N];
     float2 Gx[F2_MAXR * (F2_M + 1)];
     float2 Ycol[F2_MAXC][F2_N];
@@ -542,7 +548,7 @@ __device__ __forceinline__ void f2_prep(F2Sh& S, const Task* task, int n) {
         S.s_yhi = -(1 << 30);
         S.s_next = 0;
     }
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) S.Gs[i] = 0.f;
+    for (int i = threadIdx.x; i < n * F2_LD; i += blockDim.x) S.Gs[i] = 0.f;
 }
 
 // The product itself, after f2_prep and a block barrier, once the results of the products it
@@ -629,7 +635,7 @@ __device__ __forceinline__ void f2_run(F2Sh& S, float* f2_stage, const Globals& 
                 if (S.on)
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
-                        if (i < S.nb) atomicAdd(&Gs[((cly + S.b0 + i) & mask) * n + ((clx + S.a) & mask)], S.acc[i]);
+                        if (i < S.nb) atomicAdd(&Gs[((cly + S.row(i)) & mask) * F2_LD + ((clx + S.a) & mask)], S.acc[i]);
             };
             for (;;) {
                 int k = 0;
@@ -671,8 +677,9 @@ __device__ __forceinline__ void f2_run(F2Sh& S, float* f2_stage, const Globals& 
             for (int q = 0; q < 16; ++q) peer[q] = cluster.map_shared_rank(Gs, q < CS ? q : 0);
             for (int i = tid; i < R * n; i += nt) {
                 float part[16];
+                const int gi = (y0 + i / n) * F2_LD + (i % n);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) part[q] = q < CS ? peer[q][y0 * n + i] : 0.f;
+                for (int q = 0; q < 16; ++q) part[q] = q < CS ? peer[q][gi] : 0.f;
                 float s = 0.f;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) s += part[q];
@@ -802,7 +809,7 @@ __device__ __forceinline__ void f2_run(F2Sh& S, float* f2_stage, const Globals& 
                         const int y = (ylo + q) & mask, x = i - q * n;
                         const int owner = y / R;
                         vals[u4] = cluster.map_shared_rank(Hrow, owner)[(y - owner * R) * n + x];
-                        dst[u4] = y * n + x;
+                        dst[u4] = y * F2_LD + x;
                     }
                 }
 #pragma unroll
@@ -827,7 +834,7 @@ __device__ __forceinline__ void f2_run(F2Sh& S, float* f2_stage, const Globals& 
             float acc = 0.f;
 #pragma unroll
             for (int b = 0; b < MOT_W; ++b) {
-                const float* row = Gs + ((ly + b) & mask) * n;
+                const float* row = Gs + ((ly + b) & mask) * F2_LD;
                 float s2 = 0.f;
 #pragma unroll
                 for (int a = 0; a < MOT_W; ++a) s2 = fmaf(row[(lx + a) & mask], wx[a], s2);
