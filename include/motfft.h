@@ -30,7 +30,7 @@
 extern "C" {
 #endif
 
-#define MOT_ABI_VERSION 4
+#define MOT_ABI_VERSION 5
 
 /* ---- status codes ---------------------------------------------------------------- */
 #define MOT_OK           0
@@ -129,6 +129,11 @@ typedef struct {
     double r_cut;       /* MOT_PATH_LOCAL: pairs farther apart than r_cut leave every kernel sum
                            [0 = sqrt(40 eta / w_e) per edge, where the kernel is below e^-40].  Every
                            target needs a source point within r_cut (MOT_ENUMERIC otherwise)     */
+    int ndft;           /* d = 2, MOT_PATH_NFFT, n_grid <= 64 (M <= 16), point sets of up to 32768:
+                           1 = evaluate the trigonometric sums of the fast summation, Eq. (ndft*)
+                           for ghat and Eq. (ndft) for the result, exactly as dense FP32
+                           contractions in one thread-block cluster per product; -1 = through the
+                           oversampled grid (NFFT, with the window error of Section 5) [1]       */
 } mot_options;
 
 /* Fill *o with the defaults. */

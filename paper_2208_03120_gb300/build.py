@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmotfft.so")
 
-SOURCES = ["nfft.cu", "dense.cu", "prep.cu", "circle.cu", "solver.cu", "static_scratch.cu", "tc_gemm.cu", "local.cu"]
+SOURCES = ["nfft.cu", "ndft2d.cu", "dense.cu", "prep.cu", "circle.cu", "solver.cu", "static_scratch.cu", "tc_gemm.cu", "local.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

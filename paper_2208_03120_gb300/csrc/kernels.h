@@ -61,6 +61,14 @@ struct WaveArgs {
 };
 int wave2d_max_active_clusters();    // co-resident clusters of the persistent kernel (0 before set-up)
 cudaError_t launch_wave2d(const WaveArgs& A, int nclusters, const Globals& G, cudaStream_t st);
+// The same two kernels with the exact trigonometric sums (ndft2d.cu) in place of the oversampled
+// grid: d = 2, M <= 16, D without window deconvolution (launch_make_D deconv = false).
+cudaError_t prepare_ndft2d();
+bool ndft2d_supported(int d, int M);
+int ndft2d_max_active_clusters();
+int ndft2d_wave_max_active_clusters();
+cudaError_t launch_ndft2d(const Task* tasks, int ntask, const Globals& G, cudaStream_t st, bool msg_only);
+cudaError_t launch_wave_nd(const WaveArgs& A, int nclusters, const Globals& G, cudaStream_t st);
 // Batched 1-D fast summation of the circle (grids n <= 128): per-point window taps and base cells
 // (once per solve), the circulant of D (once per edge), and one batch Y[c] = K (phi (.) X[c]):
 // stage 0 zeroes G and spreads, stage 1 convolves, interpolates and writes the messages.
@@ -105,10 +113,11 @@ cudaError_t launch_bounds(const PrepSet* sets, int nsets, int d, float* box_raw,
 cudaError_t launch_prep(const PrepSet* sets_dev, const PrepSet* sets_host, int nsets, int d, int n_grid,
                         const double* c, double s, int* err_flag, cudaStream_t st);
 // kappa_hat by the (2M)^d FFT of Eq. (fft) in FP64, then the half-spectrum multiplier
-// D = w kappa_hat / Psi^2 for the grid of length n per dimension.
+// D = w kappa_hat / Psi^2 for the grid of length n per dimension (deconv = false: D = w kappa_hat,
+// the multiplier of the exact trigonometric sums).
 cudaError_t launch_make_D(int d, int M, int n, double eta_n, double tau, double epsB, int p,
                           const double* poly /* host [2p+1] coefficients in t = r - (tau-epsB) */,
-                          double* scratch_a, double* scratch_b, float* D, cudaStream_t st);
+                          double* scratch_a, double* scratch_b, float* D, cudaStream_t st, bool deconv = true);
 size_t make_D_scratch_doubles(int d, int M);
 size_t D_floats(int d, int M);
 // u_out[perm[i]] = eta * (log(phi[i]) + ls)

@@ -15,6 +15,7 @@
 #include "kernels.h"
 #include "fft_smem.cuh"
 #include "window.cuh"
+#include "wave.cuh"
 
 constexpr int kMaxDevices = 64;   // per-device one-time set-up tables
 
@@ -900,47 +901,6 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_fastsum2d(const Task* __restr
 // the CTA sets bit 2 (value 4) of the error word and the abort word, which stops all claims; the
 // cluster still runs its product (on whatever data) so that every CTA meets every cluster barrier.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long f2_globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_gpu(int* p, int v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ int wave_claim(const WaveArgs& A) {
-    if (*reinterpret_cast<volatile int*>(&A.ctl->abort)) return A.ntask;
-    return atomicAdd(&A.ctl->next, 1);
-}
-
-// Warp 0 waits: lane q polls the flags of dependencies q, q + 32, ... (one round trip to L2 for
-// all of them instead of one per dependency), each lane bounded by wait_ns.
-__device__ __forceinline__ void wave_wait_warp(const WaveArgs& A, int i, int epoch, int lane) {
-    const int d0 = A.tasks[i].dep0, nd = A.tasks[i].ndep;
-    unsigned long long t0 = 0;
-    for (int q = lane; q < nd; q += 32) {
-        const int* f = A.flags + A.deps[d0 + q];
-        while (ld_acquire_gpu(f) != epoch) {
-            if (*reinterpret_cast<volatile int*>(&A.ctl->abort)) return;
-            const unsigned long long now = f2_globaltimer();
-            if (t0 == 0) {
-                t0 = now;
-            } else if (now - t0 > A.wait_ns) {
-                atomicOr(A.err, 4);
-                atomicExch(&A.ctl->abort, 1);
-                return;
-            }
-            __nanosleep(32);
-        }
-    }
-}
-
 __global__ void __launch_bounds__(F2_THREADS, 1) k_wave2d(WaveArgs A, Globals G) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();

@@ -250,10 +250,12 @@ __device__ double window_ft(int k, int n) {
     return i0 * 3.14159265358979323846 * a / sinh(a * b);
 }
 
-__global__ void k_make_D(const double* __restrict__ khat, float* D, int d, int M, int n) {
+// deconv = 0: the weighted coefficients alone (for the exact trigonometric sums, which need no
+// window deconvolution).
+__global__ void k_make_D(const double* __restrict__ khat, float* D, int d, int M, int n, int deconv) {
     extern __shared__ double inv_psi2[];                   // 1 / Psi(k)^2, k = 0..M
     for (int k = threadIdx.x; k <= M; k += blockDim.x) {
-        const double p = window_ft(k, n);
+        const double p = deconv ? window_ft(k, n) : 1.0;
         inv_psi2[k] = 1.0 / (p * p);
     }
     __syncthreads();
@@ -398,7 +400,7 @@ size_t D_floats(int d, int M) {
 }
 
 cudaError_t launch_make_D(int d, int M, int n, double eta_n, double tau, double epsB, int p, const double* poly,
-                          double* scratch_a, double* scratch_b, float* D, cudaStream_t st) {
+                          double* scratch_a, double* scratch_b, float* D, cudaStream_t st, bool deconv) {
     KernelArgs K;
     K.d = d;
     K.M = M;
@@ -427,7 +429,7 @@ cudaError_t launch_make_D(int d, int M, int n, double eta_n, double tau, double 
         in = out;
         out = tmp;
     }
-    k_make_D<<<blocks_for((long long)D_floats(d, M)), 256, sizeof(double) * (M + 1), st>>>(in, D, d, M, n);
+    k_make_D<<<blocks_for((long long)D_floats(d, M)), 256, sizeof(double) * (M + 1), st>>>(in, D, d, M, n, deconv ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -143,6 +143,7 @@ void fill_defaults(mot_options& o, const mot_options* in) {
     if (o.eps_B <= 0.0) o.eps_B = 1.0 / 16.0;
     if (o.use_graphs == 0) o.use_graphs = 1;
     if (o.wavefront == 0) o.wavefront = 1;
+    if (o.ndft == 0) o.ndft = 1;
 }
 
 // =============================================================================================
@@ -241,11 +242,11 @@ int measure_and_choose(const std::vector<PrepSet>& sets, PrepSet* d_sets, float*
 }
 
 int make_D_for(double eta_e_norm, const GridChoice& g, int d, const mot_options& o, double* sa, double* sb,
-               float* D, cudaStream_t st) {
+               float* D, cudaStream_t st, bool deconv = true) {
     double poly[2 * 8 + 1];
     if (o.p > 8) return MOT_EINVAL;
     if (!boundary_poly(eta_e_norm, kTau, o.eps_B, o.p, poly)) return MOT_ENUMERIC;
-    CK(launch_make_D(d, g.M, g.n, eta_e_norm, kTau, o.eps_B, o.p, poly, sa, sb, D, st));
+    CK(launch_make_D(d, g.M, g.n, eta_e_norm, kTau, o.eps_B, o.p, poly, sa, sb, D, st, deconv));
     return MOT_OK;
 }
 
@@ -302,6 +303,7 @@ struct TreePlan {
     size_t it_reset0 = 0, it_reset_n = 0;     // iteration prologue: phi (prev kept) and gamma records
     size_t ck_reset0 = 0, ck_reset_n = 0;     // check prologue: gamma-ex records (+ acc_node zeroed)
     bool fused = false;                        // 2-D grids <= 64: one cluster kernel per level
+    bool ndft = false;                         // ... evaluating the trigonometric sums exactly (ndft2d.cu)
     // wavefront schedule (fused path): beta_k alternates between two copies from sweep to sweep
     std::vector<float*> beta2;                 // the second copy of every beta_k
     std::vector<Level> chk1;                   // check pass reading the second copy
@@ -884,7 +886,8 @@ int build_wave(TreePlan& T, int S, int q0, bool with_check, cudaStream_t st) {
     // a launch takes at most as many products as clusters fit on the GPU at once (one more would
     // run as a second wave); a product that finds its first possible launch full takes the next
     // (the persistent kernel: as many products as it runs clusters)
-    const int ncl = T.persist ? T.wave_clusters : fused2d_max_active_clusters();
+    const int ncl = T.persist ? T.wave_clusters
+                              : (T.ndft ? ndft2d_max_active_clusters() : fused2d_max_active_clusters());
     const int cap = std::max(1, ncl > 0 ? ncl : 8);
     std::vector<int> tFf((size_t)S * K), tBf((size_t)S * K), tR(S), carrier(S);
     int nlaunch = 0;
@@ -1211,7 +1214,10 @@ int run_level(TreePlan& T, Level& L, cudaStream_t st, Timer& tm, long long& nl) 
     cudaEvent_t e = nullptr;
     if (T.path == MOT_PATH_NFFT && T.fused) {
         RET(tm.begin(MOT_K_FUSED, &e));
-        CK(launch_fused2d(L.d_tgt, (int)L.tgt.size(), T.G, st, L.msg_only));
+        if (T.ndft)
+            CK(launch_ndft2d(L.d_tgt, (int)L.tgt.size(), T.G, st, L.msg_only));
+        else
+            CK(launch_fused2d(L.d_tgt, (int)L.tgt.size(), T.G, st, L.msg_only));
         RET(tm.end(e));
         nl += 1;
     } else if (T.path == MOT_PATH_NFFT) {
@@ -1283,7 +1289,10 @@ int run_wave(TreePlan& T, int S, cudaStream_t st, Timer& tm, long long& nl) {
         A.err = T.err;
         A.wait_ns = 1000000000ull;            // 1 s per wait (a chunk takes about a millisecond)
         RET(tm.begin(MOT_K_WAVE, &e));
-        CK(launch_wave2d(A, T.wave_clusters, T.G, st));
+        if (T.ndft)
+            CK(launch_wave_nd(A, T.wave_clusters, T.G, st));
+        else
+            CK(launch_wave2d(A, T.wave_clusters, T.G, st));
         RET(tm.end(e));
         nl += 1;
         return MOT_OK;
@@ -1487,11 +1496,17 @@ int tree_plan_setup(const mot_problem* P, const mot_options& o, TreePlan& T, voi
         int nmax = 0;
         for (int k = 0; k < T.K; ++k) nmax = std::max(nmax, T.n[k]);
         T.fused = fused2d_supported(T.d, g.n) && nmax <= fused2d_max_points();
+        T.ndft = false;
+        if (T.fused && o.ndft > 0) {
+            CK(prepare_ndft2d());
+            T.ndft = ndft2d_supported(T.d, g.M);
+        }
         bool any_free = false;
         for (int k = 0; k < T.K; ++k) any_free = any_free || T.free_[k];
         T.wave = T.fused && !any_free && o.wavefront > 0;
-        T.wave_clusters = g_wave_clusters_override.load() > 0 ? g_wave_clusters_override.load()
-                                                               : wave2d_max_active_clusters();
+        T.wave_clusters = g_wave_clusters_override.load() > 0
+                              ? g_wave_clusters_override.load()
+                              : (T.ndft ? ndft2d_wave_max_active_clusters() : wave2d_max_active_clusters());
         T.persist = T.wave && o.wavefront == 1 && T.wave_clusters > 0;
         if (T.wave) {
             CK(cudaMemsetAsync(T.d_flags, 0, sizeof(int) * T.wtask_cap, st));
@@ -1508,7 +1523,7 @@ int tree_plan_setup(const mot_problem* P, const mot_options& o, TreePlan& T, voi
                 T.D[k] = T.D[same];
             } else {
                 double eta_n = (T.eta / T.w[k]) / (g.s * g.s);
-                RET(make_D_for(eta_n, g, T.d, o, T.dscr_a, T.dscr_b, T.D[k], st));
+                RET(make_D_for(eta_n, g, T.d, o, T.dscr_a, T.dscr_b, T.D[k], st, !T.ndft));
             }
             CK(cudaMemsetAsync(T.grid[k], 0, gsz * sizeof(float), st));
         }
@@ -3074,10 +3089,18 @@ int fastsum_impl(int d, double eta, const float* x_src, int64_t n_src, const flo
     const double eta_n = eta / (g.s * g.s);
     size_t gsz = 1;
     for (int t = 0; t < d; ++t) gsz *= g.n;
+    // d = 2 on grids of up to 64 with sets of up to 32768 points: the exact trigonometric sums in
+    // one cluster per right-hand side (ndft2d.cu) instead of spread / FFT / gather
+    bool nd = false;
+    if (o.path == MOT_PATH_NFFT && d == 2 && o.ndft > 0 && g.M <= 16 && n_src <= fused2d_max_points() &&
+        n_tgt <= fused2d_max_points()) {
+        CK(prepare_ndft2d());
+        nd = ndft2d_supported(d, g.M);
+    }
     if (o.path == MOT_PATH_NFFT) {
         CK(prepare_window());
         CK(prepare_fftconv(d, g.n));
-        RET(make_D_for(eta_n, g, d, o, F.dscr_a, F.dscr_b, F.D, st));
+        RET(make_D_for(eta_n, g, d, o, F.dscr_a, F.dscr_b, F.D, st, !nd));
         for (int r = 0; r < nrhs; ++r) CK(cudaMemsetAsync(F.grid[r], 0, gsz * sizeof(float), st));
     } else if (o.path == MOT_PATH_DENSE) {
         for (int r = 0; r < nrhs; ++r) CK(cudaMemsetAsync(F.raw[r], 0, sizeof(float) * n_tgt, st));
@@ -3109,7 +3132,9 @@ int fastsum_impl(int d, double eta, const float* x_src, int64_t n_src, const flo
     G.n_grid = g.n;
     G.M = g.M;
     G.fac = nullptr;
-    if (o.path == MOT_PATH_NFFT) {
+    if (nd) {
+        CK(launch_ndft2d(F.d_tasks, nrhs, G, st, false));
+    } else if (o.path == MOT_PATH_NFFT) {
         int gx = std::min(F.src.maxsub, 1024), gt = std::min(F.tgt.maxsub, 1024);
         CK(launch_spread(d, F.d_tasks, nrhs, gx, G, st));
         CK(launch_fftconv(d, F.d_tasks, nrhs, G, st, nullptr));

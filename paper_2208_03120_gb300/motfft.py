@@ -60,7 +60,7 @@ class Options(C.Structure):
         ("n_grid", C.c_int), ("m", C.c_int), ("p", C.c_int),
         ("eps_B", C.c_double),
         ("use_graphs", C.c_int), ("timing", C.c_int), ("wavefront", C.c_int),
-        ("r_cut", C.c_double),
+        ("r_cut", C.c_double), ("ndft", C.c_int),
     ]
 
 

@@ -35,7 +35,7 @@ def test_header_declarations_exported(M):
 
 def test_abi_version_and_strerror(M):
     lib = M.lib()
-    assert lib.mot_abi_version() == 4
+    assert lib.mot_abi_version() == 5
     assert M.strerror(0) == "ok"
     assert "tree" in M.strerror(M.MOT_ENOTTREE)
     assert M.strerror(12345) == "unknown status"
@@ -54,7 +54,7 @@ def test_options_defaults(M):
     assert o.max_iter == 1000 and o.check_every == 10 and o.m == 4 and o.p == 3
     assert abs(o.tol_viol - 1e-6) < 1e-18 and abs(o.eps_B - 1 / 16) < 1e-15
     assert o.n_grid == 0 and o.path == M.MOT_PATH_NFFT
-    assert o.wavefront == 1 and o.use_graphs == 1
+    assert o.wavefront == 1 and o.use_graphs == 1 and o.ndft == 1
 
 
 def _fake_problem(M, K, d, n, edges, topology=0, edge_w=None):
