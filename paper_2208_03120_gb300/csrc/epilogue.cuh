@@ -154,11 +154,10 @@ struct EpiPre {
     int iter;
 };
 
-// Factor caches and epilogue constants of a task with one barrier: warps 0 / 1 fill the source /
-// target caches, warp 2 reads the scale records; thread 0 then derives the constants, which the
-// other threads may read after the caller's next barrier.  Needs at least 3 warps.
-__device__ __forceinline__ void load_task_consts(const Task& T, const Globals& G, FacCache& fc, FacCache& tf,
-                                                 EpiPre& pre, EpiConst& C, double& sLsrc) {
+// Factor caches of a task with one barrier: warps 0 / 1 fill the source / target caches, warp 2
+// reads the scale records.  Needs at least 3 warps.
+__device__ __forceinline__ void load_task_caches(const Task& T, const Globals& G, FacCache& fc, FacCache& tf,
+                                                 EpiPre& pre) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) {
         if (T.alpha == nullptr) {
@@ -176,7 +175,12 @@ __device__ __forceinline__ void load_task_consts(const Task& T, const Globals& G
         pre.iter = (G.iter ? *G.iter : 0) - T.iter_off;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+}
+
+// The epilogue constants from the caches (one thread; the FP64 part of a task's set-up).
+__device__ __forceinline__ void task_consts(const Task& T, const FacCache& fc, const FacCache& tf, const EpiPre& pre,
+                                            EpiConst& C, double& sLsrc) {
+    {
         const double Lsrc = T.alpha == nullptr ? fc.L : 0.0;
         sLsrc = Lsrc;
         C.lsphi = phi_logscale(T, tf, Lsrc);
@@ -192,6 +196,14 @@ __device__ __forceinline__ void load_task_consts(const Task& T, const Globals& G
         }
         C.invEs = 1.0 / fmax(C.E, 1.0);
     }
+}
+
+// Factor caches and epilogue constants of a task with one barrier; thread 0 derives the
+// constants, which the other threads may read after the caller's next barrier.
+__device__ __forceinline__ void load_task_consts(const Task& T, const Globals& G, FacCache& fc, FacCache& tf,
+                                                 EpiPre& pre, EpiConst& C, double& sLsrc) {
+    load_task_caches(T, G, fc, tf, pre);
+    if (threadIdx.x == 0) task_consts(T, fc, tf, pre, C, sLsrc);
 }
 
 // Target-side inputs of the epilogue of point i, loaded ahead of the kernel sum so that their

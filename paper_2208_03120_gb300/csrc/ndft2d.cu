@@ -315,11 +315,12 @@ __device__ __forceinline__ void nd_run(NDSh& S, float* dyn, const Globals& G,
     const int M = G.M;
     const float inv_n = 1.f / (float)G.n_grid;
     if (r == 0 && tid == 0) task_resets(T, G, 0);
+    // factor caches now; the FP64 epilogue constants later, by a thread idle in phase 2
     if constexpr (MSG) {
         if (warp == 0) fill_factors_warp(fc, G.fac, T.sf0, T.snf, lane);
         __syncthreads();
     } else {
-        load_task_consts(T, G, fc, tf, S.sP, S.sC, S.sLsrc);   // constants visible after the next barrier
+        load_task_caches(T, G, fc, tf, S.sP);
     }
     const bool fast = MSG || T.hgrid != nullptr;
     EpiPartial ep;
@@ -432,6 +433,8 @@ __device__ __forceinline__ void nd_run(NDSh& S, float* dyn, const Globals& G,
             const float4 b = nd_combine(a, p, M, Dp, Dm);
             if (q < CS) nd_st_cluster4(nd_mapa(&S.B4[p], q), b);
         }
+        if constexpr (!MSG)
+            if (tid == nt - 1) task_consts(T, fc, tf, S.sP, S.sC, S.sLsrc);   // read after the barrier
         cluster.sync();      // every pair's entries of B^T are in every rank's shared memory
         if (tid < ND_KF * ND_KF) {
             const int p = tid;
@@ -477,6 +480,8 @@ __device__ __forceinline__ void nd_run(NDSh& S, float* dyn, const Globals& G,
         }
     } else {
         // node step without a kernel product; the cluster barrier orders the reset above
+        if constexpr (!MSG)
+            if (tid == 0) task_consts(T, fc, tf, S.sP, S.sC, S.sLsrc);
         cluster.sync();
         if constexpr (!MSG) {
             const EpiConst C = S.sC;
