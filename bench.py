@@ -1,8 +1,9 @@
 """Benchmark: NFFT-accelerated tree Sinkhorn (Algorithm 2) on the 10-node d=2 path workload.
 
 One step = one complete solve to marginal violation <= 1e-6 through the C ABI
-(normalisation, binning, kernel Fourier coefficients, the Sinkhorn sweeps with NFFT
-fast summation, stop tests and outputs), inputs already resident in device memory.
+(normalisation, binning, kernel Fourier coefficients, the Sinkhorn sweeps with the fast
+summation -- on this workload its trigonometric sums evaluated exactly in one thread-block
+cluster per product -- stop tests and outputs), inputs already resident in device memory.
 The metric is Sinkhorn iterations per second at that violation; the dense direct
 path is measured beside it on the same workload, and the per-step latency is
 reported as p50 / p99.
@@ -190,6 +191,39 @@ def hbm_roofline(prob, n_grid, dom, kms, kls, nsolve, iters, peaks, traffic=None
             "share": {k: round(v / sum(kms.values()), 4) for k, v in kms.items() if v > 0}}
 
 
+# FP32 fused multiply-add peak of the GPU: 152 SMs x 128 FP32 lanes x 2 flops x the maximum SM clock
+# (2070 MHz); the packed fma.rn.f32x2 form issues two lanes' worth per instruction but runs on the
+# same 128 lanes per SM.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def flops_per_exact_product(prob):
+    """Multiply-add flops of one product on the exact-sum path (d = 2, 33 trigonometric values per
+    coordinate): the adjoint contraction A = sum_j e(y_j) (v_j e(x_j))^T (33 x 33 per source) and
+    the targets' bilinear forms e(y_i)^T B e(x_i) (33 x 33 per target), 2 flops per multiply-add."""
+    N = prob.n[0]
+    return 2.0 * 33 * 33 * (N + N)
+
+
+def alu_roofline(prob, n_grid, dom, kms, kls, nsolve, iters, peaks, traffic=None):
+    """FP32 roofline of the persistent kernel on the exact-sum path: algorithmic flops per launch
+    (flops_per_exact_product x products per launch) over the class's average launch duration,
+    against FP32_PEAK_TFLOPS.  The HBM byte model of the same launch is kept beside it."""
+    hb = hbm_roofline(prob, n_grid, dom, kms, kls, nsolve, iters, peaks, traffic=traffic)
+    prods = hb["products_per_launch"]
+    avg_s = hb["avg_launch_us"] / 1e6
+    flops = flops_per_exact_product(prob) * prods
+    achieved = flops / avg_s / 1e12
+    return {"bound": "alu", "kernel": dom + " (k_wave_nd, exact trigonometric sums)", "achieved": achieved,
+            "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
+            "avg_launch_us": hb["avg_launch_us"], "alg_flops_per_launch": flops,
+            "alg_flops_per_product": flops_per_exact_product(prob), "products_per_launch": prods,
+            "hbm_model": {"achieved_gbs": hb["achieved"], "peak_gbs": hb["peak"], "frac": hb["frac"],
+                          "alg_bytes_per_launch": hb["alg_bytes_per_launch"]},
+            "share": hb["share"]}
+
+
 def products_per_solve(prob, iters, check_every):
     """Kernel products executed by one solve: the initial backward pass, 2(K-1) per sweep and
     the K-1 forward products of each check pass."""
@@ -201,7 +235,7 @@ def kernel_source_hash(cls):
     # the persistent kernel's traffic also depends on the host's schedule (solver.cu)
     files = {"spread": ["nfft.cu", "common.cuh", "epilogue.cuh"], "gather": ["nfft.cu", "common.cuh", "epilogue.cuh"],
              "fused": ["nfft.cu", "common.cuh", "epilogue.cuh", "window.cuh"],
-             "wave": ["nfft.cu", "common.cuh", "epilogue.cuh", "window.cuh", "solver.cu", "kernels.h"],
+             "wave": ["ndft2d.cu", "wave.cuh", "common.cuh", "epilogue.cuh", "solver.cu", "kernels.h"],
              "fftconv": ["nfft.cu", "fft_smem.cuh"], "dense": ["dense.cu", "common.cuh", "epilogue.cuh"],
              "local": ["local.cu", "kernels.h", "solver.cu"]}.get(cls, [])
     h = hashlib.sha256()
@@ -597,8 +631,13 @@ def main():
     nsolve = max(1, min(args.steps, 3))
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    roofline = hbm_roofline(prob, last.n_grid, dom, kms, kls, nsolve, o2.iters, peaks,
-                            traffic=load_traffic(dom, args.workload) if not args.n else None)
+    # d = 2 on grids up to 64 with sets of up to 32768 points: the fused products evaluate the
+    # trigonometric sums exactly (FP32 contractions), so their roofline is the FP32 one
+    exact = (path == M.MOT_PATH_NFFT and prob.d == 2 and last.n_grid <= 64 and max(prob.n) <= 32768
+             and dom == "wave")
+    rf = alu_roofline if exact else hbm_roofline
+    roofline = rf(prob, last.n_grid, dom, kms, kls, nsolve, o2.iters, peaks,
+                  traffic=load_traffic(dom, args.workload) if not args.n else None)
     if prob.topology == W.CIRCLE and prob.d == 1 and path == M.MOT_PATH_NFFT:
         per_launch = circle1d_launch_bytes(prob, last.n_grid).get(dom, 0.0)
         avg_s = kms[dom] / 1e3 / kls[dom]
@@ -790,6 +829,9 @@ def main():
                    "iters_per_solve": last.iters, "parallelism": f"replicas{world}",
                    "root": "centre of the path (library choice, MOT_ROOT_CENTRE)",
                    "schedule": "wavefront across sweeps (library default, options.wavefront)",
+                   "fast_summation": ("exact trigonometric sums, Eqs. ndft*/ndft as FP32 contractions "
+                                      "(library default for d = 2 on grids up to 64, options.ndft)"
+                                      if exact else "NFFT through the oversampled grid"),
                    "l2": "flushed between steps (256 MB write)"},
         "latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "dense": dense,
