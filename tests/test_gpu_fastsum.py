@@ -112,3 +112,41 @@ def test_fastsum_grid_override_and_invariance(M):
                           (3.0 * xs + 5.0).astype(np.float32).astype(np.float64),
                           alpha.astype(np.float32).astype(np.float64), 9 * 0.05)
     assert inf_rel_err(b_s, ref_s) <= TOL
+
+
+@pytest.mark.parametrize("n_src,n_tgt,eta", [(2000, 1537, 0.01), (10363, 9001, 0.02), (37, 5, 0.05), (1, 700, 0.03)])
+def test_exact_sums_match_oracle_ndft(M, n_src, n_tgt, eta):
+    """d = 2 on the 64^2 grid (M = 16) evaluates the trigonometric sums of the fast summation
+    exactly (Eq. ndft* for ghat, Eq. ndft for the result): the product equals the oracle's
+    Algorithm 4 with direct NDFTs (``fastsum_ndft``, pinned to the direct sum in
+    ``tests/test_oracle_kernel.py``) on the same normalised points up to FP32 rounding -- no
+    window error.  Sizes: several 640-point chunks per CTA with a ragged tail (10363 sources over
+    16 CTAs), a handful of points per CTA, and a single source (15 CTAs without sources)."""
+    rng = np.random.default_rng(300 + n_src)
+    xs = W.uniform_ball(rng, n_src, 2, 0.24).astype(np.float32)
+    xt = W.uniform_ball(rng, n_tgt, 2, 0.24).astype(np.float32)
+    alpha = rng.uniform(0.0, 1.0, size=n_src)
+    beta, s = _run(M, xs, xt, alpha, eta, n_grid=64)
+    # the library maps x to x / s on the unit torus (period 2 tau = 1) with eta / s^2; the kernel
+    # of Eq. (Ker-reg) depends only on differences, so the centre of that map drops out
+    ref = OK.fastsum_ndft(xt.astype(np.float64) / s, xs.astype(np.float64) / s,
+                          alpha.astype(np.float32).astype(np.float64), eta / (s * s), 0.5, 1.0 / 16.0, 3, 16)
+    assert np.max(np.abs(beta - ref)) <= 2e-6 * np.max(np.abs(ref))
+    # the grid path on the same input carries the window error on top
+    b_grid, _ = _run(M, xs, xt, alpha, eta, n_grid=64, ndft=-1)
+    ref_d = OK.direct_sum(xt.astype(np.float64), xs.astype(np.float64), alpha.astype(np.float32).astype(np.float64), eta)
+    assert inf_rel_err(b_grid, ref_d) <= TOL and inf_rel_err(beta, ref_d) <= TOL
+
+
+def test_exact_sums_multiple_rhs(M):
+    """Several right-hand sides: one cluster per right-hand side, each equal to its own product."""
+    rng = np.random.default_rng(12)
+    xs = W.uniform_ball(rng, 3000, 2, 0.2).astype(np.float32)
+    xt = W.uniform_ball(rng, 2500, 2, 0.2).astype(np.float32)
+    A = rng.uniform(size=(4, 3000))
+    beta, _ = _run(M, xs, xt, A, 0.02)
+    for r in range(4):
+        b1, _ = _run(M, xs, xt, A[r], 0.02)
+        np.testing.assert_allclose(beta[r], b1[0] if b1.ndim > 1 else b1, rtol=0, atol=1e-6 * np.max(np.abs(b1)))
+        ref = OK.direct_sum(xt.astype(np.float64), xs.astype(np.float64), A[r].astype(np.float32).astype(np.float64), 0.02)
+        assert inf_rel_err(beta[r], ref) <= TOL

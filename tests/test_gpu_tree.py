@@ -199,6 +199,30 @@ def test_centre_root_fixed_sweeps(M, path):
     assert abs(out.S_last - res.S[-1]) <= REL * abs(res.S[-1])
 
 
+def test_grid_path_fixed_sweeps_matches_oracle_and_exact_path(M):
+    """The oversampled-grid product (options.ndft = -1) still runs Algorithm 2 on d = 2 trees: 40
+    sweeps rooted at the centre equal the oracle's 40, and the exact-sum product's 40 within the
+    window error of the grid path."""
+    rng = np.random.default_rng(4243)
+    prob = W.random_problem(rng, W.TREE, 7, 2, 900, 0.03, shape="tree-random")
+    centre = _centre(7, prob.edges)
+    prob.root = -1
+    out_g, u_g = gpu_solve(M, prob, max_iter=40, tol_viol=-1.0, check_every=10, ndft=-1)
+    out_e, u_e = gpu_solve(M, prob, max_iter=40, tol_viol=-1.0, check_every=10, ndft=1)
+    assert out_g.iters == 40 and out_e.iters == 40
+    prob.root = centre
+    u_or, res = oracle_solve(prob, 40)
+    rep_g, rep_e, rep_o = exact_report(prob, u_g), exact_report(prob, u_e), exact_report(prob, u_or)
+    assert_parity(prob, u_g, u_or, rep_g, rep_o)
+    assert_parity(prob, u_e, u_or, rep_e, rep_o)
+    assert abs(out_g.S_last - res.S[-1]) <= REL * abs(res.S[-1])
+    assert abs(out_e.S_last - res.S[-1]) <= REL * abs(res.S[-1])
+    fe, fg = OS.gauge_fix(u_e, prob.mu), OS.gauge_fix(u_g, prob.mu)
+    scale = max(float(np.max(np.abs(v))) for v in fe) + prob.eta
+    for va, vb in zip(fe, fg):
+        assert np.max(np.abs(va - vb)) <= 1e-4 * scale
+
+
 @pytest.mark.parametrize("path", [0, 1])
 def test_barycenter_free_centre(M, path):
     """Fixed-support barycenter (Section 6.2): star with a free centre (phi = 1) and four
@@ -285,18 +309,20 @@ def test_wavefront_equals_sweep_by_sweep(M, shape, check_every, max_iter, wave):
         assert a.launches < b.launches
 
 
+@pytest.mark.parametrize("ndft", [1, -1])
 @pytest.mark.parametrize("nclusters", [1, 3, 40])
-def test_persistent_wavefront_any_cluster_count(M, nclusters):
+def test_persistent_wavefront_any_cluster_count(M, nclusters, ndft):
     """The persistent wavefront kernel claims products in a topological order and waits only for
     products claimed earlier, so its result does not depend on how many clusters it runs: one (the
     products one after another), fewer than fit, and more than fit at once (later clusters start
-    when earlier ones leave).  Each run equals the sweep-by-sweep order of Algorithm 2."""
+    when earlier ones leave).  Each run equals the sweep-by-sweep order of Algorithm 2.  Both
+    products: the exact trigonometric sums (ndft = 1) and the oversampled grid (ndft = -1)."""
     prob = W.path10_d2(n=2000)
     prob.root = -1
-    ref, ur = gpu_solve(M, prob, max_iter=30, tol_viol=-1.0, check_every=10, wavefront=-1)
+    ref, ur = gpu_solve(M, prob, max_iter=30, tol_viol=-1.0, check_every=10, wavefront=-1, ndft=ndft)
     M.hook_wave_clusters(nclusters)
     try:
-        out, u = gpu_solve(M, prob, max_iter=30, tol_viol=-1.0, check_every=10, wavefront=1)
+        out, u = gpu_solve(M, prob, max_iter=30, tol_viol=-1.0, check_every=10, wavefront=1, ndft=ndft)
     finally:
         M.hook_wave_clusters(0)
     assert out.status == 0 and out.iters == 30
