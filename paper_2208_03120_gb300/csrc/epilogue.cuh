@@ -50,6 +50,7 @@ struct EpiConst {
     double lsphi;      // log-scale of the scalings written (EPI_PHI / EPI_ROOT)
     double E;          // exp(total log-scale) of P_i = raw_i T_i e^{L} (EPI_MARG / EPI_ROOT)
     double invEs;      // 1 / max(E, 1): |P_i - mu_i| is summed in FP32 scaled by it
+    double Es;         // max(E, 1)
     double ls_phi_k;   // log-scale of the node's current scaling (EPI_MARG)
     float inv_mx_old;  // 1 / mx of the previous root scaling (EPI_ROOT)
 };
@@ -123,7 +124,8 @@ __device__ __forceinline__ void epi_prepare(const Task& T, const FacCache& tf, d
         C.E = exp(Lold + (T.mode == EPI_ROOT ? tf.L : Lsrc));
         C.inv_mx_old = 1.f / mx_of(T.phi_sc, 1);
     }
-    C.invEs = 1.0 / fmax(C.E, 1.0);
+    C.Es = fmax(C.E, 1.0);
+    C.invEs = 1.0 / C.Es;
 }
 
 // One warp fills a factor cache: lanes stride over the factors, reading each factor and its
@@ -194,7 +196,8 @@ __device__ __forceinline__ void task_consts(const Task& T, const FacCache& fc, c
             C.E = exp(pre.Lold + (T.mode == EPI_ROOT ? tf.L : Lsrc));
             C.inv_mx_old = pre.inv_mx_old;
         }
-        C.invEs = 1.0 / fmax(C.E, 1.0);
+        C.Es = fmax(C.E, 1.0);
+        C.invEs = 1.0 / C.Es;
     }
 }
 
@@ -385,30 +388,31 @@ __device__ __forceinline__ void epi_block_finish(const Task& T, const Globals& G
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         if (lane == 0) {
-            // FP64 only here: the block's sums combined with their scales
-            const double l = (double)v[2] + C.lsphi * (double)v[3];
-            const double m = C.E * (double)v[4];
-            const double vi = (double)v[5] / C.invEs;
-            const double pl = C.E * (double)v[6] + C.ls_phi_k * m;
+            // FP64 only here, and only what the mode produces: the block's sums with their scales
+            // (products only: this part's FP64 division is slow)
             if (has_out) {
                 T.out_sc->ls = Lsrc;
                 atomic_max_pos(&T.out_sc->mx_bits, v[0]);
                 if (c) atomicAdd(&T.out_sc->clamped, c);
             }
             if (mode == EPI_MARG && T.acc_node) {
-                atomicAdd(T.acc_node + 0, vi);
-                atomicAdd(T.acc_node + 1, pl);
+                const double m = C.E * (double)v[4];
+                atomicAdd(T.acc_node + 0, (double)v[5] * C.Es);
+                atomicAdd(T.acc_node + 1, C.E * (double)v[6] + C.ls_phi_k * m);
                 atomicAdd(T.acc_node + 2, m);
             }
             if (has_phi) {
-                T.phi_sc->ls = phi_logscale(T, tf, Lsrc);
+                T.phi_sc->ls = C.lsphi;
                 atomic_max_pos(&T.phi_sc->mx_bits, v[1]);
                 IterAcc* nxt = G.acc + ((iter + 1) % G.R);
-                if (d_log && l != 0.0) atomicAdd(&nxt->logphi, l);
+                if (d_log) {
+                    const double l = (double)v[2] + C.lsphi * (double)v[3];
+                    if (l != 0.0) atomicAdd(&nxt->logphi, l);
+                }
                 if (mode == EPI_ROOT || mode == EPI_CROOT) {
                     IterAcc* cur = G.acc + (iter % G.R);
-                    atomicAdd(&cur->mass, m);
-                    atomicAdd(&cur->rootviol, vi);
+                    atomicAdd(&cur->mass, C.E * (double)v[4]);
+                    atomicAdd(&cur->rootviol, (double)v[5] * C.Es);
                 }
             }
         }
