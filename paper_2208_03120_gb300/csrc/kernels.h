@@ -120,6 +120,23 @@ cudaError_t launch_make_D(int d, int M, int n, double eta_n, double tau, double 
                           double* scratch_a, double* scratch_b, float* D, cudaStream_t st, bool deconv = true);
 size_t make_D_scratch_doubles(int d, int M);
 size_t D_floats(int d, int M);
+// Per-set arguments of the batched output / cold-start launches (one launch for all sets).
+struct OutSet {
+    const float* phi;
+    const VecScale* sc;
+    const int* perm;
+    int n;
+    double* u;                   // output (nullptr: skip the set)
+};
+struct OutBatch {
+    int nsets;
+    double eta;
+    OutSet s[64];
+};
+// u[k][perm[i]] = eta * (log(phi[k][i]) + ls_k) for every set k
+cudaError_t launch_output_batch(const OutBatch& B, cudaStream_t st);
+// phi[k] = 1 and a fresh scale record for every set k (u: unused)
+cudaError_t launch_init_cold_batch(const OutBatch& B, cudaStream_t st);
 // u_out[perm[i]] = eta * (log(phi[i]) + ls)
 cudaError_t launch_output(const float* phi, const VecScale* sc, const int* perm, int n, double eta,
                           double* u_out, cudaStream_t st);

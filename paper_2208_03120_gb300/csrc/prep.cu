@@ -1,5 +1,7 @@
 // Set-up kernels: normalisation onto the torus, binning, the spectral multiplier D
 // (Eqs. Ker-reg, kappa_tilde, fft; Algorithm 4, precomputation), scalings in / out.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace {
@@ -9,8 +11,16 @@ __device__ __forceinline__ unsigned int ord_enc(float f) {
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
+// Block-level reductions first (one global atomic per block and value: thousands of warps
+// hitting the same words serialise in L2).
 __global__ void k_box(const PrepSet* __restrict__ sets, int d, unsigned int* box) {
+    __shared__ unsigned int smn[3], smx[3];
     const PrepSet S = sets[blockIdx.y];
+    if (threadIdx.x < 3) {
+        smn[threadIdx.x] = 0xffffffffu;
+        smx[threadIdx.x] = 0u;
+    }
+    __syncthreads();
     unsigned int mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0u, 0u, 0u};
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S.n; j += gridDim.x * blockDim.x) {
         for (int t = 0; t < d; ++t) {
@@ -23,9 +33,14 @@ __global__ void k_box(const PrepSet* __restrict__ sets, int d, unsigned int* box
         unsigned int a = __reduce_min_sync(0xffffffffu, mn[t]);
         unsigned int b = __reduce_max_sync(0xffffffffu, mx[t]);
         if ((threadIdx.x & 31) == 0) {
-            atomicMin(&box[2 * t], a);
-            atomicMax(&box[2 * t + 1], b);
+            atomicMin(&smn[t], a);
+            atomicMax(&smx[t], b);
         }
+    }
+    __syncthreads();
+    if (threadIdx.x < d) {
+        atomicMin(&box[2 * threadIdx.x], smn[threadIdx.x]);
+        atomicMax(&box[2 * threadIdx.x + 1], smx[threadIdx.x]);
     }
 }
 
@@ -47,8 +62,13 @@ __global__ void k_radius(const PrepSet* __restrict__ sets, int d, unsigned int* 
         }
         r2 = fmaxf(r2, s);
     }
+    __shared__ unsigned int sr;
+    if (threadIdx.x == 0) sr = 0u;
+    __syncthreads();
     r2 = warp_max(r2);
-    if ((threadIdx.x & 31) == 0) atomicMax(&box[2 * d], __float_as_uint(r2));
+    if ((threadIdx.x & 31) == 0) atomicMax(&sr, __float_as_uint(r2));
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(&box[2 * d], sr);
 }
 
 __global__ void k_decode(const unsigned int* box, int d, float* out) {
@@ -294,6 +314,29 @@ __global__ void k_output(const float* __restrict__ phi, const VecScale* sc, cons
         u_out[perm[i]] = eta * (log((double)phi[i]) + ls);
 }
 
+// Every set of a solve in one launch (blockIdx.y = set).
+__global__ void k_output_batch(OutBatch B) {
+    const OutSet S = B.s[blockIdx.y];
+    if (S.u == nullptr) return;
+    const double ls = S.sc->ls;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x)
+        S.u[S.perm[i]] = B.eta * (log((double)S.phi[i]) + ls);
+}
+
+__global__ void k_init_cold_batch(OutBatch B) {
+    const OutSet S = B.s[blockIdx.y];
+    float* phi = const_cast<float*>(S.phi);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x) phi[i] = 1.f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        VecScale* sc = const_cast<VecScale*>(S.sc);
+        sc->ls = 0.0;
+        sc->mx_bits = __float_as_uint(1.f);
+        sc->clamped = 0u;
+        sc->ls_prev = 0.0;
+        sc->mx_prev_bits = __float_as_uint(1.f);
+    }
+}
+
 __global__ void k_init_cold(float* phi, VecScale* sc, int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) phi[i] = 1.f;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -355,8 +398,8 @@ cudaError_t launch_bounds(const PrepSet* sets, int nsets, int d, float* box_raw,
     init[2 * d] = 0u;
     cudaError_t e = cudaMemcpyAsync(box_raw, init, sizeof(unsigned int) * (2 * d + 1), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    k_box<<<dim3(64, nsets), 256, 0, st>>>(sets, d, (unsigned int*)box_raw);
-    k_radius<<<dim3(64, nsets), 256, 0, st>>>(sets, d, (unsigned int*)box_raw);
+    k_box<<<dim3(16, nsets), 256, 0, st>>>(sets, d, (unsigned int*)box_raw);
+    k_radius<<<dim3(16, nsets), 256, 0, st>>>(sets, d, (unsigned int*)box_raw);
     k_decode<<<1, 32, 0, st>>>((const unsigned int*)box_raw, d, out);
     return cudaGetLastError();
 }
@@ -430,6 +473,22 @@ cudaError_t launch_make_D(int d, int M, int n, double eta_n, double tau, double 
         out = tmp;
     }
     k_make_D<<<blocks_for((long long)D_floats(d, M)), 256, sizeof(double) * (M + 1), st>>>(in, D, d, M, n, deconv ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_output_batch(const OutBatch& B, cudaStream_t st) {
+    int nmax = 0;
+    for (int k = 0; k < B.nsets; ++k) nmax = std::max(nmax, B.s[k].n);
+    if (B.nsets <= 0 || nmax <= 0) return cudaSuccess;
+    k_output_batch<<<dim3(std::min((nmax + 255) / 256, 64), B.nsets), 256, 0, st>>>(B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_cold_batch(const OutBatch& B, cudaStream_t st) {
+    int nmax = 0;
+    for (int k = 0; k < B.nsets; ++k) nmax = std::max(nmax, B.s[k].n);
+    if (B.nsets <= 0 || nmax <= 0) return cudaSuccess;
+    k_init_cold_batch<<<dim3(std::min((nmax + 255) / 256, 64), B.nsets), 256, 0, st>>>(B);
     return cudaGetLastError();
 }
 

@@ -2154,11 +2154,22 @@ struct TreeOps : PlanOps {
     int init(const double* const* u_warm, cudaStream_t st, Timer& tm, long long& nl) override {
         int minus1 = -1;
         CK(cudaMemcpyAsync(T.iter, &minus1, sizeof(int), cudaMemcpyHostToDevice, st));
+        OutBatch cold;                                             // every cold start in one launch
+        cold.nsets = 0;
+        cold.eta = T.eta;
         for (int k = 0; k < T.K; ++k) {
             const double* uw = (u_warm && !T.free_[k]) ? u_warm[T.order[k]] : nullptr;
+            if (uw == nullptr && T.K <= 64) {
+                cold.s[cold.nsets++] = OutSet{T.phi[k], T.phi_sc(k), T.sets[k].perm, T.n[k], nullptr};
+                continue;
+            }
             CK(launch_init_phi(T.phi[k], T.phi_sc(k), T.sets[k].perm, T.sets[k].mu_d, T.n[k], uw, T.eta,
                                &T.acc[0].logphi, T.box_scratch, st));
             nl += uw ? 2 : 1;
+        }
+        if (cold.nsets > 0) {
+            CK(launch_init_cold_batch(cold, st));
+            nl += 1;
         }
         T.par = 0;                                                 // the first beta copy
         for (auto& L : T.bwd) RET(run_level(T, L, st, tm, nl));   // Algorithm 2, steps 3-5
@@ -2181,11 +2192,13 @@ struct TreeOps : PlanOps {
     bool constrained(int k) const override { return !T.free_[k]; }
     double eta() const override { return T.eta; }
     int output(double* const* u, double* const*, cudaStream_t st, long long& nl) override {
-        for (int k = 0; k < T.K && u; ++k) {
-            if (!u[T.order[k]]) continue;
-            CK(launch_output(T.phi[k], T.phi_sc(k), T.sets[k].perm, T.n[k], T.eta, u[T.order[k]], st));
-            nl += 1;
-        }
+        if (!u) return MOT_OK;
+        OutBatch B;                                                // every set's potentials in one launch
+        B.nsets = T.K;
+        B.eta = T.eta;
+        for (int k = 0; k < T.K; ++k) B.s[k] = OutSet{T.phi[k], T.phi_sc(k), T.sets[k].perm, T.n[k], u[T.order[k]]};
+        CK(launch_output_batch(B, st));
+        nl += 1;
         return MOT_OK;
     }
     void geometry(mot_result* r) const override {
@@ -2204,11 +2217,22 @@ struct CircleOps : PlanOps {
     int init(const double* const* u_warm, cudaStream_t st, Timer& tm, long long& nl) override {
         int minus1 = -1;
         CK(cudaMemcpyAsync(C.iter, &minus1, sizeof(int), cudaMemcpyHostToDevice, st));
+        OutBatch cold;                                             // every cold start in one launch
+        cold.nsets = 0;
+        cold.eta = C.eta;
         for (int k = 0; k < C.K; ++k) {
             const double* uw = u_warm ? u_warm[k] : nullptr;
+            if (uw == nullptr) {
+                cold.s[cold.nsets++] = OutSet{C.phi[k], C.phi_sc(k), C.sets[k].perm, C.n[k], nullptr};
+                continue;
+            }
             CK(launch_init_phi(C.phi[k], C.phi_sc(k), C.sets[k].perm, C.sets[k].mu_d, C.n[k], uw, C.eta,
                                &C.acc[0].logphi, C.box_scratch, st));
-            nl += uw ? 2 : 1;
+            nl += 2;
+        }
+        if (cold.nsets > 0) {
+            CK(launch_init_cold_batch(cold, st));
+            nl += 1;
         }
         cudaEvent_t e = nullptr;                                   // Algorithm 3, steps 3-5
         RET(tm.begin(MOT_K_NODE, &e));
@@ -2227,9 +2251,12 @@ struct CircleOps : PlanOps {
     bool constrained(int) const override { return true; }
     double eta() const override { return C.eta; }
     int output(double* const* u, double* const* pair, cudaStream_t st, long long& nl) override {
-        for (int k = 0; k < C.K && u; ++k) {
-            if (!u[k]) continue;
-            CK(launch_output(C.phi[k], C.phi_sc(k), C.sets[k].perm, C.n[k], C.eta, u[k], st));
+        if (u) {
+            OutBatch B;                                            // every set's potentials in one launch
+            B.nsets = C.K;
+            B.eta = C.eta;
+            for (int k = 0; k < C.K; ++k) B.s[k] = OutSet{C.phi[k], C.phi_sc(k), C.sets[k].perm, C.n[k], u[k]};
+            CK(launch_output_batch(B, st));
             nl += 1;
         }
         // pair marginals Pi_{0,k} (Section 6.3): after a full sweep and the check pass, Gam_k and
