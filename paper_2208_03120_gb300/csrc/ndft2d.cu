@@ -22,8 +22,10 @@
 //      (row 32 and column 32 on the side), all lanes reading the same sources (broadcast reads of
 //      128 contiguous bytes), with packed FP32 FMAs (fma.rn.f32x2);
 //   2. the 20 slices are summed through shared memory; every target's e(u^y), e(u^x) is written
-//      ([value][target]); the cluster barrier publishes every rank's partial A; every CTA sums the
-//      16 partials (distributed shared memory, float4) and forms B^T;
+//      ([value][target]); every rank pushes the four entries (cc, ss, cs, sc) of each frequency
+//      pair to the pair's owner (rank p mod CS) as one 16-byte store into distributed shared
+//      memory; after the first cluster barrier each owner sums the CS partials, forms its pairs'
+//      entries of B^T and pushes them to every rank; after the second every CTA holds B^T;
 //   3. warp w takes 32 targets, its lanes a 4-target x 8-row tile of T = E_x B^T, then
 //      beta_i = sum_r T_ir e_r(u_i^y) (the 4 row groups summed by shuffles), and one thread per
 //      target runs the epilogue of the sweep step (epilogue.cuh).
@@ -50,7 +52,7 @@ namespace {
 #define ND_PAIRS_RANK 37    // frequency pairs per rank for clusters of 8 or more: ceil(17 * 17 / 8)
                             // (pair p belongs to rank p % CS)
 // dynamic shared memory: source records P [ND_CH][ND_R], Q [ND_CH][ND_R] (then the per-warp partial
-// A, [ND_WARPS][ND_NA]); target values E_y [ND_E][ND_CH], E_x [ND_E][ND_CH]
+// A, [ND_WARPS][ND_WSZ], within the bound below); target values E_y [ND_E][ND_CH], E_x [ND_E][ND_CH]
 #define ND_DYN_FLOATS (2 * ND_CH * ND_R > ND_WARPS * ND_NA ? 2 * ND_CH * ND_R : ND_WARPS * ND_NA)
 #define ND_DYN_SMEM (ND_DYN_FLOATS * 4)
 
