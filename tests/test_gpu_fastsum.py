@@ -150,3 +150,35 @@ def test_exact_sums_multiple_rhs(M):
         np.testing.assert_allclose(beta[r], b1[0] if b1.ndim > 1 else b1, rtol=0, atol=1e-6 * np.max(np.abs(b1)))
         ref = OK.direct_sum(xt.astype(np.float64), xs.astype(np.float64), A[r].astype(np.float32).astype(np.float64), 0.02)
         assert inf_rel_err(beta[r], ref) <= TOL
+
+
+@pytest.mark.parametrize("n_grid,M_", [(32, 8)])
+def test_exact_sums_smaller_grids(M, n_grid, M_):
+    """A grid of 32 (M = 8): the frequencies beyond M carry no weight, and the product still equals
+    the oracle's direct-NDFT fast summation with that M.  (The library weights the frequencies at
+    |k_t| = M by 1/2 on both sides where the oracle keeps -M once; for d = 2 the two differ by the
+    corner terms of size kappa_hat(M, M), which at M = 4 exceed the 2e-6 bar.)"""
+    rng = np.random.default_rng(500 + n_grid)
+    xs = W.uniform_ball(rng, 3001, 2, 0.24).astype(np.float32)
+    xt = W.uniform_ball(rng, 2222, 2, 0.24).astype(np.float32)
+    alpha = rng.uniform(0.0, 1.0, size=3001)
+    eta = 0.08
+    beta, s = _run(M, xs, xt, alpha, eta, n_grid=n_grid)
+    ref = OK.fastsum_ndft(xt.astype(np.float64) / s, xs.astype(np.float64) / s,
+                          alpha.astype(np.float32).astype(np.float64), eta / (s * s), 0.5, 1.0 / 16.0, 3, M_)
+    assert np.max(np.abs(beta - ref)) <= 2e-6 * np.max(np.abs(ref))
+
+
+def test_exact_sums_largest_sets_sampled(M):
+    """The largest sets of the exact-sum kernel (32768 points: 2048 per CTA, four chunks of up to
+    640), checked against the oracle's direct-NDFT fast summation on 2000 sampled targets."""
+    rng = np.random.default_rng(77)
+    n = 32768
+    xs = W.uniform_ball(rng, n, 2, 0.24).astype(np.float32)
+    xt = W.uniform_ball(rng, n, 2, 0.24).astype(np.float32)
+    alpha = rng.uniform(0.0, 1.0, size=n)
+    beta, s = _run(M, xs, xt, alpha, 0.02, n_grid=64)
+    idx = np.random.default_rng(78).choice(n, 2000, replace=False)
+    ref = OK.fastsum_ndft(xt[idx].astype(np.float64) / s, xs.astype(np.float64) / s,
+                          alpha.astype(np.float32).astype(np.float64), 0.02 / (s * s), 0.5, 1.0 / 16.0, 3, 16)
+    assert np.max(np.abs(beta[idx] - ref)) <= 2e-6 * np.max(np.abs(ref))
