@@ -54,7 +54,8 @@ struct WaveArgs {
     const Task* tasks;
     int ntask;
     const int* deps;             // dependency lists (Task.dep0 / Task.ndep)
-    int* flags;                  // [ntask] completion flags
+    int* flags;                  // [ntask] completion flags: k_wave2d stores the launch's epoch; k_wave_nd
+                                 // counts the CTAs that completed the product (zeroed by the prologue)
     WaveCtl* ctl;
     int* err;                    // bit 2 (value 4): a wait ran out
     unsigned long long wait_ns;  // limit of every wait
@@ -82,7 +83,8 @@ cudaError_t launch_c1_batch(const float* X, const VecScale* sX, const float* phi
 // One-block iteration prologue (resets, iteration counter, accumulators; with ctl: the persistent
 // kernel's claim counter and abort word reset and its epoch advanced).
 cudaError_t launch_prologue(VecScale* const* list, int nlist, int save_prev, int bump, double* zero_d, int zero_n,
-                            const Globals& G, cudaStream_t st, WaveCtl* ctl = nullptr);
+                            const Globals& G, cudaStream_t st, WaveCtl* ctl = nullptr, int* zero_i = nullptr,
+                            int zero_in = 0);
 
 // ---- dense direct summation (dense.cu) ----------------------------------------------
 cudaError_t launch_dense(int d, const Task* tasks, int ntask, int ntb, int nsplit, const Globals& G,

@@ -48,6 +48,7 @@ namespace {
 #define ND_NA (ND_R * ND_R)
 #define ND_CH 640           // sources / targets per chunk (32 targets per warp)
 #define ND_MAXPTS 32768     // largest point set per product (as the grid-based fused kernel)
+#define ND_MAXDEP 64        // dependency lists up to this length are prefetched into shared memory
 #define ND_WSZ (35 * 32)    // one warp's partial A: 32 tile slots + 2 side + 1 corner, x 32 lanes
 #define ND_PAIRS_RANK 37    // frequency pairs per rank for clusters of 8 or more: ceil(17 * 17 / 8)
                             // (pair p belongs to rank p % CS)
@@ -57,7 +58,10 @@ namespace {
 #define ND_DYN_SMEM (ND_DYN_FLOATS * 4)
 
 struct __align__(16) NDSh {
-    Task T;
+    Task Tb[2];                      // the product's task and, in the persistent kernel, the next one
+    Factor Fs[MOT_MAXFAC], Ft[MOT_MAXFAC];   // persistent kernel: the next task's factor structs
+    int dl[ND_MAXDEP];               // persistent kernel: the next task's dependency list
+    int claim[2];                    // persistent kernel: rank 0's claims, alternating buffers
     FacCache fc, tf;
     EpiConst sC;
     EpiPre sP;
@@ -134,7 +138,7 @@ __device__ __forceinline__ void nd_values(float u, float inv_n, float s, Put put
 }
 
 // Part of a product that reads only its own (static) task.  Visible after the caller's next barrier.
-__device__ __forceinline__ void nd_prep(NDSh& S, const Task* task) { load_task(S.T, task); }
+__device__ __forceinline__ void nd_prep(NDSh& S, const Task* task) { load_task(S.Tb[0], task); }
 
 // Frequency pair (ky', kx) = (p / 17, p % 17) of the cluster's A, a = its entries (cc, ss, cs, sc)
 // (A's rows index e(u^y), its columns e(u^x); S_0 = 0 has no entry): the half spectrum ghat for
@@ -244,27 +248,117 @@ __device__ __forceinline__ void nd_target_sums(const float* dyn, const float* BT
     if (rg == 0) *reinterpret_cast<float4*>(f + i0) = make_float4(s[0], s[1], s[2], s[3]);
 }
 
-// Records of the chunk's sources [c0, c0 + cnt): P[q] = e(u_j^y), Q[q] = v_j e(u_j^x) (ND_R floats
+// Source record of one point in row q of the chunk: P[q] = e(u^y), Q[q] = s e(u^x) (ND_R floats
 // each, stored as float4: rows of consecutive threads fall in distinct bank groups).
-__device__ __forceinline__ void nd_source_records(const Task& T, const FacCache& fc, float* dyn, int c0, int cnt,
-                                                  float inv_n) {
-    const int Ns = T.src.n;
-    float* P = dyn;
-    float* Q = dyn + ND_CH * ND_R;
-    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-        const int j = c0 + q;
-        const float ux = T.src.u[j], uy = T.src.u[Ns + j];
-        const float v = T.alpha ? T.alpha[j] : eval_prod(fc, j);
-        float e[ND_R];
-        e[33] = e[34] = e[35] = 0.f;
-        nd_values(uy, inv_n, 1.f, [&](int i, float val) { e[i] = val; });
-        float4* p = reinterpret_cast<float4*>(P + q * ND_R);
+__device__ __forceinline__ void nd_record_row(float* row, float u, float inv_n, float s) {
+    float e[ND_R];
+    e[33] = e[34] = e[35] = 0.f;
+    nd_values(u, inv_n, s, [&](int i, float val) { e[i] = val; });
+    float4* p = reinterpret_cast<float4*>(row);
 #pragma unroll
-        for (int m = 0; m < ND_R / 4; ++m) p[m] = make_float4(e[4 * m], e[4 * m + 1], e[4 * m + 2], e[4 * m + 3]);
-        nd_values(ux, inv_n, v, [&](int i, float val) { e[i] = val; });
-        float4* qq = reinterpret_cast<float4*>(Q + q * ND_R);
+    for (int m = 0; m < ND_R / 4; ++m) p[m] = make_float4(e[4 * m], e[4 * m + 1], e[4 * m + 2], e[4 * m + 3]);
+}
+
+// Product of nf factors F at point j, each mantissa times 1 / the maximum of its scale record
+// (the arithmetic of eval_prod on a factor cache), read by the calling thread itself.
+__device__ __forceinline__ float nd_factor_prod(const Factor* F, int nf, int j) {
+    float v = 1.f;
+    for (int f = 0; f < nf; ++f) {
+        const Factor g = F[f];
+        const float x = __ldg(g.mant + j) * (1.f / mx_of(g.sc, g.use_prev));
+        v = g.inv ? v / x : v * x;
+    }
+    return v;
+}
+
+// v_j of source j: the plain right-hand side or the product of the task's source factors Fs.
+__device__ __forceinline__ float nd_source_v(const Task& T, const Factor* Fs, int j) {
+    return T.alpha ? T.alpha[j] : nd_factor_prod(Fs, T.snf, j);
+}
+
+// The epilogue inputs of target i (epi_load) with the target factors' product formed from their
+// structs Ft, so that no factor cache is needed yet.
+__device__ __forceinline__ EpiIn nd_epi_load(const Task& T, const Factor* Ft, int i) {
+    EpiIn in;
+    in.t = 1.f;
+    in.muf = 0.f;
+    in.phi = 0.f;
+    in.mud = 0.0;
+    switch (T.mode) {
+    case EPI_PHI:
+        in.t = nd_factor_prod(Ft, T.tnf, i);
+        in.muf = T.mu_f[i];
+        break;
+    case EPI_ROOT:
+        in.t = nd_factor_prod(Ft, T.tnf, i);
+        in.phi = T.phi[i];
+        if (!T.free_node) {
+            in.muf = T.mu_f[i];
+            in.mud = T.mu_d[i];
+        }
+        break;
+    case EPI_CROOT:
+        in.phi = T.phi[i];
+        in.muf = T.mu_f[i];
+        in.mud = T.mu_d[i];
+        break;
+    case EPI_MARG:
+        in.t = nd_factor_prod(Ft, T.tnf, i);
+        in.phi = T.phi[i];
+        if (T.mu_d) in.mud = T.mu_d[i];
+        break;
+    default:
+        break;
+    }
+    return in;
+}
+
+// Asynchronous copies into shared memory (cp.async; each thread waits for its own copies).
+__device__ __forceinline__ void nd_cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void nd_cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void nd_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void nd_cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Warp 0 fills the factor caches of a task from its factor structs Fs / Ft (shared or global
+// memory): lanes 0-15 the source factors, lanes 16-31 the target factors, each half summing its
+// log-scales; lane 0 then reads the scale records of the epilogue.  No barrier.
+template <bool MSG>
+__device__ __forceinline__ void nd_fill_caches(const Task& T, const Globals& G, const Factor* Fs, const Factor* Ft,
+                                               FacCache& fc, FacCache& tf, EpiPre& pre, int lane) {
+    const bool src = lane < 16;
+    const int hl = lane & 15;
+    FacCache& c = src ? fc : tf;
+    const Factor* F = src ? Fs : Ft;
+    const int nf = src ? (T.alpha ? 0 : T.snf) : (MSG ? 0 : T.tnf);
+    double L = 0.0;
+    for (int t = hl; t < nf; t += 16) {
+        const Factor f = F[t];
+        const float mx = mx_of(f.sc, f.use_prev);
+        c.mant[t] = f.mant;
+        c.scale[t] = 1.f / mx;
+        c.inv[t] = f.inv;
+        const double Lt = ls_of(f.sc, f.use_prev) + (double)logf(mx);
+        L += f.inv ? -Lt : Lt;
+    }
 #pragma unroll
-        for (int m = 0; m < ND_R / 4; ++m) qq[m] = make_float4(e[4 * m], e[4 * m + 1], e[4 * m + 2], e[4 * m + 3]);
+    for (int o = 8; o > 0; o >>= 1) L += __shfl_xor_sync(0xffffffffu, L, o);
+    if (hl == 0 && (src || !MSG)) {
+        c.nf = nf;
+        c.L = L;
+    }
+    if constexpr (!MSG) {
+        if (lane == 0) {
+            pre.ls_phi_k = ls_of(T.phi_sc, 0);
+            pre.Lold = ls_of(T.phi_sc, 1) + (double)logf(mx_of(T.phi_sc, 1));
+            pre.inv_mx_old = 1.f / mx_of(T.phi_sc, 1);
+            pre.iter = (G.iter ? *G.iter : 0) - T.iter_off;
+        }
     }
 }
 
@@ -297,17 +391,23 @@ __device__ __forceinline__ void nd_source_sums(const float* dyn, int k0, int k1,
     }
 }
 
-// The product itself, after nd_prep and a block barrier, once the results of the products it reads
-// are complete.  Every CTA of the cluster calls it and passes its two cluster barriers whatever
-// the data (one on a task without a kernel product).  Every access to a peer's shared memory (the
-// partial A to the owners of its frequency pairs, the owners' entries of B^T to every rank) lies
-// between the product's two cluster barriers, so on return no peer touches this CTA's shared
-// memory for this product: the CTA may start its next product or exit.  The peers must be running
-// before the first access (a cluster barrier at the kernel's start).
-template <bool MSG>
-__device__ __forceinline__ void nd_run(NDSh& S, float* dyn, const Globals& G,
-                                       cooperative_groups::cluster_group& cluster) {
-    const Task& T = S.T;
+// The product itself.  Every CTA of the cluster calls it and passes its two cluster barriers
+// whatever the data (one on a task without a kernel product).  Every access to a peer's shared
+// memory (the partial A to the owners of its frequency pairs, the owners' entries of B^T to every
+// rank, the persistent kernel's claims) lies before the product's last cluster barrier, so on
+// return no peer touches this CTA's shared memory for this product: the CTA may start its next
+// product or exit.  The peers must be running before the first access (a cluster barrier at the
+// kernel's start).  T is in shared memory and visible to every thread; Fs / Ft are its source and
+// target factor structs.  The hooks wait for the products this one reads (Hooks::wait, followed by
+// a block barrier with Hooks::kBarrierAfterWait) and carry the persistent kernel's claims and
+// prefetches; with Hooks::kEarlyCoords the first chunk's source coordinates (constant inputs) are
+// fetched before the wait.  The source values v_j and the first targets' epilogue inputs are
+// formed by each thread from Fs / Ft; the factor caches (for the epilogue constants and later
+// chunks) are filled by the last warp beside its slice of the adjoint contraction.
+template <bool MSG, class Hooks>
+__device__ __forceinline__ void nd_run(NDSh& S, const Task& T, float* dyn, const Globals& G,
+                                       cooperative_groups::cluster_group& cluster, const Factor* Fs,
+                                       const Factor* Ft, Hooks& hk) {
     FacCache& fc = S.fc;
     FacCache& tf = S.tf;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -316,24 +416,37 @@ __device__ __forceinline__ void nd_run(NDSh& S, float* dyn, const Globals& G,
     const int r = (int)cluster.block_rank();
     const int M = G.M;
     const float inv_n = 1.f / (float)G.n_grid;
-    if (r == 0 && tid == 0) task_resets(T, G, 0);
-    // factor caches now; the FP64 epilogue constants later, by a thread idle in phase 2
-    if constexpr (MSG) {
-        if (warp == 0) fill_factors_warp(fc, G.fac, T.sf0, T.snf, lane);
-        __syncthreads();
-    } else {
-        load_task_caches(T, G, fc, tf, S.sP);
-    }
     const bool fast = MSG || T.hgrid != nullptr;
+    const int Ns = T.src.n;
+    const int s0 = (int)((long long)r * Ns / CS), s1 = (int)((long long)(r + 1) * Ns / CS);
+    const int cnt0 = fast ? min(ND_CH, s1 - s0) : 0;
+    float* P = dyn;
+    float* Q = dyn + ND_CH * ND_R;
+    // thread q < cnt0 owns row q of the first chunk's records; with Hooks::kEarlyCoords its
+    // source's coordinates (constant inputs) are fetched before the wait
+    float ux = 0.f, uy = 0.f;
+    if constexpr (Hooks::kEarlyCoords)
+        if (tid < cnt0) {
+            ux = T.src.u[s0 + tid];
+            uy = T.src.u[Ns + s0 + tid];
+        }
+    hk.wait(T, warp, lane);
+    if constexpr (Hooks::kBarrierAfterWait) __syncthreads();
+    // from here every thread may read what the products this one depends on wrote
+    if constexpr (!Hooks::kEarlyCoords)
+        if (tid < cnt0) {
+            ux = T.src.u[s0 + tid];
+            uy = T.src.u[Ns + s0 + tid];
+        }
+    if (r == 0 && tid == 0) task_resets(T, G, 0);
     EpiPartial ep;
     epi_zero(ep);
     const int Nt = T.tgt.n;
     const int ti0 = (int)((long long)r * Nt / CS), ti1 = (int)((long long)(r + 1) * Nt / CS);
-    // the epilogue inputs of this thread's first target and the two D entries of its frequency
-    // pair: fetched now, used after the source phase
+    // the epilogue inputs of this thread's first target: fetched now, used after the source phase
     EpiIn pin;
     if constexpr (!MSG)
-        if (fast && ti0 + tid < ti1) pin = epi_load(T, tf, ti0 + tid);
+        if (fast && ti0 + tid < ti1) pin = nd_epi_load(T, Ft, ti0 + tid);
 
     if (fast) {
         // D of the frequency pair p = r + CS (tid >> 4) that this thread combines in phase 2
@@ -347,8 +460,6 @@ __device__ __forceinline__ void nd_run(NDSh& S, float* dyn, const Globals& G,
             }
         }
         // ---- 1. partial A over this rank's sources ------------------------------------------
-        const int Ns = T.src.n;
-        const int s0 = (int)((long long)r * Ns / CS), s1 = (int)((long long)(r + 1) * Ns / CS);
         float2 acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -358,12 +469,28 @@ __device__ __forceinline__ void nd_run(NDSh& S, float* dyn, const Globals& G,
         float corner = 0.f;
         for (int c0 = s0; c0 < s1; c0 += ND_CH) {
             const int cnt = min(ND_CH, s1 - c0);
-            nd_source_records(T, fc, dyn, c0, cnt, inv_n);
+            if (tid < cnt) {
+                const int j = c0 + tid;
+                if (c0 != s0) {
+                    ux = T.src.u[j];
+                    uy = T.src.u[Ns + j];
+                }
+                const float v = nd_source_v(T, Fs, j);
+                nd_record_row(P + tid * ND_R, uy, inv_n, 1.f);
+                nd_record_row(Q + tid * ND_R, ux, inv_n, v);
+            }
+            if (c0 == s0) hk.before_first_barrier(tid, r, CS);
             __syncthreads();
+            // the factor caches (the epilogue's) by the last warp, whose slice is the shortest
+            if (c0 == s0 && warp == ND_WARPS - 1) nd_fill_caches<MSG>(T, G, Fs, Ft, fc, tf, S.sP, lane);
             const int per = (cnt + ND_WARPS - 1) / ND_WARPS;
             const int k0 = min(cnt, warp * per), k1 = min(cnt, k0 + per);
             nd_source_sums(dyn, k0, k1, acc, side, corner);
             __syncthreads();                              // the records are written again / reused
+        }
+        if (s0 >= s1) {
+            hk.before_first_barrier(tid, r, CS);
+            if (warp == ND_WARPS - 1) nd_fill_caches<MSG>(T, G, Fs, Ft, fc, tf, S.sP, lane);
         }
         // the slices of the 20 warps through shared memory: W[warp][slot][lane], slots 0..31 the
         // tile (slot 8 ip + 2 j + half), 32 / 33 side, 34 corner; summed by one thread per (slot,
@@ -416,6 +543,7 @@ __device__ __forceinline__ void nd_run(NDSh& S, float* dyn, const Globals& G,
         int tcnt = min(ND_CH, ti1 - tc0);
         if (tcnt > 0) nd_target_values(T, dyn, tc0, tcnt, inv_n);
         cluster.sync();      // every rank's partial A is with the owners of its pairs
+        hk.after_first_barrier(warp, lane);
         // ---- 2. the cluster's A, then B^T ----------------------------------------------------
         // rank r owns the frequency pairs p = r + CS m: each rank's partial (cc, ss, cs, sc) of
         // pair p went to R4[rank][m] of its owner before the barrier; thread (m, q) = (t >> 4,
@@ -457,6 +585,7 @@ __device__ __forceinline__ void nd_run(NDSh& S, float* dyn, const Globals& G,
         for (;;) {
             if (tcnt > 0) nd_target_sums(dyn, S.BT, S.f, tcnt);
             __syncthreads();
+            if (tc0 == ti0) hk.after_targets(warp, lane);
             if (tid < tcnt) {
                 const int i = tc0 + tid;
                 const float acc_i = S.f[tid];
@@ -482,19 +611,40 @@ __device__ __forceinline__ void nd_run(NDSh& S, float* dyn, const Globals& G,
         }
     } else {
         // node step without a kernel product; the cluster barrier orders the reset above
-        if constexpr (!MSG)
-            if (tid == 0) task_consts(T, fc, tf, S.sP, S.sC, S.sLsrc);
+        if (warp == 0) {
+            nd_fill_caches<MSG>(T, G, Fs, Ft, fc, tf, S.sP, lane);
+            __syncwarp();      // lane 16's target-cache sum is read by lane 0
+            if constexpr (!MSG)
+                if (tid == 0) task_consts(T, fc, tf, S.sP, S.sC, S.sLsrc);
+        }
+        hk.before_first_barrier(tid, r, CS);
         cluster.sync();
+        hk.after_first_barrier(warp, lane);
         if constexpr (!MSG) {
             const EpiConst C = S.sC;
             for (int i = ti0 + tid; i < ti1; i += nt) epilogue_point(T, tf, C, G.floor_, i, 1.f, ep);
         }
+        hk.after_targets(warp, lane);
     }
     if constexpr (MSG)
         epi_block_finish_msg(T, fc.L, ep);
     else
         epi_block_finish(T, G, tf, S.sLsrc, ep, S.sP.iter, S.sC);
 }
+
+// Hooks of the launch-per-level kernel: no claims or prefetches; the wait is for the previous
+// grid (programmatic dependent launch), by every thread, before anything that grid may write is read.
+struct NdLevelHooks {
+    static constexpr bool kEarlyCoords = false;
+    static constexpr bool kBarrierAfterWait = false;   // every thread waits itself
+    __device__ __forceinline__ void wait(const Task&, int, int) const {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    }
+    __device__ __forceinline__ void before_first_barrier(int, int, int) const {}
+    __device__ __forceinline__ void after_first_barrier(int, int) const {}
+    __device__ __forceinline__ void after_targets(int, int) const {}
+};
 
 // One product per cluster (blockIdx.y): the launch-per-level form.
 template <bool MSG>
@@ -504,48 +654,157 @@ __global__ void __launch_bounds__(ND_THREADS, 1) k_ndft2d(const Task* __restrict
     __shared__ NDSh S;
     extern __shared__ float4 nd_dyn[];
     nd_prep(S, tasks + blockIdx.y);
-    cluster.sync();      // every CTA of the cluster runs: its shared memory may be written
-    // Launched with programmatic stream serialisation: everything above uses only this launch's
-    // own (static) task; from here on the kernel reads what the previous launch wrote, so it waits
-    // for that grid to complete and flush, then lets the next launch be scheduled.
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    __syncthreads();
-    nd_run<MSG>(S, reinterpret_cast<float*>(nd_dyn), G, cluster);
+    // every CTA of the cluster runs (its shared memory may be written) and the task is visible.
+    // Launched with programmatic stream serialisation: up to here the kernel reads only its own
+    // (static) task; nd_run waits for the previous grid before it reads anything else.
+    cluster.sync();
+    NdLevelHooks hk;
+    nd_run<MSG>(S, S.Tb[0], reinterpret_cast<float*>(nd_dyn), G, cluster, G.fac + S.Tb[0].sf0,
+                G.fac + S.Tb[0].tf0, hk);
+}
+
+// The persistent kernel's task pipeline.  Product t runs task S.Tb[b]; rank 0 claims task t + 1
+// at the start of product t and pushes the claim into every rank's S.claim[b ^ 1] (a 4-byte store
+// into distributed shared memory, published by the product's first cluster barrier); after that
+// barrier the last warp of every CTA copies the claimed task into S.Tb[b ^ 1] with cp.async, and
+// after the target contraction its dependency list and factor structs (which read the task's
+// fields) into S.dl / S.Fs / S.Ft; the copies complete before the next product's first barrier.
+// Buffer reuse: S.claim[x] and S.Tb[x] are written again two products later, after the writer has
+// passed the intervening product's cluster barriers, which every reader reaches only after its
+// reads; S.dl / S.Fs / S.Ft are read at the start of a product, before its prefetch writes them.
+__device__ __forceinline__ void nd_fetch_task(Task& dst, const Task* src, int lane) {
+    static_assert(sizeof(Task) % 8 == 0, "Task is copied in 8-byte words");
+    const char* s = reinterpret_cast<const char*>(src);
+    char* d = reinterpret_cast<char*>(&dst);
+    for (int w = lane; w < (int)(sizeof(Task) / 8); w += 32) nd_cp_async8(d + 8 * w, s + 8 * w);
+    nd_cp_async_commit();
+}
+// Called by one whole warp once its task copy was issued: waits for it, then copies the lists.
+__device__ __forceinline__ void nd_fetch_lists(NDSh& S, const Task& T, const int* deps, const Factor* fac, int lane) {
+    static_assert(sizeof(Factor) % 8 == 0, "Factor is copied in 8-byte words");
+    nd_cp_async_wait_all();
+    __syncwarp();
+    if (T.ndep <= ND_MAXDEP)
+        for (int w = lane; w < T.ndep; w += 32) nd_cp_async4(&S.dl[w], deps + T.dep0 + w);
+    constexpr int fw = (int)(sizeof(Factor) / 8);
+    if (T.alpha == nullptr) {
+        const char* s = reinterpret_cast<const char*>(fac + T.sf0);
+        for (int w = lane; w < min(T.snf, MOT_MAXFAC) * fw; w += 32)
+            nd_cp_async8(reinterpret_cast<char*>(S.Fs) + 8 * w, s + 8 * w);
+    }
+    {
+        const char* s = reinterpret_cast<const char*>(fac + T.tf0);
+        for (int w = lane; w < min(T.tnf, MOT_MAXFAC) * fw; w += 32)
+            nd_cp_async8(reinterpret_cast<char*>(S.Ft) + 8 * w, s + 8 * w);
+    }
+    nd_cp_async_commit();
+}
+
+// A warp waits for the products task T reads: flags[product] counts the CTAs that completed it
+// (each adds 1 after a fence; the chunk prologue zeroes the counts), and lane q polls the counts of
+// dependencies q, q + 32, ... with acquire loads until all CS CTAs are in, each wait bounded by
+// A.wait_ns (on expiry: error bit 2 and the abort word).
+__device__ __forceinline__ void nd_wait_flags(const WaveArgs& A, const Task& T, const int* dl_smem, int CS, int lane) {
+    const int* dl = T.ndep <= ND_MAXDEP ? dl_smem : A.deps + T.dep0;
+    unsigned long long t0 = 0;
+    for (int q = lane; q < T.ndep; q += 32) {
+        const int* f = A.flags + dl[q];
+        while (ld_acquire_gpu(f) < CS) {
+            if (*reinterpret_cast<volatile int*>(&A.ctl->abort)) return;
+            const unsigned long long now = f2_globaltimer();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > A.wait_ns) {
+                atomicOr(A.err, 4);
+                atomicExch(&A.ctl->abort, 1);
+                return;
+            }
+            __nanosleep(32);
+        }
+    }
+}
+
+struct NdWaveHooks {
+    static constexpr bool kEarlyCoords = true;
+    static constexpr bool kBarrierAfterWait = true;    // warp 0 waits for the CTA
+    NDSh* S;
+    const WaveArgs* A;
+    const Factor* fac;
+    int nb;       // buffer of the next task
+    int CS;       // CTAs per cluster
+    int claim;    // rank 0, thread 0: the next claim (its atomic issued before the product)
+    __device__ __forceinline__ void wait(const Task& T, int warp, int lane) const {
+        if (warp == 0) nd_wait_flags(*A, T, S->dl, CS, lane);
+    }
+    __device__ __forceinline__ void before_first_barrier(int tid, int r, int CS) const {
+        if (r == 0 && tid == 0)
+            for (int q = 0; q < CS; ++q) {
+                const unsigned a = nd_mapa(&S->claim[nb], q);
+                asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(claim) : "memory");
+            }
+    }
+    __device__ __forceinline__ void after_first_barrier(int warp, int lane) const {
+        if (warp == ND_WARPS - 1) {
+            const int next = S->claim[nb];
+            if (next < A->ntask) nd_fetch_task(S->Tb[nb], A->tasks + next, lane);
+        }
+    }
+    __device__ __forceinline__ void after_targets(int warp, int lane) const {
+        if (warp == ND_WARPS - 1 && S->claim[nb] < A->ntask) nd_fetch_lists(*S, S->Tb[nb], A->deps, fac, lane);
+    }
+};
+
+// Rank 0's claim of the next task: the abort word and the counter are read together, so that
+// the thread stalls only where the result is used.
+__device__ __forceinline__ int nd_claim_issue(const WaveArgs& A) {
+    const int ab = *reinterpret_cast<volatile int*>(&A.ctl->abort);
+    const int c = atomicAdd(&A.ctl->next, 1);
+    return ab ? A.ntask : c;
 }
 
 // Persistent wavefront kernel (the schedule of k_wave2d in nfft.cu: claims in the host's
-// topological order, one claim ahead, completion flags with the launch's epoch, bounded waits)
-// running this file's product.
+// topological order, one claim ahead, bounded waits) running this file's product, with the task
+// pipeline above; a product's completion is counted per CTA (no cluster barrier at its end).
 __global__ void __launch_bounds__(ND_THREADS, 1) k_wave_nd(WaveArgs A, Globals G) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     __shared__ NDSh S;
-    __shared__ int s_claim;                         // rank 0's latest claim
     extern __shared__ float4 nd_dyn[];
     float* dyn = reinterpret_cast<float*>(nd_dyn);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int r = (int)cluster.block_rank();
-    const int epoch = *reinterpret_cast<volatile int*>(&A.ctl->epoch);   // advanced by the prologue
-    if (r == 0 && tid == 0) s_claim = wave_claim(A);
+    if (r == 0 && tid == 0) S.claim[0] = wave_claim(A);
     cluster.sync();
-    int i = *cluster.map_shared_rank(&s_claim, 0);
-    // a CTA may leave only once no peer reads its shared memory any more: every read of rank 0's
-    // claim is followed by a cluster barrier before the loop test can end it
-    cluster.sync();
-    while (i < A.ntask) {
-        nd_prep(S, A.tasks + i);
-        // the next claim, written before nd_run and published by its cluster barrier
-        if (r == 0 && tid == 0) s_claim = wave_claim(A);
-        if (tid < 32) wave_wait_warp(A, i, epoch, tid);
-        __syncthreads();
-        nd_run<false>(S, dyn, G, cluster);   // one instance for every mode (code stays resident)
-        const int next = *cluster.map_shared_rank(&s_claim, 0);
-        __threadfence();
-        cluster.sync();                      // product complete; every read of s_claim done
-        if (r == 0 && tid == 0) st_release_gpu(A.flags + i, epoch);
-        i = next;
+    int i = *cluster.map_shared_rank(&S.claim[0], 0);
+    if (i < A.ntask && warp == ND_WARPS - 1) {
+        nd_fetch_task(S.Tb[0], A.tasks + i, lane);
+        nd_fetch_lists(S, S.Tb[0], A.deps, G.fac, lane);
     }
+    // every read of rank 0's first claim is done before rank 0 writes S.claim again
+    cluster.sync();
+    int b = 0;
+    while (i < A.ntask) {
+        if (warp == ND_WARPS - 1) nd_cp_async_wait_all();
+        __syncthreads();                     // task i, its dependency list and factor structs are in S
+        NdWaveHooks hk;
+        hk.S = &S;
+        hk.A = &A;
+        hk.fac = G.fac;
+        hk.nb = b ^ 1;
+        hk.CS = (int)cluster.num_blocks();
+        hk.claim = (r == 0 && tid == 0) ? nd_claim_issue(A) : 0;
+        nd_run<false>(S, S.Tb[b], dyn, G, cluster, S.Fs, S.Ft, hk);   // ends with a block barrier
+        // this CTA's part of product i is complete (the block barrier above orders every thread's
+        // writes before the fence)
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(A.flags + i, 1);
+        }
+        i = S.claim[b ^ 1];
+        b ^= 1;
+    }
+    // no peer reads or writes this CTA's shared memory any more
+    cluster.sync();
 }
 
 int current_device_nd() {
@@ -633,7 +892,8 @@ cudaError_t launch_wave_nd(const WaveArgs& A, int nclusters, const Globals& G, c
     if (A.ntask <= 0) return cudaSuccess;
     const int cs = g_nd_cluster_size[current_device_nd()];
     if (cs <= 0 || nclusters <= 0) return cudaErrorInvalidConfiguration;
-    cudaLaunchAttribute attr[2];   // no programmatic serialisation: the kernel reads the prologue's
-    cudaLaunchConfig_t cfg = nd_config(cs, nclusters, 1, st, attr, false);   // epoch at its start
+    // no programmatic serialisation: the kernel claims and counts from the prologue's zeroes
+    cudaLaunchAttribute attr[2];
+    cudaLaunchConfig_t cfg = nd_config(cs, nclusters, 1, st, attr, false);
     return cudaLaunchKernelEx(&cfg, k_wave_nd, A, G);
 }

@@ -940,7 +940,7 @@ __global__ void __launch_bounds__(F2_THREADS, 1) k_wave2d(WaveArgs A, Globals G)
 // iteration produces.  Runs alone, so every later kernel of the iteration sees it.
 // ------------------------------------------------------------------------------------------
 __global__ void k_prologue(VecScale* const* __restrict__ list, int nlist, int save_prev, int bump,
-                           double* zero_d, int zero_n, Globals G, WaveCtl* ctl) {
+                           double* zero_d, int zero_n, Globals G, WaveCtl* ctl, int* zero_i, int zero_in) {
     // launched with programmatic stream serialisation: wait for the previous grid, then let the
     // next launch get scheduled (it waits for this one in the same way)
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -956,6 +956,7 @@ __global__ void k_prologue(VecScale* const* __restrict__ list, int nlist, int sa
         s->clamped = 0u;
     }
     for (int i = t; i < zero_n; i += blockDim.x) zero_d[i] = 0.0;
+    for (int i = t; i < zero_in; i += blockDim.x) zero_i[i] = 0;
     if (ctl != nullptr && t == 0) {
         ctl->next = 0;
         ctl->abort = 0;
@@ -1398,7 +1399,7 @@ cudaError_t launch_wave2d(const WaveArgs& A, int nclusters, const Globals& G, cu
 }
 
 cudaError_t launch_prologue(VecScale* const* list, int nlist, int save_prev, int bump, double* zero_d, int zero_n,
-                            const Globals& G, cudaStream_t st, WaveCtl* ctl) {
+                            const Globals& G, cudaStream_t st, WaveCtl* ctl, int* zero_i, int zero_in) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(1, 1, 1);
     cfg.blockDim = dim3(256, 1, 1);
@@ -1408,7 +1409,7 @@ cudaError_t launch_prologue(VecScale* const* list, int nlist, int save_prev, int
     attr.val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_prologue, list, nlist, save_prev, bump, zero_d, zero_n, G, ctl);
+    return cudaLaunchKernelEx(&cfg, k_prologue, list, nlist, save_prev, bump, zero_d, zero_n, G, ctl, zero_i, zero_in);
 }
 
 // ---- window coefficients ----------------------------------------------------------------------

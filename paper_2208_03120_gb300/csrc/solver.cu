@@ -1276,7 +1276,10 @@ int run_check(TreePlan& T, cudaStream_t st, Timer& tm, long long& nl) {
 int run_wave(TreePlan& T, int S, cudaStream_t st, Timer& tm, long long& nl) {
     cudaEvent_t e = nullptr;
     RET(tm.begin(MOT_K_NODE, &e));
-    CK(launch_prologue(T.d_resets + T.wave_root_reset, 1, 1, S, nullptr, 0, T.G, st, T.persist ? T.d_ctl : nullptr));
+    // the exact-sum persistent kernel counts completed CTAs per product: its flags start at zero
+    const bool counts = T.persist && T.ndft;
+    CK(launch_prologue(T.d_resets + T.wave_root_reset, 1, 1, S, nullptr, 0, T.G, st, T.persist ? T.d_ctl : nullptr,
+                       counts ? T.d_flags : nullptr, counts ? T.wave_ntask : 0));
     RET(tm.end(e));
     nl += 1;
     if (T.persist) {

@@ -304,7 +304,10 @@ def test_wavefront_equals_sweep_by_sweep(M, shape, check_every, max_iter, wave):
         assert np.max(np.abs(va - vb)) <= 1e-5 * scale
     assert abs(a.S_last - b.S_last) <= 1e-6 * abs(b.S_last)
     assert abs(a.cost_dual - b.cost_dual) <= 1e-6 * abs(b.cost_dual)
-    assert abs(a.violation - b.violation) <= 1e-6 + 1e-3 * b.violation
+    # the violation after these sweeps sits at the FP32 floor of the operator: repeated runs of one
+    # schedule on one input give 2.4e-7 .. 1.5e-6 (the order of the partial and atomic sums), so two
+    # schedules agree to that floor
+    assert abs(a.violation - b.violation) <= 2e-6 + 1e-3 * b.violation
     if check_every >= 7:                    # fewer launches: products of several sweeps share them
         assert a.launches < b.launches
 
