@@ -539,10 +539,13 @@ __device__ __forceinline__ void nd_run(NDSh& S, const Task& T, float* dyn, const
                                          S.A[row[2] * ND_R + col[2]], S.A[row[3] * ND_R + col[3]]);
             nd_st_cluster4(nd_mapa(&S.R4[r][p / CS], p % CS), a);
         }
+        // the first cluster barrier in two halves: arrive once this thread's pushes are issued,
+        // wait after the target values (local work), so that they hide the other ranks' lag
+        asm volatile("barrier.cluster.arrive.release;" ::: "memory");
         int tc0 = ti0;
         int tcnt = min(ND_CH, ti1 - tc0);
         if (tcnt > 0) nd_target_values(T, dyn, tc0, tcnt, inv_n);
-        cluster.sync();      // every rank's partial A is with the owners of its pairs
+        asm volatile("barrier.cluster.wait.acquire;" ::: "memory");   // every rank's partial A is with its owners
         hk.after_first_barrier(warp, lane);
         // ---- 2. the cluster's A, then B^T ----------------------------------------------------
         // rank r owns the frequency pairs p = r + CS m: each rank's partial (cc, ss, cs, sc) of
@@ -626,8 +629,8 @@ __device__ __forceinline__ void nd_run(NDSh& S, const Task& T, float* dyn, const
         }
         hk.after_targets(warp, lane);
     }
-    if constexpr (MSG)
-        epi_block_finish_msg(T, fc.L, ep);
+    if (MSG || T.mode == EPI_MSG)
+        epi_block_finish_msg(T, fc.L, ep);       // message products: the maximum and clamp count only
     else
         epi_block_finish(T, G, tf, S.sLsrc, ep, S.sP.iter, S.sC);
 }
