@@ -266,13 +266,28 @@ __global__ void __launch_bounds__(256, 3) k_c1_spread(const float* __restrict__ 
 
 // grid (ceil(nt / C1_TGT), ceil(n0 / 32)): convolution of 32 columns' grids, then two targets per
 // thread for each column, message epilogue (floor, maximum, clamp count) and block reduction.
+// With R.raw (a batch producing Gam_k, k >= 2): the row dots of phi^k's update are formed as the
+// columns are produced, raw_i += sum_c beta_k[c][i] phi^1_c Gam_k[c][i] over the block's columns
+// (beta_k and phi^1 normalised by their maxima, Gam_k as its mantissas: its maximum is not known
+// yet, so R.raw_sc carries Gam_k's log-scale with a unit maximum), added atomically.
+struct C1Rowdot {
+    const float* beta;        // beta_k [c][i] (nt per column)
+    const VecScale* s_beta;
+    const float* phi1;        // phi^1 [n0]
+    const VecScale* s_phi1;
+    float* raw;               // [nt]; nullptr: no row dots
+    VecScale* raw_sc;         // log-scale of Gam_k with maximum 1
+};
+
 __global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, const float* __restrict__ cvec,
                                                    const int* __restrict__ l0, const float* __restrict__ w, int nt,
                                                    int n0, int ng, float* __restrict__ Y, float floor_,
-                                                   VecScale* out_sc, const VecScale* sA, const VecScale* sB) {
+                                                   VecScale* out_sc, const VecScale* sA, const VecScale* sB,
+                                                   C1Rowdot R) {
     __shared__ float sGc[C1_COLS][128 + 1];
     __shared__ float sH[C1_COLS][128 + 1];
     __shared__ float sC[128];
+    __shared__ float sPh[C1_COLS];       // row dots: phi^1 of the block's columns, normalised
     __shared__ float s_mx[8];
     __shared__ unsigned int s_cl[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -280,6 +295,8 @@ __global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, 
     const int ncol = min(C1_COLS, n0 - c0);
     for (int i = tid; i < ng; i += blockDim.x) sC[i] = cvec[i];
     for (int i = tid; i < ncol * ng; i += blockDim.x) sGc[i / ng][i % ng] = G[(size_t)c0 * ng + i];
+    const bool rd = R.raw != nullptr;
+    if (rd && tid < C1_COLS) sPh[tid] = tid < ncol ? R.phi1[c0 + tid] * (1.f / mx_of(R.s_phi1, 0)) : 0.f;
     __syncthreads();
     // only the cells this block's targets read (targets are sorted by cell): [l0 of the first,
     // l0 of the last + MOT_W - 1], about a quarter of the grid per block
@@ -301,17 +318,21 @@ __global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, 
     __syncthreads();
     float mx = 0.f;
     unsigned int clamps = 0u;
-    auto emit = [&](float s, int q, int i) {
+    const float sbeta = rd ? 1.f / mx_of(R.s_beta, 0) : 0.f;
+    float part = 0.f;                                       // this thread's row dot of target i
+    auto emit = [&](float s, int q, int i, float b) {      // b: beta_k[c0 + q][i] (row dots)
         if (!(s >= floor_)) {
             s = floor_;
             clamps++;
         }
         mx = fmaxf(mx, s);
         Y[(size_t)(c0 + q) * nt + i] = s;
+        if (rd) part = fmaf(sPh[q] * b, s, part);
     };
     for (int k = 0; k < C1_TGT / 256; ++k) {
         const int i = blockIdx.x * C1_TGT + k * blockDim.x + tid;
         if (i >= nt) break;
+        part = 0.f;
         float t[MOT_W];
         const float* hp[MOT_W];                             // column 0 of each tap's grid cell
         const int b = l0[i];
@@ -321,21 +342,26 @@ __global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, 
             hp[a] = &sH[0][(b + a) & mask];
         }
         if (ncol == C1_COLS) {
+            // the row dots' beta_k values of this target: all loads issued before the columns' sums
+            float bv[C1_COLS];
+#pragma unroll
+            for (int q = 0; q < C1_COLS; ++q) bv[q] = rd ? __ldg(R.beta + (size_t)(c0 + q) * nt + i) : 0.f;
 #pragma unroll
             for (int q = 0; q < C1_COLS; ++q) {             // constant offsets q * (128 + 1)
                 float s = 0.f;
 #pragma unroll
                 for (int a = 0; a < MOT_W; ++a) s = fmaf(hp[a][q * (128 + 1)], t[a], s);
-                emit(s, q, i);
+                emit(s, q, i, bv[q]);
             }
         } else {
             for (int q = 0; q < ncol; ++q) {
                 float s = 0.f;
 #pragma unroll
                 for (int a = 0; a < MOT_W; ++a) s = fmaf(hp[a][q * (128 + 1)], t[a], s);
-                emit(s, q, i);
+                emit(s, q, i, rd ? __ldg(R.beta + (size_t)(c0 + q) * nt + i) : 0.f);
             }
         }
+        if (rd) atomicAdd(R.raw + i, part * sbeta);
     }
     mx = warp_max(mx);
 #pragma unroll
@@ -353,6 +379,7 @@ __global__ void __launch_bounds__(256) k_c1_gather(const float* __restrict__ G, 
             c += s_cl[k];
         }
         out_sc->ls = sA->ls + (double)logf(mx_of(sA, 0)) + sB->ls + (double)logf(mx_of(sB, 0));
+        if (rd) R.raw_sc->ls = out_sc->ls;       // its maximum stays 1 (never set)
         atomic_max_pos(&out_sc->mx_bits, m);
         if (c) atomicAdd(&out_sc->clamped, c);
     }
@@ -410,7 +437,8 @@ cudaError_t launch_c1_circulant(const float* D, int M, int n, float* c, cudaStre
 cudaError_t launch_c1_batch(const float* X, const VecScale* sX, const float* phi, const VecScale* sP, const int* l0s,
                             const float* ws, int ns, const int* l0t, const float* wt, int nt, int n0, int ng,
                             const float* cvec, float* G, float* Y, float floor_, VecScale* out_sc, cudaStream_t st,
-                            int stage) {
+                            int stage, const float* rd_beta, const VecScale* rd_sbeta, const float* rd_phi1,
+                            const VecScale* rd_sphi1, float* rd_raw, VecScale* rd_raw_sc) {
     const int nb = (n0 + C1_COLS - 1) / C1_COLS;
     if (stage == 0) {
         cudaError_t e = cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n0 * ng, st);
@@ -421,8 +449,9 @@ cudaError_t launch_c1_batch(const float* X, const VecScale* sX, const float* phi
         const int items = nb * splits;
         k_c1_spread<<<std::min(items, 3 * 152), 256, 0, st>>>(X, sX, phi, sP, l0s, ws, ns, n0, ng, splits, G);
     } else {
+        const C1Rowdot R{rd_beta, rd_sbeta, rd_phi1, rd_sphi1, rd_raw, rd_raw_sc};
         k_c1_gather<<<dim3((nt + C1_TGT - 1) / C1_TGT, nb), 256, 0, st>>>(G, cvec, l0t, wt, nt, n0, ng, Y, floor_,
-                                                                         out_sc, sP, sX);
+                                                                         out_sc, sP, sX, R);
     }
     return cudaGetLastError();
 }

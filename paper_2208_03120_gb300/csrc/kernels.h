@@ -79,7 +79,9 @@ cudaError_t launch_c1_circulant(const float* D, int M, int n, float* c, cudaStre
 cudaError_t launch_c1_batch(const float* X, const VecScale* sX, const float* phi, const VecScale* sP, const int* l0s,
                             const float* ws, int ns, const int* l0t, const float* wt, int nt, int n0, int ng,
                             const float* cvec, float* G, float* Y, float floor_, VecScale* out_sc, cudaStream_t st,
-                            int stage);
+                            int stage, const float* rd_beta = nullptr, const VecScale* rd_sbeta = nullptr,
+                            const float* rd_phi1 = nullptr, const VecScale* rd_sphi1 = nullptr,
+                            float* rd_raw = nullptr, VecScale* rd_raw_sc = nullptr);
 // One-block iteration prologue (resets, iteration counter, accumulators; with ctl: the persistent
 // kernel's claim counter and abort word reset and its epoch advanced).
 cudaError_t launch_prologue(VecScale* const* list, int nlist, int save_prev, int bump, double* zero_d, int zero_n,

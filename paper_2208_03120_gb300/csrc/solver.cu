@@ -1795,7 +1795,9 @@ void c_build(CirclePlan& C) {
             } else {
                 c_add_factor(C, C.beta[k], C.beta_sc(k));
                 c_add_factor(C, C.phi[0], C.phi_sc(0));
-                c_add_factor(C, C.gam[k], C.gam_sc(k));
+                // row dots formed in the batch (k >= 2 on the 1-D path) take Gam_k unnormalised:
+                // its log-scale with a unit maximum
+                c_add_factor(C, C.gam[k], (C.c1 && k >= 2) ? C.raw_sc(k) : C.gam_sc(k));
             }
             t.snf = 3;
             t.phi = C.phi[k];
@@ -1861,11 +1863,19 @@ int c_run_batch(CirclePlan& C, CBatch& B, cudaStream_t st, Timer& tm, long long&
     cudaEvent_t e = nullptr;
     if (C.c1) {
         const int s = B.s, t = B.t;
+        // a batch producing Gam_t (t >= 2) also forms the row dots of phi^t's update (c_node)
+        const bool rows = t >= 2 && B.Y == C.gam[t];
         for (int stage = 0; stage < 2; ++stage) {
             RET(tm.begin(stage == 0 ? MOT_K_SPREAD : MOT_K_GATHER, &e));
-            CK(launch_c1_batch(B.X, B.sX, C.phi[s], C.phi_sc(s), C.c1_l0[s], C.c1_w[s], C.n[s], C.c1_l0[t],
-                               C.c1_w[t], C.n[t], C.n0, C.g.n, C.c1_c[B.edge], C.c1_G, B.Y, C.G.floor_, B.out_sc,
-                               st, stage));
+            if (rows)
+                CK(launch_c1_batch(B.X, B.sX, C.phi[s], C.phi_sc(s), C.c1_l0[s], C.c1_w[s], C.n[s], C.c1_l0[t],
+                                   C.c1_w[t], C.n[t], C.n0, C.g.n, C.c1_c[B.edge], C.c1_G, B.Y, C.G.floor_,
+                                   B.out_sc, st, stage, C.beta[t], C.beta_sc(t), C.phi[0], C.phi_sc(0), C.raw[t],
+                                   C.raw_sc(t)));
+            else
+                CK(launch_c1_batch(B.X, B.sX, C.phi[s], C.phi_sc(s), C.c1_l0[s], C.c1_w[s], C.n[s], C.c1_l0[t],
+                                   C.c1_w[t], C.n[t], C.n0, C.g.n, C.c1_c[B.edge], C.c1_G, B.Y, C.G.floor_,
+                                   B.out_sc, st, stage));
             RET(tm.end(e));
         }
         nl += 3;                // memset, spread, gather
@@ -1924,18 +1934,22 @@ int c_run_batch_tc(CirclePlan& C, CBatch& B, cudaStream_t st, Timer& tm, long lo
 
 int c_node(CirclePlan& C, int k, int pass, cudaStream_t st, Timer& tm, long long& nl) {
     cudaEvent_t e = nullptr;
-    RET(tm.begin(MOT_K_CIRCLE, &e));
-    if (k == 0)
-        CK(launch_colsum(C.gam[1], C.gam_sc(1), C.beta[1], C.beta_sc(1), C.phi[1], C.phi_sc(1), C.n[1], C.n0, C.raw[0],
-                         st));
-    else
-        CK(launch_rowdot(C.beta[k], C.beta_sc(k), C.gam[k], C.gam_sc(k), C.phi[0], C.phi_sc(0), C.n[k], C.n0,
-                         C.raw[k], st));
-    RET(tm.end(e));
+    // on the 1-D path the row dots of k >= 2 were formed by the batch that produced Gam_k
+    if (!(C.c1 && k >= 2)) {
+        RET(tm.begin(MOT_K_CIRCLE, &e));
+        if (k == 0)
+            CK(launch_colsum(C.gam[1], C.gam_sc(1), C.beta[1], C.beta_sc(1), C.phi[1], C.phi_sc(1), C.n[1], C.n0,
+                             C.raw[0], st));
+        else
+            CK(launch_rowdot(C.beta[k], C.beta_sc(k), C.gam[k], C.gam_sc(k), C.phi[0], C.phi_sc(0), C.n[k], C.n0,
+                             C.raw[k], st));
+        RET(tm.end(e));
+        nl += 1;
+    }
     RET(tm.begin(MOT_K_NODE, &e));
     CK(launch_epi(C.d, C.d_node + pass * C.K + k, 1, std::min((C.n[k] + 255) / 256, 1024), C.G, st));
     RET(tm.end(e));
-    nl += 2;
+    nl += 1;
     return MOT_OK;
 }
 
