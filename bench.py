@@ -784,27 +784,45 @@ def main():
         serving = serving_replay(M, W, dev, args.serving_requests, flush)
 
     # ---- end to end through the C ABI with host buffers ---------------------------------
-    xh = [torch.from_numpy(a).pin_memory() for a in prob.x]
-    muh = [torch.from_numpy(m).pin_memory() for m in prob.mu]
-    uh = [torch.empty(n, dtype=torch.float64).pin_memory() for n in prob.n]
-    xd = [torch.empty_like(a, device=dev) for a in xh]
-    mud = [torch.empty_like(m, device=dev) for m in muh]
-    h2d = sum(a.numel() * a.element_size() for a in xh) + sum(m.numel() * m.element_size() for m in muh)
-    d2h = sum(a.numel() * a.element_size() for a in uh)
+    # the step's inputs (every set's points and weights) and results (every set's potentials) each
+    # live in one contiguous pinned host buffer per type, copied in one transfer each way; the
+    # per-set arguments of mot_solve are views of the matching device buffers
+    def offsets(sizes):                     # each array starts on a 256-byte boundary
+        offs, o = [], 0
+        for n in sizes:
+            offs.append(o)
+            o += (int(n) + 63) // 64 * 64
+        return offs, o
+    xo, xt = offsets(a.size for a in prob.x)
+    mo, mt = offsets(m.size for m in prob.mu)
+    uo, ut = offsets(prob.n)
+    xh_all = torch.zeros(xt, dtype=torch.float32).pin_memory()
+    muh_all = torch.zeros(mt, dtype=torch.float64).pin_memory()
+    for o, a in zip(xo, prob.x):
+        xh_all[o:o + a.size] = torch.from_numpy(a.reshape(-1))
+    for o, m in zip(mo, prob.mu):
+        muh_all[o:o + m.size] = torch.from_numpy(m.reshape(-1))
+    uh_all = torch.empty(ut, dtype=torch.float64).pin_memory()
+    xd_all = torch.empty_like(xh_all, device=dev)
+    mud_all = torch.empty_like(muh_all, device=dev)
+    ud_all = torch.empty(ut, dtype=torch.float64, device=dev)
+    xd = [xd_all[o:o + a.size].view(a.shape) for o, a in zip(xo, prob.x)]
+    mud = [mud_all[o:o + m.size] for o, m in zip(mo, prob.mu)]
+    ud = [ud_all[o:o + n] for o, n in zip(uo, prob.n)]
+    # bytes of the inputs and results themselves (the copies also move the alignment padding)
+    h2d = sum(a.nbytes for a in prob.x) + sum(m.nbytes for m in prob.mu)
+    d2h = 8 * sum(int(n) for n in prob.n)
     et, ei = 0.0, 0
     for r in range(max(1, min(args.steps, 5)) + 1):
         with torch.cuda.stream(stream):
             flush.random_(0, 255)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for a, b in zip(xd, xh):
-                a.copy_(b, non_blocking=True)
-            for a, b in zip(mud, muh):
-                a.copy_(b, non_blocking=True)
+            xd_all.copy_(xh_all, non_blocking=True)
+            mud_all.copy_(muh_all, non_blocking=True)
             o4 = M.mot_solve(xd, mud, prob.eta, topo, edges=prob.edges, root=prob.root, opt=opt, workspace=ws,
-                             stream=stream, u_out=u)
-            for a, b in zip(uh, u):
-                a.copy_(b, non_blocking=True)
+                             stream=stream, u_out=ud)
+            uh_all.copy_(ud_all, non_blocking=True)
             e1.record(stream)
         e1.synchronize()
         if r > 0:
